@@ -1,0 +1,144 @@
+"""GB300-native per-cell chemistry substep (DeepFlame's CVODE / DNN hot path).
+
+Python front end of ``libdfchem.so``: torch tensors in, device pointers to
+the C ABI of ``include/df_chem.h``.  PyTorch provides device memory and
+streams only; every step of the computation runs in the library's kernels.
+
+    mech = Mechanism("mech.json")          # or a mechanism dict
+    status, nsub = integrate(mech, T, p, Y, dt)   # T, Y updated in place
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+import tempfile
+
+from . import _lib
+
+__all__ = ["Mechanism", "rhs", "jacobian", "integrate", "IntegOpts", "default_opts"]
+
+IntegOpts = _lib.IntegOpts
+default_opts = _lib.default_opts
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, name, dtype=None, numel=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Mechanism:
+    """A loaded mechanism (species, reactions, thermo) resident on the device."""
+
+    def __init__(self, src):
+        lib = _lib.load()
+        path = src
+        tmp = None
+        if isinstance(src, dict):
+            fd, tmp = tempfile.mkstemp(suffix=".json")
+            with os.fdopen(fd, "w") as f:
+                json.dump(src, f)
+            path = tmp
+        h = C.c_void_p()
+        try:
+            _lib.check(lib.df_mech_load(os.fsencode(path), C.byref(h)), "df_mech_load")
+        finally:
+            if tmp:
+                os.unlink(tmp)
+        self._h = h
+        ns, nr = C.c_int(), C.c_int()
+        _lib.check(lib.df_mech_info(h, C.byref(ns), C.byref(nr)), "df_mech_info")
+        self.n_species, self.n_reactions = ns.value, nr.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_lnA(self, lnA=None, stream=None):
+        """Override ln A_j (device tensor of M doubles); None restores the file."""
+        torch = _torch()
+        ptr = None if lnA is None else _dptr(lnA, "lnA", torch.float64, self.n_reactions)
+        _lib.check(_lib.load().df_mech_set_lnA(self._h, ptr, _stream_ptr(stream)), "df_mech_set_lnA")
+
+    def last_stats(self, stream=None):
+        a, r = C.c_int64(), C.c_int64()
+        _lib.check(_lib.load().df_chem_last_stats(self._h, C.byref(a), C.byref(r), _stream_ptr(stream)),
+                   "df_chem_last_stats")
+        return a.value, r.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().df_mech_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _cells(mech, T, p, Y):
+    torch = _torch()
+    n = T.numel()
+    return n, _dptr(T, "T", torch.float64), _dptr(p, "p", torch.float64, n), \
+        _dptr(Y, "Y", torch.float64, mech.n_species * n)
+
+
+def rhs(mech: Mechanism, T, p, Y, stream=None):
+    """dy/dt [(N+1), ncells] and heat release [ncells] (W/m^3)."""
+    torch = _torch()
+    n, pT, pp, pY = _cells(mech, T, p, Y)
+    dydt = torch.empty((mech.n_species + 1, n), dtype=torch.float64, device=T.device)
+    qdot = torch.empty(n, dtype=torch.float64, device=T.device)
+    _lib.check(_lib.load().df_chem_rhs(mech.handle, n, pT, pp, pY, _dptr(dydt, "dydt"), _dptr(qdot, "qdot"),
+                                       _stream_ptr(stream)), "df_chem_rhs")
+    return dydt, qdot
+
+
+def jacobian(mech: Mechanism, T, p, Y, stream=None):
+    """Analytic Jacobian [ncells, N+1, N+1] of (dT/dt, dY/dt) w.r.t. (T, Y)."""
+    torch = _torch()
+    n, pT, pp, pY = _cells(mech, T, p, Y)
+    m = mech.n_species + 1
+    J = torch.empty((n, m, m), dtype=torch.float64, device=T.device)
+    _lib.check(_lib.load().df_chem_jacobian(mech.handle, n, pT, pp, pY, _dptr(J, "J"), _stream_ptr(stream)),
+               "df_chem_jacobian")
+    return J
+
+
+def integrate(mech: Mechanism, T, p, Y, dt: float, opts: IntegOpts | None = None, status=None,
+              nsub=None, stream=None):
+    """Advance every cell over dt in place (T [ncells], Y [N, ncells]).
+    Returns (status, nsub) int32 device tensors."""
+    torch = _torch()
+    n, pT, pp, pY = _cells(mech, T, p, Y)
+    if status is None:
+        status = torch.empty(n, dtype=torch.int32, device=T.device)
+    if nsub is None:
+        nsub = torch.empty(n, dtype=torch.int32, device=T.device)
+    o = C.byref(opts) if opts is not None else None
+    _lib.check(_lib.load().df_chem_integrate(mech.handle, n, pT, pp, pY, float(dt), o,
+                                             _dptr(status, "status", torch.int32, n),
+                                             _dptr(nsub, "nsub", torch.int32, n), _stream_ptr(stream)),
+               "df_chem_integrate")
+    return status, nsub

@@ -1,0 +1,197 @@
+// C-ABI entry points: argument checks, handle life cycle, error reporting.
+// Every compute step runs in the kernels of integrate.cu (and the other .cu
+// files); this file only validates and forwards.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace df {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DF_OK;
+  return set_error(e == cudaErrorMemoryAllocation ? DF_ENOMEM : DF_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace df
+
+using namespace df;
+
+extern "C" {
+
+void df_integ_opts_default(df_integ_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->rtol = 1e-8;
+  o->atol_Y = 1e-14;
+  o->atol_T = 1e-8;
+  o->h0 = 1e-9;
+  o->h_min = 1e-22;
+  o->max_substeps = 100000;
+  o->method = 0;
+  o->block_threads = 0;
+  o->blocks_per_sm = 0;
+  o->order_by_T = 0;
+}
+
+const char* df_strerror(int code) {
+  switch (code) {
+    case DF_OK: return "success";
+    case DF_EINVAL: return "invalid argument";
+    case DF_ENOMEM: return "out of memory";
+    case DF_ECUDA: return "CUDA error";
+    case DF_EMECH: return "invalid mechanism";
+    case DF_EWORKSPACE: return "workspace too small";
+    case DF_ETIMEOUT: return "bounded device wait ran out";
+    case DF_EUNSUPPORTED: return "unsupported size or feature";
+    default: return "unknown error";
+  }
+}
+
+int df_get_last_error_detail(char* buf, size_t n) {
+  const std::string& s = g_last_error;
+  if (buf && n > 0) {
+    size_t k = s.size() < n - 1 ? s.size() : n - 1;
+    memcpy(buf, s.data(), k);
+    buf[k] = 0;
+  }
+  return (int)s.size();
+}
+
+int df_mech_load(const char* path, df_mech** out) {
+  if (!path || !out) return set_error(DF_EINVAL, "df_mech_load: null argument");
+  *out = nullptr;
+  df_mech* m = new (std::nothrow) df_mech();
+  if (!m) return set_error(DF_ENOMEM, "df_mech_load: host allocation");
+  int rc = parse_mechanism(path, m);
+  if (rc) {
+    delete m;
+    return rc;
+  }
+  rc = cuda_check(cudaGetDevice(&m->device), "cudaGetDevice");
+  cudaDeviceProp prop;
+  if (!rc) rc = cuda_check(cudaGetDeviceProperties(&prop, m->device), "cudaGetDeviceProperties");
+  if (!rc) {
+    m->num_sms = prop.multiProcessorCount;
+    m->max_smem_optin = prop.sharedMemPerBlockOptin;
+  }
+  if (!rc) rc = cuda_check(cudaMalloc(&m->blob_dev, sizeof(double) * m->dims.total + 8), "cudaMalloc blob");
+  if (!rc)
+    rc = cuda_check(cudaMemcpy(m->blob_dev, m->blob_host.data(), sizeof(double) * m->dims.total,
+                               cudaMemcpyHostToDevice),
+                    "upload mechanism");
+  if (!rc) rc = cuda_check(cudaMalloc(&m->counters, 4 * sizeof(unsigned long long)), "cudaMalloc counters");
+  if (!rc) rc = cuda_check(cudaMemset(m->counters, 0, 4 * sizeof(unsigned long long)), "clear counters");
+  if (rc) {
+    df_mech_free(m);
+    return rc;
+  }
+  *out = m;
+  return DF_OK;
+}
+
+void df_mech_free(df_mech* m) {
+  if (!m) return;
+  if (m->blob_dev) cudaFree(m->blob_dev);
+  if (m->counters) cudaFree(m->counters);
+  delete m;
+}
+
+int df_mech_info(const df_mech* m, int* n_species, int* n_reactions) {
+  if (!m) return set_error(DF_EINVAL, "df_mech_info: null handle");
+  if (n_species) *n_species = m->dims.N;
+  if (n_reactions) *n_reactions = m->dims.M;
+  return DF_OK;
+}
+
+int df_mech_set_lnA(df_mech* m, const double* lnA, df_stream_t stream) {
+  if (!m) return set_error(DF_EINVAL, "df_mech_set_lnA: null handle");
+  if (lnA && !is_device_ptr(lnA)) return set_error(DF_EINVAL, "df_mech_set_lnA: lnA must be device memory");
+  return launch_set_lnA(m, lnA, (cudaStream_t)stream);
+}
+
+static int check_cells(const char* fn, const df_mech* m, int64_t ncells) {
+  if (!m) return set_error(DF_EINVAL, std::string(fn) + ": null mechanism");
+  if (ncells < 0 || ncells > (int64_t)1 << 31)
+    return set_error(DF_EINVAL, std::string(fn) + ": ncells must be in [0, 2^31]");
+  return DF_OK;
+}
+
+static int check_dev(const char* fn, const char* name, const void* p) {
+  if (!is_device_ptr(p)) return set_error(DF_EINVAL, std::string(fn) + ": " + name + " must be device memory");
+  return DF_OK;
+}
+
+int df_chem_rhs(const df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y,
+                double* dydt, double* qdot, df_stream_t stream) {
+  int rc = check_cells("df_chem_rhs", m, ncells);
+  if (rc || ncells == 0) return rc;
+  if ((rc = check_dev("df_chem_rhs", "T", T)) || (rc = check_dev("df_chem_rhs", "p", p)) ||
+      (rc = check_dev("df_chem_rhs", "Y", Y)) || (rc = check_dev("df_chem_rhs", "dydt", dydt)))
+    return rc;
+  if (qdot && (rc = check_dev("df_chem_rhs", "qdot", qdot))) return rc;
+  return launch_rhs(m, ncells, T, p, Y, dydt, qdot, (cudaStream_t)stream);
+}
+
+int df_chem_jacobian(const df_mech* m, int64_t ncells, const double* T, const double* p,
+                     const double* Y, double* J, df_stream_t stream) {
+  int rc = check_cells("df_chem_jacobian", m, ncells);
+  if (rc || ncells == 0) return rc;
+  if ((rc = check_dev("df_chem_jacobian", "T", T)) || (rc = check_dev("df_chem_jacobian", "p", p)) ||
+      (rc = check_dev("df_chem_jacobian", "Y", Y)) || (rc = check_dev("df_chem_jacobian", "J", J)))
+    return rc;
+  return launch_jacobian(m, ncells, T, p, Y, J, (cudaStream_t)stream);
+}
+
+int df_chem_integrate(const df_mech* mc, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                      const df_integ_opts* opts, int32_t* status, int32_t* nsub, df_stream_t stream) {
+  df_mech* m = const_cast<df_mech*>(mc);
+  int rc = check_cells("df_chem_integrate", m, ncells);
+  if (rc || ncells == 0) return rc;
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return set_error(DF_EINVAL, "df_chem_integrate: dt must be finite and >= 0");
+  if ((rc = check_dev("df_chem_integrate", "T", T)) || (rc = check_dev("df_chem_integrate", "p", p)) ||
+      (rc = check_dev("df_chem_integrate", "Y", Y)) || (rc = check_dev("df_chem_integrate", "status", status)))
+    return rc;
+  if (nsub && (rc = check_dev("df_chem_integrate", "nsub", nsub))) return rc;
+  df_integ_opts o;
+  if (opts) o = *opts;
+  else df_integ_opts_default(&o);
+  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
+      o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.block_threads < 0 || o.block_threads > 1024 ||
+      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0)
+    return set_error(DF_EINVAL, "df_chem_integrate: invalid options");
+  return launch_integrate(m, ncells, T, p, Y, dt, o, status, nsub, (cudaStream_t)stream);
+}
+
+int df_chem_last_stats(const df_mech* m, int64_t* accepted, int64_t* rejected, df_stream_t stream) {
+  if (!m) return set_error(DF_EINVAL, "df_chem_last_stats: null handle");
+  unsigned long long h[4];
+  int rc = cuda_check(cudaMemcpyAsync(h, m->counters, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+                      "read counters");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "synchronise stream");
+  if (rc) return rc;
+  if (accepted) *accepted = (int64_t)h[1];
+  if (rejected) *rejected = (int64_t)h[2];
+  return DF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// FP64 throughput probe: eight independent fused multiply-add chains per
+// thread on a grid that fills every SM.  The measured rate is the denominator
+// of the integrator's FP64 roofline fraction.
+#include "common.cuh"
+#include "../../include/df_probe.h"
+
+namespace df {
+
+__global__ void __launch_bounds__(256) k_dfma_chains(double* out, int iters, double a, double b) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double x0 = 1.0 + tid * 1e-9, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+  double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[tid] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+}  // namespace df
+
+using namespace df;
+
+extern "C" int df_probe_fp64_peak(int iters, double* gflops, double* ms) {
+  if (iters < 1 || !gflops) return set_error(DF_EINVAL, "df_probe_fp64_peak: iters >= 1 and gflops required");
+  int dev = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  cudaDeviceProp prop;
+  if ((rc = cuda_check(cudaGetDeviceProperties(&prop, dev), "properties"))) return rc;
+  const int threads = 256;
+  const int blocks = prop.multiProcessorCount * 8;
+  double* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rc = cuda_check(cudaMalloc(&out, sizeof(double) * threads * blocks), "cudaMalloc");
+  if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && !rc; ++rep) {
+    cudaEventRecord(e0, st);
+    k_dfma_chains<<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1, st);
+    rc = cuda_check(cudaEventSynchronize(e1), "probe kernel");
+    float t = 0.f;
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+    if (!rc && rep > 0 && t < best) best = t;  // first run is warm-up
+  }
+  if (!rc) {
+    const double flops = 2.0 * 8.0 * (double)iters * threads * blocks;
+    *gflops = flops / (best * 1e-3) / 1e9;
+    if (ms) *ms = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  return rc;
+}
