@@ -1,0 +1,310 @@
+"""Throughput of the per-cell chemistry substep on GB300.
+
+One step = one df_chem_integrate call that advances every cell of the
+uneven-stiffness workload (9-species H2/air mechanism, 2^20 cells, bimodal
+T ~ U[700,1000] | U[1800,2500] K, p ~ U[1,10] atm, dt = 1 us) from its seeded
+initial state, in one persistent launch.  Metric: cell-steps/s (cells
+advanced by one dt per second), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the CPU oracle (FP64 Radau IIA, rtol 1e-10) on the
+host cores over bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "h2air-9sp-25r bimodal-T 2^20 cells dt=1us (uneven-stiffness batch)"
+NCELLS = 1 << 20
+METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
+UNIT = "cell-steps/s"
+# FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
+# 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 3.42e9) of one launch on
+# 65536 cells of this field divided by the 152525 attempts that launch counted
+# (profiles/integrator_thread9_h2air_bimodal.md).
+FLOP_PER_SUBSTEP = 22416
+
+
+def _rank_info():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(sample_cells: int, threads: int):
+    """The oracle as it stands, timed on the host cores over a bounded sample."""
+    from oracle.oracle import Mech
+    from paper_2210_07094_gb300 import synth
+    mech = synth.h2_air_mechanism()
+    f = synth.field(1, mech, sample_cells, seed=synth.FIELD_SEED + 1 + 1000)
+    o = Mech(mech)
+    t0 = time.perf_counter()
+    _, _, st, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"], threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": sample_cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sample_cells} cells of the same bimodal field (seeded), Radau IIA rtol 1e-10, "
+                      f"OpenMP over cells; {dt:.2f} s", "failed_cells": int(np.sum(st != 0))}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_info()
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    sample = args.ref_cells
+    from oracle.oracle import Mech
+    from paper_2210_07094_gb300 import synth
+    mech = synth.h2_air_mechanism()
+    o = Mech(mech)
+    times = []
+    for s in range(args.warmup + args.steps):
+        f = synth.field(1, mech, sample, seed=synth.FIELD_SEED + 1 + s)
+        t0 = time.perf_counter()
+        o.integrate(f["T"], f["p"], f["Y"], f["dt"], threads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = sample * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_cells_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} cells per step of the bimodal field, Radau IIA rtol 1e-10"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-cells", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=NCELLS,
+                    help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2210_07094_gb300 as df
+    from paper_2210_07094_gb300 import synth
+
+    rank, world, local = _rank_info()
+    ncells = args.cells
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    mech = synth.h2_air_mechanism()
+    m = df.Mechanism(mech)
+    # each rank advances its own 2^20 cells (independent cells: weak scaling)
+    f = synth.field(1, mech, ncells, seed=synth.FIELD_SEED + 1 + 7919 * rank)
+    dev = torch.device("cuda", local)
+    T0 = torch.tensor(f["T"], device=dev)
+    p = torch.tensor(f["p"], device=dev)
+    Y0 = torch.tensor(f["Y"], device=dev)
+    T, Y = T0.clone(), Y0.clone()
+    status = torch.empty(ncells, dtype=torch.int32, device=dev)
+    nsub = torch.empty(ncells, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        T.copy_(T0)
+        Y.copy_(Y0)
+        df.integrate(m, T, p, Y, f["dt"], status=status, nsub=nsub)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").strip().isdigit() else local)
+    clocks.start()
+    time.sleep(0.5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    acc_tot = rej_tot = 0
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict L2 between timed steps (not timed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        a, r = m.last_stats()  # synchronises; outside the events
+        acc_tot += a
+        rej_tot += r
+    barrier()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * ncells * args.steps / t_max
+    st = status.cpu().numpy()
+    ns = nsub.cpu().numpy()
+
+    # end to end through the public API with host buffers (pinned), per step:
+    # H2D of T, p, Y; integrate; D2H of T, Y, status
+    Th = torch.tensor(f["T"]).pin_memory()
+    ph = torch.tensor(f["p"]).pin_memory()
+    Yh = torch.tensor(f["Y"]).pin_memory()
+    To_h = torch.empty_like(Th).pin_memory()
+    Yo_h = torch.empty_like(Yh).pin_memory()
+    st_h = torch.empty(ncells, dtype=torch.int32).pin_memory()
+    Td, pd, Yd = torch.empty_like(T0), torch.empty_like(p), torch.empty_like(Y0)
+    h2d = (Th.numel() + ph.numel() + Yh.numel()) * 8
+    d2h = (To_h.numel() + Yo_h.numel()) * 8 + st_h.numel() * 4
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Td.copy_(Th, non_blocking=True)
+        pd.copy_(ph, non_blocking=True)
+        Yd.copy_(Yh, non_blocking=True)
+        df.integrate(m, Td, pd, Yd, f["dt"], status=status, nsub=nsub)
+        To_h.copy_(Td, non_blocking=True)
+        Yo_h.copy_(Yd, non_blocking=True)
+        st_h.copy_(status, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    te = torch.tensor([e2e_t], device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * ncells * e2e_steps / float(te.item())
+
+    peaks = _peaks()
+    subs = (acc_tot + rej_tot) / args.steps
+    roof = None
+    fp64_peak = None
+    from paper_2210_07094_gb300 import _lib
+    import ctypes as C
+    g = C.c_double()
+    _lib.check(_lib.load().df_probe_fp64_peak(20000, C.byref(g), None), "df_probe_fp64_peak")
+    fp64_peak = g.value
+    if FLOP_PER_SUBSTEP:
+        achieved = FLOP_PER_SUBSTEP * subs / (t_local / args.steps) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (fp64_peak / 1e3), "traffic": None,
+                "peak_source": "measured FP64 DFMA throughput (df_probe_fp64_peak), this GPU, this run",
+                "flop_per_substep": FLOP_PER_SUBSTEP}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if ncells == NCELLS else f"profiling case: {ncells} cells of the same field",
+                   "cells_per_gpu": ncells, "mechanism": "9 species / 25 reactions "
+                   "(4 third-body, 2 Troe)", "method": "RODAS4 (default tolerances rtol 1e-6, atol_Y 1e-10, atol_T 1e-6 K)",
+                   "l2": "256 MB buffer written between timed steps (not timed)",
+                   "step": "D2D reset of T, Y to the initial state + one integrate launch",
+                   "parallelism": f"replicas x{world} (independent cells)"},
+        "substeps": {"accepted_per_step": acc_tot / args.steps, "rejected_per_step": rej_tot / args.steps,
+                     "nsub_mean": float(ns.mean()), "nsub_max": int(ns.max()), "nsub_min": int(ns.min()),
+                     "failed_cells": int(np.sum(st != 0))},
+        "roofline": roof,
+        "fp64_peak_gflops_measured": fp64_peak,
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,7 +70,9 @@ typedef struct df_integ_opts {
   int32_t block_threads;  /* 0: autotune; else threads per block               */
   int32_t blocks_per_sm;  /* 0: autotune; else resident blocks per SM          */
   int32_t order_by_T;     /* 1: hand out hot cells first (longest-work first)  */
-  int32_t reserved[3];
+  int32_t path;           /* 0: auto (thread per cell if N <= 16), 1: thread per
+                             cell, 2: warp per cell                            */
+  int32_t reserved[2];
 } df_integ_opts;
 
 void df_integ_opts_default(df_integ_opts* opts);
@@ -135,6 +137,39 @@ int df_chem_jacobian(const df_mech* mech, int64_t ncells, const double* T, const
 int df_chem_integrate(const df_mech* mech, int64_t ncells, double* T, const double* p, double* Y,
                       double dt, const df_integ_opts* opts, int32_t* status, int32_t* nsub,
                       df_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint of the integrator (an extension beyond the paper: kinetic
+ * sensitivity and calibration of the chemistry substep of Sec. 2.3).
+ *
+ * Gradient of L = sum_c [ gT1[c] T_c(dt) + sum_k gY1[k*ncells+c] Y_kc(dt)
+ *                         + gQ1[c] qdot_c(dt) ]
+ * (qdot = -sum_k H_k wdot_k in W/m^3 at the final state) with respect to each
+ * cell's initial T, Y and to ln A_j of every reaction, for the map the
+ * integrator computes with RODAS4 and the given options, its accepted step
+ * sequence held fixed (discrete adjoint).  The call recomputes the forward
+ * pass, storing one checkpoint per accepted step, then sweeps back.
+ *
+ *  T0, p, Y0     inputs as for df_chem_integrate (device, not modified)
+ *  gT1, gY1, gQ1 cotangents (device; each may be NULL = 0)
+ *  gT0 [ncells], gY0 [N*ncells] (device, may be NULL): dL/dT0, dL/dY0
+ *  g_lnA [M] (device, may be NULL): dL/d ln A_j summed over cells (summation
+ *                order fixed: bitwise reproducible)
+ *  status, nsub [ncells] (device; nsub may be NULL): per-cell status and number
+ *                of accepted steps; a cell with more than max_steps accepted
+ *                steps gets DF_CELL_MAXSTEPS and a zero gradient
+ *  workspace     device memory of at least df_chem_adjoint_workspace_size()
+ *                bytes, owned by the caller.  On return its first
+ *                ncells*max_steps*(N+2) doubles hold the checkpoints
+ *                [cell][step][T, Y_1..Y_N, h] of the accepted steps.
+ * Built for mechanisms of 3 and 9 species (one cell per thread); other sizes
+ * return DF_EUNSUPPORTED.  Errors: DF_EINVAL, DF_EWORKSPACE, DF_EUNSUPPORTED,
+ * DF_ECUDA. */
+int df_chem_adjoint_workspace_size(const df_mech* mech, int64_t ncells, int32_t max_steps, size_t* bytes);
+int df_chem_adjoint(const df_mech* mech, int64_t ncells, const double* T0, const double* p, const double* Y0,
+                    double dt, const df_integ_opts* opts, int32_t max_steps, const double* gT1,
+                    const double* gY1, const double* gQ1, double* gT0, double* gY0, double* g_lnA,
+                    int32_t* status, int32_t* nsub, void* workspace, size_t ws_bytes, df_stream_t stream);
 
 /* Work counters of the last df_chem_integrate on this handle (host values; the
  * call synchronises `stream`): accepted and rejected substeps summed over all

@@ -17,6 +17,11 @@ extern "C" {
  * Returns 0 or a negative DF_E* code (DF_EINVAL for iters < 1). */
 int df_probe_fp64_peak(int iters, double* gflops, double* ms);
 
+/* y[i] = exp(x[i]) for i < n by the library's own table-driven exponential
+ * (the one the rate kernels use), so that its accuracy can be checked against
+ * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */
+int df_probe_exp(const double* x, double* y, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

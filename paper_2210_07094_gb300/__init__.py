@@ -16,7 +16,8 @@ import tempfile
 
 from . import _lib
 
-__all__ = ["Mechanism", "rhs", "jacobian", "integrate", "IntegOpts", "default_opts"]
+__all__ = ["Mechanism", "rhs", "jacobian", "integrate", "adjoint", "chem_step", "IntegOpts",
+           "default_opts"]
 
 IntegOpts = _lib.IntegOpts
 default_opts = _lib.default_opts
@@ -142,3 +143,87 @@ def integrate(mech: Mechanism, T, p, Y, dt: float, opts: IntegOpts | None = None
                                              _dptr(nsub, "nsub", torch.int32, n), _stream_ptr(stream)),
                "df_chem_integrate")
     return status, nsub
+
+
+def adjoint(mech: Mechanism, T0, p, Y0, dt: float, gT1=None, gY1=None, gQ1=None,
+            opts: IntegOpts | None = None, max_steps: int = 64, stream=None):
+    """Discrete adjoint of integrate() (RODAS4, accepted steps frozen).
+
+    Returns a dict with gT0 [ncells], gY0 [N, ncells], g_lnA [M] (summed over
+    cells), status, nsub and the checkpoint workspace (uint8 device tensor whose
+    leading doubles are [cell][step][T, Y..., h])."""
+    torch = _torch()
+    lib = _lib.load()
+    n, pT, pp, pY = _cells(mech, T0, p, Y0)
+    dev = T0.device
+    size = C.c_size_t()
+    _lib.check(lib.df_chem_adjoint_workspace_size(mech.handle, n, int(max_steps), C.byref(size)),
+               "df_chem_adjoint_workspace_size")
+    ws = torch.empty(size.value, dtype=torch.uint8, device=dev)
+    out = {
+        "gT0": torch.empty(n, dtype=torch.float64, device=dev),
+        "gY0": torch.empty((mech.n_species, n), dtype=torch.float64, device=dev),
+        "g_lnA": torch.empty(mech.n_reactions, dtype=torch.float64, device=dev),
+        "status": torch.empty(n, dtype=torch.int32, device=dev),
+        "nsub": torch.empty(n, dtype=torch.int32, device=dev),
+        "workspace": ws,
+    }
+
+    def opt(t, name, numel):
+        if t is None:
+            return None
+        t = t.contiguous()
+        out["_keep_" + name] = t
+        return _dptr(t, name, torch.float64, numel)
+
+    o = C.byref(opts) if opts is not None else None
+    _lib.check(lib.df_chem_adjoint(mech.handle, n, pT, pp, pY, float(dt), o, int(max_steps),
+                                   opt(gT1, "gT1", n), opt(gY1, "gY1", mech.n_species * n),
+                                   opt(gQ1, "gQ1", n), _dptr(out["gT0"], "gT0"), _dptr(out["gY0"], "gY0"),
+                                   _dptr(out["g_lnA"], "g_lnA"), _dptr(out["status"], "status"),
+                                   _dptr(out["nsub"], "nsub"), _dptr(ws, "workspace"), size.value,
+                                   _stream_ptr(stream)), "df_chem_adjoint")
+    for k in [k for k in out if k.startswith("_keep_")]:
+        del out[k]
+    return out
+
+
+def _make_chem_step():
+    torch = _torch()
+
+    class ChemStep(torch.autograd.Function):
+        """(T0, p, Y0, lnA) -> (T(dt), Y(dt), qdot(dt)); backward by the discrete adjoint."""
+
+        @staticmethod
+        def forward(ctx, T0, p, Y0, lnA, mech, dt, opts, max_steps):
+            mech.set_lnA(lnA.detach().contiguous())
+            T = T0.detach().clone()
+            Y = Y0.detach().clone()
+            status, _ = integrate(mech, T, p, Y, dt, opts)
+            _, qdot = rhs(mech, T, p, Y)
+            ctx.save_for_backward(T0.detach(), p, Y0.detach(), lnA.detach())
+            ctx.mech, ctx.dt, ctx.opts, ctx.max_steps = mech, dt, opts, max_steps
+            ctx.mark_non_differentiable(status)
+            return T, Y, qdot, status
+
+        @staticmethod
+        def backward(ctx, gT, gY, gQ, _gs):
+            T0, p, Y0, lnA = ctx.saved_tensors
+            ctx.mech.set_lnA(lnA.contiguous())
+            r = adjoint(ctx.mech, T0, p, Y0, ctx.dt, gT, gY, gQ, ctx.opts, ctx.max_steps)
+            return r["gT0"], None, r["gY0"], r["g_lnA"], None, None, None, None
+
+    return ChemStep
+
+
+_chem_step = None
+
+
+def chem_step(mech: Mechanism, T0, p, Y0, lnA, dt: float, opts: IntegOpts | None = None,
+              max_steps: int = 64):
+    """Differentiable chemistry substep: returns (T, Y, qdot, status).  Gradients
+    flow to T0, Y0 and lnA (the natural logs of the pre-exponential factors)."""
+    global _chem_step
+    if _chem_step is None:
+        _chem_step = _make_chem_step()
+    return _chem_step.apply(T0, p, Y0, lnA, mech, dt, opts, max_steps)

@@ -22,7 +22,7 @@ class IntegOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
                 ("h0", C.c_double), ("h_min", C.c_double), ("max_substeps", C.c_int32),
                 ("method", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("order_by_T", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("order_by_T", C.c_int32), ("path", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class DFError(RuntimeError):
@@ -45,9 +45,13 @@ SIGNATURES = [
     ("df_chem_jacobian", _i, [_p, _i64, _p, _p, _p, _p, _p]),
     ("df_chem_integrate", _i, [_p, _i64, _p, _p, _p, _d, _p, _p, _p, _p]),
     ("df_chem_last_stats", _i, [_p, _p, _p, _p]),
+    ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),
+    ("df_chem_adjoint", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
+                             _p, _sz, _p]),
     ("df_strerror", C.c_char_p, [_i]),
     ("df_get_last_error_detail", _i, [C.c_char_p, _sz]),
     ("df_probe_fp64_peak", _i, [_i, _p, _p]),
+    ("df_probe_exp", _i, [_p, _p, C.c_longlong, _p]),
 ]
 
 

@@ -1,0 +1,390 @@
+// Discrete adjoint of the RODAS4 chemistry substep (one cell per thread).
+//
+// Target: the gradient of
+//   L = sum_c [ gT1_c T_c(dt) + sum_k gY1_kc Y_kc(dt) + gQ1_c qdot_c(dt) ]
+// with respect to every cell's initial state (T, Y) and to ln A_j of every
+// reaction, for the DISCRETE map the integrator computes, with its accepted
+// step sequence h_0..h_{S-1} held fixed (the usual discrete-adjoint
+// convention; Sandu et al., "Discrete adjoints of Rosenbrock methods").  The
+// paper has no adjoint; this is the sensitivity / calibration extension of the
+// chemistry substep of Sec. 2.3.
+//
+// Per accepted step, in reverse: recompute the stages K_s and the LU of
+// W = I/(h gamma) - J(y) from the checkpoint (y_i, h_i), then with
+// Kbar_s = m_s lambda (+ later-stage terms):
+//   Rbar_s = W^{-T} Kbar_s
+//   Kbar_j += (c_sj / h) Rbar_s                           (j < s)
+//   Ybar_s = J(Y_s)^T Rbar_s,  lambda += Ybar_s,  Kbar_j += a_sj Ybar_s
+//   thbar  += (df/dlnA)(Y_s)^T Rbar_s
+//   lambda += d/de [J(y + e K_s)^T Rbar_s]               (W depends on y)
+//   thbar  += d/de [(df/dlnA)(y + e K_s)^T Rbar_s]
+// The directional derivatives come from forward-mode dual numbers through the
+// same rate and Jacobian code as the integrator (exact, no differencing).
+// qdot's gradient at the final state: n dual evaluations of the right-hand side.
+//
+// Cells are assigned statically (cell = global thread index) and the per-cell
+// ln A gradients are summed over threads in a fixed order, then over blocks by a
+// second kernel in a fixed order: the result is bitwise reproducible.
+#include <algorithm>
+
+#include "rosenbrock.cuh"
+
+namespace df {
+
+static __constant__ RosTab c_tab_adj;
+static bool g_adj_ready[64] = {false};
+
+struct AdjArgs {
+  const double* blob;
+  MechDims d;
+  int64_t ncells;
+  const double* T0;
+  const double* p;
+  const double* Y0;
+  double dt;
+  double rtol, atolY, atolT, h0, hmin;
+  int max_sub;
+  int cap;  // checkpoints per cell
+  const double* gT1;
+  const double* gY1;
+  const double* gQ1;
+  double* gT0;
+  double* gY0;
+  int32_t* status;
+  int32_t* nsub;
+  double* ckpt;     // [ncells][cap][n + 1]: y_i then h_i
+  double* partial;  // [gridDim.x][M]
+  int stage_blob;
+};
+
+template <int NS>
+__host__ __device__ constexpr int adj_ws_doubles(int M) {
+  // Dual C, wdot, gRT, hRT, cpR (10 NS) + Dual J (2 n^2) + W (n^2) + K, Kbar (12 n)
+  // + theta (M) + u, ud (2 NS) + v (n)
+  return 12 * NS + 3 * (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
+  constexpr int n = NS + 1;
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, stride = blockDim.x;
+  double2* etab = reinterpret_cast<double2*>(smem);
+  for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
+  int boff = 128;
+  const double* blob = a.blob;
+  if (a.stage_blob) {
+    for (int i = tid; i < a.d.total; i += stride) smem[boff + i] = a.blob[i];
+    blob = smem + boff;
+    boff += (a.d.total + 1) & ~1;
+  }
+  __syncthreads();
+  const MechView mv = make_view(blob, a.d, etab);
+  const int M = a.d.M;
+  double* base = smem + boff;
+  // Dual vectors (value part at even offsets)
+  Dual* dbase = reinterpret_cast<Dual*>(base) + tid;
+  SVT<Dual> dC{dbase, stride}, dW{dbase + NS * stride, stride}, dG{dbase + 2 * NS * stride, stride},
+      dH{dbase + 3 * NS * stride, stride}, dCp{dbase + 4 * NS * stride, stride},
+      dJ{dbase + 5 * NS * stride, stride};
+  // double views of the same storage
+  double* vb = base + 2 * tid;
+  SV C{vb, 2 * stride}, wd{vb + 2 * NS * stride, 2 * stride}, gRT{vb + 4 * NS * stride, 2 * stride},
+      hRT{vb + 6 * NS * stride, 2 * stride}, cpR{vb + 8 * NS * stride, 2 * stride},
+      Jv{vb + 10 * NS * stride, 2 * stride};
+  double* rest = base + (10 * NS + 2 * n * n) * stride + tid;
+  SV Wv{rest, stride};
+  SV Kv{rest + n * n * stride, stride};
+  SV Kb{rest + (n * n + 6 * n) * stride, stride};
+  SV th{rest + (n * n + 12 * n) * stride, stride};
+  SV uu{rest + (n * n + 12 * n + M) * stride, stride};
+  SV ud{rest + (n * n + 12 * n + M + NS) * stride, stride};
+  SV vv{rest + (n * n + 12 * n + M + 2 * NS) * stride, stride};
+  const RosTab& tb = c_tab_adj;
+  for (int j = 0; j < M; ++j) th[j] = 0.0;
+
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + tid;
+  if (cell < a.ncells) {
+    double y[n];
+    y[0] = a.T0[cell];
+    bool ok = isfinite(y[0]) && y[0] > 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      y[1 + k] = a.Y0[(int64_t)k * a.ncells + cell];
+      ok = ok && isfinite(y[1 + k]);
+    }
+    const double pc = 10.0 * a.p[cell];
+    ok = ok && isfinite(pc) && pc > 0.0;
+    int status = ok ? DF_CELL_OK : DF_CELL_NONFINITE;
+    double* ck = a.ckpt + cell * (int64_t)a.cap * (n + 1);
+    // ---- forward with checkpoints --------------------------------------
+    double t = 0.0, h = fmin(a.h0, a.dt);
+    int nacc = 0, nrej = 0;
+    bool last_rej = false, done = !ok || !(a.dt > 0.0);
+    while (!done) {
+      bool last = false;
+      if (t + h >= a.dt) {
+        h = a.dt - t;
+        last = true;
+      }
+      double yold[n], ynew[n], en;
+#pragma unroll
+      for (int i = 0; i < n; ++i) yold[i] = y[i];
+      const double hstep = h;
+      const bool sok =
+          ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew, en);
+      const int before = nacc;
+      step_control(tb, sok, en, last, a.dt, y, ynew, t, h, nacc, nrej, last_rej, done);
+      if (nacc > before) {
+        if (nacc > a.cap) {
+          status = DF_CELL_MAXSTEPS;
+          done = true;
+        } else {
+          double* slot = ck + (int64_t)(nacc - 1) * (n + 1);
+#pragma unroll
+          for (int i = 0; i < n; ++i) slot[i] = yold[i];
+          slot[n] = hstep;
+        }
+      }
+      if (!done) {
+        if (nacc + nrej >= a.max_sub) {
+          status = DF_CELL_MAXSTEPS;
+          done = true;
+        } else if (h < a.hmin) {
+          status = DF_CELL_HMIN;
+          done = true;
+        }
+      }
+    }
+    double lam[n];
+    if (status == DF_CELL_OK) {
+      // ---- cotangent at the final state --------------------------------
+      lam[0] = a.gT1 ? a.gT1[cell] : 0.0;
+#pragma unroll
+      for (int k = 0; k < NS; ++k) lam[1 + k] = a.gY1 ? a.gY1[(int64_t)k * a.ncells + cell] : 0.0;
+      const double gq = a.gQ1 ? a.gQ1[cell] : 0.0;
+      if (gq != 0.0) {
+        for (int kk = 0; kk < n; ++kk) {
+          Dual yd[n], fd[n];
+#pragma unroll
+          for (int i = 0; i < n; ++i) yd[i] = Dual(y[i], i == kk ? 1.0 : 0.0);
+          const Dual q = eval_thread<NS, false, Dual>(mv, pc, yd, fd, dC, dW, dG, dH, dCp, dJ);
+#pragma unroll
+          for (int i = 0; i < n; ++i)
+            if (i == kk) lam[i] += gq * 0.1 * q.d;
+        }
+        ThetaHook hk{2, vv, gq, th, uu, ud};
+        double fq[n];
+        eval_thread<NS, false, double>(mv, pc, y, fq, C, wd, gRT, hRT, cpR, Jv, &hk);
+      }
+      // ---- reverse sweep over the accepted steps -----------------------
+      for (int istep = nacc - 1; istep >= 0; --istep) {
+        const double* slot = ck + (int64_t)istep * (n + 1);
+        double yi[n], ynew[n], en;
+#pragma unroll
+        for (int i = 0; i < n; ++i) yi[i] = slot[i];
+        const double hs = slot[n];
+        int piv[n];
+        ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
+                        en, piv);
+        const double ih = 1.0 / hs;
+        double yb[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) yb[i] = lam[i];
+        for (int s = 0; s < tb.s; ++s)
+#pragma unroll
+          for (int i = 0; i < n; ++i) Kb[s * n + i] = tb.m[s] * lam[i];
+        for (int s = tb.s - 1; s >= 0; --s) {
+          // Rbar = W^{-T} Kbar_s  (W = P^T L U: U^T w = b, L^T z = w, x = P^T z)
+          double r[n];
+#pragma unroll
+          for (int i = 0; i < n; ++i) r[i] = Kb[s * n + i];
+#pragma unroll
+          for (int k = 0; k < n; ++k) {
+            double acc = r[k];
+#pragma unroll
+            for (int j = 0; j < k; ++j) acc -= Wv[j * n + k] * r[j];
+            r[k] = acc * Wv[k * n + k];
+          }
+#pragma unroll
+          for (int k = n - 1; k >= 0; --k) {
+            double acc = r[k];
+#pragma unroll
+            for (int j = k + 1; j < n; ++j) acc -= Wv[j * n + k] * r[j];
+            r[k] = acc;
+          }
+#pragma unroll
+          for (int k = n - 1; k >= 0; --k) {
+            const int pk = piv[k];
+#pragma unroll
+            for (int i = k + 1; i < n; ++i)
+              if (i == pk) {
+                const double tmp = r[k];
+                r[k] = r[i];
+                r[i] = tmp;
+              }
+          }
+          for (int j = 0; j < s; ++j)
+#pragma unroll
+            for (int i = 0; i < n; ++i) Kb[j * n + i] += (tb.c[s][j] * ih) * r[i];
+#pragma unroll
+          for (int i = 0; i < n; ++i) vv[i] = r[i];
+          // F_s = f(Y_s): Ybar_s = J(Y_s)^T Rbar, theta += (df/dlnA)(Y_s)^T Rbar
+          double ysg[n], fs[n];
+#pragma unroll
+          for (int i = 0; i < n; ++i) {
+            double acc = yi[i];
+            for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
+            ysg[i] = acc;
+          }
+          {
+            ThetaHook hk{1, vv, 0.0, th, uu, ud};
+            eval_thread<NS, true, double>(mv, pc, ysg, fs, C, wd, gRT, hRT, cpR, Jv, &hk);
+          }
+#pragma unroll
+          for (int jc = 0; jc < n; ++jc) {
+            double acc = 0.0;
+#pragma unroll
+            for (int i = 0; i < n; ++i) acc += Jv[i * n + jc] * r[i];
+            yb[jc] += acc;
+            for (int j = 0; j < s; ++j) Kb[j * n + jc] += tb.a[s][j] * acc;
+          }
+          // W depends on y through J(y): d/de [J(y + e K_s)^T Rbar] and the ln A analogue
+          {
+            Dual yd[n], fd[n];
+#pragma unroll
+            for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kv[s * n + i]);
+            ThetaHook hk{1, vv, 0.0, th, uu, ud};
+            eval_thread<NS, true, Dual>(mv, pc, yd, fd, dC, dW, dG, dH, dCp, dJ, &hk);
+#pragma unroll
+            for (int jc = 0; jc < n; ++jc) {
+              double acc = 0.0;
+#pragma unroll
+              for (int i = 0; i < n; ++i) acc += dJ[i * n + jc].d * r[i];
+              yb[jc] += acc;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < n; ++i) lam[i] = yb[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < n; ++i) lam[i] = 0.0;
+      for (int j = 0; j < M; ++j) th[j] = 0.0;
+    }
+    if (a.gT0) a.gT0[cell] = lam[0];
+    if (a.gY0) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) a.gY0[(int64_t)k * a.ncells + cell] = lam[1 + k];
+    }
+    a.status[cell] = status;
+    if (a.nsub) a.nsub[cell] = nacc;
+  }
+  // fixed-order sum of the per-thread ln A gradients of this block
+  __syncthreads();
+  if (a.partial) {
+    for (int j = tid; j < M; j += stride) {
+      double acc = 0.0;
+      for (int q = 0; q < stride; ++q) acc += base[(size_t)(10 * NS + 2 * n * n + n * n + 12 * n + j) * stride + q];
+      a.partial[(int64_t)blockIdx.x * M + j] = acc;
+    }
+  }
+}
+
+__global__ void k_adjoint_reduce(const double* partial, int64_t nblocks, int M, double* g) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  double acc = 0.0;
+  for (int64_t b = 0; b < nblocks; ++b) acc += partial[b * M + j];
+  g[j] = acc;
+}
+
+static int ensure_adj_table(int dev) {
+  if (dev < 0 || dev >= 64) return DF_OK;
+  if (g_adj_ready[dev]) return DF_OK;
+  RosTab t = make_rodas4();
+  int rc = cuda_check(cudaMemcpyToSymbol(c_tab_adj, &t, sizeof(t)), "upload RODAS4 table");
+  if (!rc) g_adj_ready[dev] = true;
+  return rc;
+}
+
+static constexpr int ADJ_THREADS = 32;
+
+size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap) {
+  const int n = m->dims.N + 1;
+  const int64_t blocks = (ncells + ADJ_THREADS - 1) / ADJ_THREADS;
+  return sizeof(double) * ((size_t)ncells * cap * (n + 1) + (size_t)blocks * m->dims.M) + 256;
+}
+
+template <int NS>
+static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
+  const int threads = ADJ_THREADS;
+  size_t sm = sizeof(double) * (128 + ((m->dims.total + 1) & ~1) + (size_t)adj_ws_doubles<NS>(m->dims.M) * threads);
+  a.stage_blob = 1;
+  if (sm > m->max_smem_optin) {
+    a.stage_blob = 0;
+    sm = sizeof(double) * (128 + (size_t)adj_ws_doubles<NS>(m->dims.M) * threads);
+  }
+  if (sm > m->max_smem_optin) return set_error(DF_EUNSUPPORTED, "adjoint workspace exceeds shared memory");
+  auto kf = k_adjoint_thread<NS>;
+  int rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                      "set adjoint shared memory");
+  if (rc) return rc;
+  const int64_t blocks = (a.ncells + threads - 1) / threads;
+  kf<<<(unsigned)blocks, threads, sm, st>>>(a);
+  rc = cuda_check(cudaGetLastError(), "adjoint kernel launch");
+  if (rc) return rc;
+  if (g_lnA && m->dims.M > 0) {
+    k_adjoint_reduce<<<(m->dims.M + 127) / 128, 128, 0, st>>>(a.partial, blocks, m->dims.M, g_lnA);
+    rc = cuda_check(cudaGetLastError(), "adjoint reduction launch");
+  }
+  return rc;
+}
+
+int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
+                   double dt, const df_integ_opts& o, int cap, const double* gT1, const double* gY1,
+                   const double* gQ1, double* gT0, double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
+                   void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (o.method != 0) return set_error(DF_EUNSUPPORTED, "the adjoint is built for RODAS4 (method 0)");
+  const size_t need = adjoint_workspace_bytes(m, ncells, cap);
+  if (!ws || ws_bytes < need) return set_error(DF_EWORKSPACE, "adjoint workspace too small");
+  int rc = ensure_adj_table(m->device);
+  if (rc) return rc;
+  const int n = m->dims.N + 1;
+  AdjArgs a;
+  memset(&a, 0, sizeof(a));
+  a.blob = m->blob_dev;
+  a.d = m->dims;
+  a.ncells = ncells;
+  a.T0 = T0;
+  a.p = p;
+  a.Y0 = Y0;
+  a.dt = dt;
+  a.rtol = o.rtol;
+  a.atolY = o.atol_Y;
+  a.atolT = o.atol_T;
+  a.h0 = o.h0;
+  a.hmin = o.h_min;
+  a.max_sub = o.max_substeps;
+  a.cap = cap;
+  a.gT1 = gT1;
+  a.gY1 = gY1;
+  a.gQ1 = gQ1;
+  a.gT0 = gT0;
+  a.gY0 = gY0;
+  a.status = status;
+  a.nsub = nsub;
+  a.ckpt = static_cast<double*>(ws);
+  a.partial = static_cast<double*>(ws) + (size_t)ncells * cap * (n + 1);
+  switch (m->dims.N) {
+    case 3:
+      return adjoint_dispatch<3>(m, a, st, g_lnA);
+    case 9:
+      return adjoint_dispatch<9>(m, a, st, g_lnA);
+    default:
+      return set_error(DF_EUNSUPPORTED, "the adjoint is built for 3- and 9-species mechanisms");
+  }
+}
+
+}  // namespace df

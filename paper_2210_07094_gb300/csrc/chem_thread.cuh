@@ -18,26 +18,32 @@
 //                                           Sec. 2.2 df0DFoam; h conserved)
 #pragma once
 #include "common.cuh"
+#include "fastexp.cuh"
+#include "dual.cuh"
 
 namespace df {
 
-// strided view of a per-thread vector in shared memory
-struct SV {
-  double* p;
+// strided view of a per-thread vector (any scalar type) in shared memory
+template <class S>
+struct SVT {
+  S* p;
   int s;
-  __device__ __forceinline__ double& operator[](int i) const { return p[i * s]; }
+  __device__ __forceinline__ S& operator[](int i) const { return p[i * s]; }
 };
+typedef SVT<double> SV;
 
 struct MechView {
   const double* sp;
   const double* rx;
   const double* tr;
   const double* eff;
+  const double2* etab;  // 2^(j/64) table of exp_tang (shared memory)
   int M;
 };
 
-__device__ __forceinline__ MechView make_view(const double* blob, const MechDims& d) {
+__device__ __forceinline__ MechView make_view(const double* blob, const MechDims& d, const double2* etab) {
   MechView v;
+  v.etab = etab;
   v.sp = blob + d.off_sp;
   v.rx = blob + d.off_rx;
   v.tr = blob + d.off_tr;
@@ -59,143 +65,235 @@ __device__ __forceinline__ RxSlots load_slots(const double* r) {
   return s;
 }
 
+// Rate of one reaction (Sec. 2.3 eq. (sourceeq) bracket, with the Arrhenius
+// K_f, K_r = K_f/K_c, third-body [M] and Troe falloff) at temperature T and
+// concentrations C.  S is the scalar type (double, or Dual for directional
+// derivatives); Vec is any indexable vector of S.  NS > 0 fixes the species
+// count at compile time; otherwise Nrt is used.  With WITH_J it also returns
+// the pieces of dq/dT|_C and dq/dC.
+template <class S>
+struct RateOutT {
+  bool active;
+  RxMeta mt;
+  RxSlots sl;
+  S q;       // net rate [mol/cm^3/s]
+  S fk, rk;  // effective forward / reverse coefficients (x [M] for third body)
+  S dqdT;    // dq/dT at fixed C
+  S dqdM;    // dq/d[M] (third body, Troe); multiplies eps_l for dq/dC_l
+  S cr[3], cp[3];
+};
+typedef RateOutT<double> RateOut;
+
+template <int NS, bool WITH_J, class S, class Vec>
+__device__ __forceinline__ void rate_one(const MechView& mv, const double* r, int Nrt, S T, S lnT, S invT,
+                                         S lnP0RT, const Vec& C, const Vec& gRT, const Vec& hRT,
+                                         RateOutT<S>& o) {
+  const int N = NS > 0 ? NS : Nrt;
+  o.active = false;
+  const double lnA = r[0];
+  if (lnA == -INFINITY) return;  // A = 0: no rate
+  const double beta = r[1], EaR = r[2];
+  const RxMeta mt = load_meta(r);
+  o.mt = mt;
+  const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
+  const int type = mt.flags & 3;
+  const bool rev = (mt.flags & 4) != 0;
+  const S lnkf = lnA + beta * lnT - EaR * invT;
+  const S one(1.0);
+  const S cr0 = C[mt.reac[0]];
+  const S cr1 = nr > 1 ? S(C[mt.reac[1]]) : one;
+  const S cr2 = nr > 2 ? S(C[mt.reac[2]]) : one;
+  const S cp0 = C[mt.prod[0]];
+  const S cp1 = np > 1 ? S(C[mt.prod[1]]) : one;
+  const S cp2 = np > 2 ? S(C[mt.prod[2]]) : one;
+  o.cr[0] = cr0; o.cr[1] = cr1; o.cr[2] = cr2;
+  o.cp[0] = cp0; o.cp[1] = cp1; o.cp[2] = cp2;
+  const S Pf = cr0 * cr1 * cr2;
+  const S Pb = cp0 * cp1 * cp2;
+  // sum_k nu_kj g_k/RT and sum_k nu_kj h_k/RT (products minus reactants)
+  S sg = gRT[mt.prod[0]] - gRT[mt.reac[0]];
+  S sh(0.0);
+  if (WITH_J) sh = hRT[mt.prod[0]] - hRT[mt.reac[0]];
+  if (np > 1) { sg += gRT[mt.prod[1]]; if (WITH_J) sh += hRT[mt.prod[1]]; }
+  if (np > 2) { sg += gRT[mt.prod[2]]; if (WITH_J) sh += hRT[mt.prod[2]]; }
+  if (nr > 1) { sg -= gRT[mt.reac[1]]; if (WITH_J) sh -= hRT[mt.reac[1]]; }
+  if (nr > 2) { sg -= gRT[mt.reac[2]]; if (WITH_J) sh -= hRT[mt.reac[2]]; }
+  const int dnu = np - nr;
+  const S lnKcinv = sg - (double)dnu * lnP0RT;  // ln(1/K_c)
+  S kf, kr, mult(1.0), dqdM(0.0), dlnk(0.0);
+  const RxSlots sl = load_slots(r);
+  o.sl = sl;
+  if (type == 2) {
+    const double* tr = mv.tr + TR_REC * sl.troe;
+    const double* ef = mv.eff + N * sl.eff;
+    S Mc(0.0);
+#pragma unroll
+    for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
+    const S kinf = exp_tang(lnkf, mv.etab);
+    const S lnk0 = lnA + tr[0] + tr[1] * lnT - tr[2] * invT;
+    const S k0 = exp_tang(lnk0, mv.etab);
+    const S Pr = k0 * Mc / kinf;
+    if (!(val(Pr) > 0.0)) return;  // no low-pressure rate or no collider: k = 0
+    const S e3 = exp_tang(-T * tr[4], mv.etab);
+    const S e1 = exp_tang(-T * tr[5], mv.etab);
+    const S e2 = exp_tang(-tr[6] * invT, mv.etab);
+    const S Fc = (1.0 - tr[3]) * e3 + tr[3] * e1 + e2;
+    const S Lc = log10(Fc);
+    const S cc = -0.4 - 0.67 * Lc;
+    const S nn = 0.75 - 1.27 * Lc;
+    const S L = log10(Pr);
+    const S x = L + cc;
+    const S den = nn - 0.14 * x;
+    const S f1 = x / den;
+    const S q1 = 1.0 / (1.0 + f1 * f1);
+    const S log10F = Lc * q1;
+    const S F = exp_tang(LN10 * log10F, mv.etab);
+    const S onePr = 1.0 / (1.0 + Pr);
+    kf = kinf * Pr * onePr * F;
+    const S invKc = rev ? exp_tang(lnKcinv, mv.etab) : S(0.0);
+    kr = kf * invKc;
+    if (WITH_J) {
+      const S df1_dL = nn / (den * den);
+      const S df1_dLc = (-0.67 * den - x * (-1.27 + 0.67 * 0.14)) / (den * den);
+      const S dlogF_dL = -2.0 * Lc * f1 * df1_dL * q1 * q1;
+      const S dlogF_dLc = q1 - 2.0 * Lc * f1 * df1_dLc * q1 * q1;
+      const S g = onePr + dlogF_dL;  // d ln k / d ln Pr
+      const S dlnkinf = (beta + EaR * invT) * invT;
+      const S dlnk0 = (tr[1] + tr[2] * invT) * invT;
+      const S dFc = -(1.0 - tr[3]) * tr[4] * e3 - tr[3] * tr[5] * e1 + tr[6] * invT * invT * e2;
+      dlnk = dlnkinf + g * (dlnk0 - dlnkinf) + dlogF_dLc * dFc / Fc;
+      // dk/d[M] = k0 F g / (1 + Pr); rate per unit k is (Pf - Pb/K_c)
+      dqdM = k0 * F * g * onePr * (Pf - Pb * invKc);
+    }
+  } else {
+    kf = exp_tang(lnkf, mv.etab);
+    kr = rev ? exp_tang(lnkf + lnKcinv, mv.etab) : S(0.0);
+    if (type == 1) {
+      const double* ef = mv.eff + N * sl.eff;
+      S Mc(0.0);
+#pragma unroll
+      for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
+      mult = Mc;
+      dqdM = kf * Pf - kr * Pb;
+    }
+    if (WITH_J) dlnk = (beta + EaR * invT) * invT;
+  }
+  o.active = true;
+  o.q = mult * (kf * Pf - kr * Pb);
+  o.fk = mult * kf;
+  o.rk = mult * kr;
+  o.dqdM = dqdM;
+  if (WITH_J) {
+    const S dlnKc = (sh - (double)dnu) * invT;
+    o.dqdT = mult * (kf * Pf * dlnk - kr * Pb * (dlnk - dlnKc));
+  } else {
+    o.dqdT = S(0.0);
+  }
+}
+
+// Optional accumulation of d/d ln A_j of a weighted sum of the right-hand side
+// (the discrete adjoint's parameter gradient).  Mode 1: weights v (adjoint
+// vector of dy/dt), i.e. th[j] += v . d f / d ln A_j = q_j sum_k nu_kj u_k with
+// u_k = (W_k v_{Y_k} - v_T H_k / cp) / rho.  Mode 2: heat release, th[j] +=
+// g * d qdot / d ln A_j with qdot = -0.1 sum_k H_k wdot_k [W/m^3].  With a Dual
+// scalar only the derivative part is accumulated.
+struct ThetaHook {
+  int mode;   // 0: off
+  SV v;       // mode 1: adjoint vector (n entries)
+  double g;   // mode 2: weight
+  SV th;      // per-thread accumulator, M entries
+  SV u;       // per-thread scratch, N entries (value parts)
+  SV ud;      // per-thread scratch, N entries (derivative parts, Dual only)
+};
+
+__device__ __forceinline__ void th_add(const ThetaHook& h, int j, double x) { h.th[j] += x; }
+__device__ __forceinline__ void th_add(const ThetaHook& h, int j, const Dual& x) { h.th[j] += x.d; }
+__device__ __forceinline__ void u_store(const ThetaHook& h, int k, double x) { h.u[k] = x; }
+__device__ __forceinline__ void u_store(const ThetaHook& h, int k, const Dual& x) { h.u[k] = x.v; h.ud[k] = x.d; }
+__device__ __forceinline__ double u_load(const ThetaHook& h, int k, double) { return h.u[k]; }
+__device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) { return Dual(h.u[k], h.ud[k]); }
+
 // Evaluate f = dy/dt for y = (T, Y) and, when WITH_J, the analytic Jacobian
 // J = df/dy (row-major in the strided view Jv, n x n with n = NS + 1).
 // Returns qdot = -sum_k H_k wdot_k in erg/(cm^3 s).
-template <int NS, bool WITH_J>
-__device__ __forceinline__ double eval_thread(const MechView& mv, const double pc, const double (&y)[NS + 1],
-                                              double (&f)[NS + 1], SV C, SV wdot, SV gRT, SV hRT, SV cpR,
-                                              SV Jv) {
+template <int NS, bool WITH_J, class S = double>
+__device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, const S (&y)[NS + 1], S (&f)[NS + 1],
+                                         SVT<S> C, SVT<S> wdot, SVT<S> gRT, SVT<S> hRT, SVT<S> cpR, SVT<S> Jv,
+                                         const ThetaHook* hook = nullptr) {
   constexpr int n = NS + 1;
-  const double T = y[0];
-  const double lnT = log(T);
-  const double invT = 1.0 / T;
-  double sumYW = 0.0;
+  const S T = y[0];
+  const S lnT = log(T);
+  const S invT = 1.0 / T;
+  S sumYW(0.0), cpm(0.0);
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const double* a = mv.sp + SP_REC * k + 2;
-    cpR[k] = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-    const double hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
-                      a[5] * invT;
-    const double sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    const S cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    cpR[k] = cpk;
+    const S hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
+                 a[5] * invT;
+    const S sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
     hRT[k] = hk;
     gRT[k] = hk - sk;
     sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];
+    cpm += y[1 + k] * cpk * mv.sp[SP_REC * k + 1];
   }
-  const double rho = pc * invT / (RU * sumYW);
+  cpm = cpm * RU;
+  const S rho = pc * invT / (RU * sumYW);
+  const S invrho = 1.0 / rho;
+  const S invcp = 1.0 / cpm;
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
-    wdot[k] = 0.0;
+    wdot[k] = S(0.0);
+  }
+  if (hook && hook->mode) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const S Hk = RU * T * hRT[k];
+      S uk;
+      if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * hook->v[1 + k] - hook->v[0] * Hk * invcp) * invrho;
+      else uk = -0.1 * hook->g * Hk;
+      u_store(*hook, k, uk);
+    }
   }
   if (WITH_J) {
 #pragma unroll
-    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;
+    for (int i = 0; i < n * n; ++i) Jv[i] = S(0.0);
   }
-  const double lnP0RT = LOG_PSTD_RU - lnT;
+  const S lnP0RT = LOG_PSTD_RU - lnT;
   for (int j = 0; j < mv.M; ++j) {
-    const double* r = mv.rx + RX_REC * j;
-    const double lnA = r[0];
-    if (lnA == -INFINITY) continue;  // A = 0: no rate
-    const double beta = r[1], EaR = r[2];
-    const RxMeta mt = load_meta(r);
+    RateOutT<S> ro;
+    rate_one<NS, WITH_J>(mv, mv.rx + RX_REC * j, NS, T, lnT, invT, lnP0RT, C, gRT, hRT, ro);
+    if (!ro.active) continue;
+    const RxMeta mt = ro.mt;
     const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
-    const int type = mt.flags & 3;
-    const bool rev = (mt.flags & 4) != 0;
-    const double lnkf = lnA + beta * lnT - EaR * invT;
-    // concentration products
-    const double cr0 = C[mt.reac[0]];
-    const double cr1 = nr > 1 ? C[mt.reac[1]] : 1.0;
-    const double cr2 = nr > 2 ? C[mt.reac[2]] : 1.0;
-    const double cp0 = C[mt.prod[0]];
-    const double cp1 = np > 1 ? C[mt.prod[1]] : 1.0;
-    const double cp2 = np > 2 ? C[mt.prod[2]] : 1.0;
-    const double Pf = cr0 * cr1 * cr2;
-    const double Pb = cp0 * cp1 * cp2;
-    // sum_k nu_kj g_k/RT and sum_k nu_kj h_k/RT (products minus reactants)
-    double sg = gRT[mt.prod[0]] - gRT[mt.reac[0]];
-    double sh = 0.0;
-    if (WITH_J) sh = hRT[mt.prod[0]] - hRT[mt.reac[0]];
-    if (np > 1) { sg += gRT[mt.prod[1]]; if (WITH_J) sh += hRT[mt.prod[1]]; }
-    if (np > 2) { sg += gRT[mt.prod[2]]; if (WITH_J) sh += hRT[mt.prod[2]]; }
-    if (nr > 1) { sg -= gRT[mt.reac[1]]; if (WITH_J) sh -= hRT[mt.reac[1]]; }
-    if (nr > 2) { sg -= gRT[mt.reac[2]]; if (WITH_J) sh -= hRT[mt.reac[2]]; }
-    const int dnu = np - nr;
-    const double lnKcinv = sg - dnu * lnP0RT;  // ln(1/K_c)
-    double kf, kr, mult = 1.0, dqdM = 0.0, dlnk = 0.0;
-    const RxSlots sl = load_slots(r);
-    if (type == 2) {
-      const double* tr = mv.tr + TR_REC * sl.troe;
-      const double* ef = mv.eff + NS * sl.eff;
-      double Mc = 0.0;
-#pragma unroll
-      for (int l = 0; l < NS; ++l) Mc += ef[l] * C[l];
-      const double kinf = exp(lnkf);
-      const double lnk0 = lnA + tr[0] + tr[1] * lnT - tr[2] * invT;
-      const double k0 = exp(lnk0);
-      const double Pr = k0 * Mc / kinf;
-      if (!(Pr > 0.0)) continue;  // no low-pressure rate or no collider: k = 0
-      const double e3 = exp(-T * tr[4]), e1 = exp(-T * tr[5]), e2 = exp(-tr[6] * invT);
-      const double Fc = (1.0 - tr[3]) * e3 + tr[3] * e1 + e2;
-      const double Lc = log10(Fc);
-      const double cc = -0.4 - 0.67 * Lc;
-      const double nn = 0.75 - 1.27 * Lc;
-      const double L = log10(Pr);
-      const double x = L + cc;
-      const double den = nn - 0.14 * x;
-      const double f1 = x / den;
-      const double q1 = 1.0 / (1.0 + f1 * f1);
-      const double log10F = Lc * q1;
-      const double F = exp(LN10 * log10F);
-      const double onePr = 1.0 / (1.0 + Pr);
-      kf = kinf * Pr * onePr * F;
-      kr = rev ? kf * exp(lnKcinv) : 0.0;
-      if (WITH_J) {
-        const double df1_dL = nn / (den * den);
-        const double df1_dLc = (-0.67 * den - x * (-1.27 + 0.67 * 0.14)) / (den * den);
-        const double dlogF_dL = -Lc * 2.0 * f1 * df1_dL * q1 * q1;
-        const double dlogF_dLc = q1 - Lc * 2.0 * f1 * df1_dLc * q1 * q1;
-        const double g = onePr + dlogF_dL;  // d ln k / d ln Pr
-        const double dlnkinf = (beta + EaR * invT) * invT;
-        const double dlnk0 = (tr[1] + tr[2] * invT) * invT;
-        const double dFc = -(1.0 - tr[3]) * tr[4] * e3 - tr[3] * tr[5] * e1 + tr[6] * invT * invT * e2;
-        dlnk = dlnkinf + g * (dlnk0 - dlnkinf) + dlogF_dLc * dFc / Fc;
-        // dk/d[M] = k0 F g / (1 + Pr); rate per unit k is (Pf - Pb/K_c)
-        dqdM = k0 * F * g * onePr * (Pf - (rev ? Pb * exp(lnKcinv) : 0.0));
-      }
-    } else {
-      kf = exp(lnkf);
-      kr = rev ? exp(lnkf + lnKcinv) : 0.0;
-      if (type == 1) {
-        const double* ef = mv.eff + NS * sl.eff;
-        double Mc = 0.0;
-#pragma unroll
-        for (int l = 0; l < NS; ++l) Mc += ef[l] * C[l];
-        mult = Mc;
-        dqdM = kf * Pf - kr * Pb;
-      }
-      if (WITH_J) dlnk = (beta + EaR * invT) * invT;
-    }
-    const double q = mult * (kf * Pf - kr * Pb);
+    const S q = ro.q;
     wdot[mt.reac[0]] -= q;
     if (nr > 1) wdot[mt.reac[1]] -= q;
     if (nr > 2) wdot[mt.reac[2]] -= q;
     wdot[mt.prod[0]] += q;
     if (np > 1) wdot[mt.prod[1]] += q;
     if (np > 2) wdot[mt.prod[2]] += q;
+    if (hook && hook->mode) {
+      S w = u_load(*hook, mt.prod[0], q) - u_load(*hook, mt.reac[0], q);
+      if (np > 1) w += u_load(*hook, mt.prod[1], q);
+      if (np > 2) w += u_load(*hook, mt.prod[2], q);
+      if (nr > 1) w -= u_load(*hook, mt.reac[1], q);
+      if (nr > 2) w -= u_load(*hook, mt.reac[2], q);
+      th_add(*hook, j, q * w);
+    }
     if (WITH_J) {
-      const double dlnKc = (sh - dnu) * invT;
-      const double dqdT = mult * (kf * Pf * dlnk - kr * Pb * (dlnk - dlnKc));
       // d q / d C of each reactant / product entry (product rule, no division)
-      const double fk = mult * kf, rk = mult * kr;
-      double dr[3], dp[3];
-      dr[0] = fk * cr1 * cr2;
-      dr[1] = fk * cr0 * cr2;
-      dr[2] = fk * cr0 * cr1;
-      dp[0] = -rk * cp1 * cp2;
-      dp[1] = -rk * cp0 * cp2;
-      dp[2] = -rk * cp0 * cp1;
-      const double* ef = (type != 0) ? mv.eff + NS * sl.eff : nullptr;
+      S dr[3], dp[3];
+      dr[0] = ro.fk * ro.cr[1] * ro.cr[2];
+      dr[1] = ro.fk * ro.cr[0] * ro.cr[2];
+      dr[2] = ro.fk * ro.cr[0] * ro.cr[1];
+      dp[0] = -(ro.rk * ro.cp[1] * ro.cp[2]);
+      dp[1] = -(ro.rk * ro.cp[0] * ro.cp[2]);
+      dp[2] = -(ro.rk * ro.cp[0] * ro.cp[1]);
+      const int type = mt.flags & 3;
+      const double* ef = (type != 0) ? mv.eff + NS * ro.sl.eff : nullptr;
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
         const bool isr = a < 3;
@@ -203,7 +301,7 @@ __device__ __forceinline__ double eval_thread(const MechView& mv, const double p
         if (ia >= (isr ? nr : np)) continue;
         const double sgn = isr ? -1.0 : 1.0;
         const int row = 1 + (isr ? mt.reac[ia] : mt.prod[ia]);
-        Jv[row * n] += sgn * dqdT;
+        Jv[row * n] += sgn * ro.dqdT;
         Jv[row * n + 1 + mt.reac[0]] += sgn * dr[0];
         if (nr > 1) Jv[row * n + 1 + mt.reac[1]] += sgn * dr[1];
         if (nr > 2) Jv[row * n + 1 + mt.reac[2]] += sgn * dr[2];
@@ -211,40 +309,34 @@ __device__ __forceinline__ double eval_thread(const MechView& mv, const double p
         if (np > 1) Jv[row * n + 1 + mt.prod[1]] += sgn * dp[1];
         if (np > 2) Jv[row * n + 1 + mt.prod[2]] += sgn * dp[2];
         if (ef) {
-          const double cM = sgn * dqdM;
+          const S cM = sgn * ro.dqdM;
 #pragma unroll
           for (int l = 0; l < NS; ++l) Jv[row * n + 1 + l] += cM * ef[l];
         }
       }
     }
   }
-  // mixture cp (mass) and heat release
-  double cpm = 0.0, Hw = 0.0;
+  // heat release
+  S Hw(0.0);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) {
-    cpm += y[1 + k] * cpR[k] * mv.sp[SP_REC * k + 1];
-    Hw += hRT[k] * wdot[k];
-  }
-  cpm *= RU;
-  Hw *= RU * T;
-  const double invrho = 1.0 / rho;
-  const double invcp = 1.0 / cpm;
+  for (int k = 0; k < NS; ++k) Hw += hRT[k] * wdot[k];
+  Hw = Hw * (RU * T);
 #pragma unroll
   for (int k = 0; k < NS; ++k) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;
-  f[0] = -Hw * invrho * invcp;
+  f[0] = -(Hw * invrho * invcp);
   if (WITH_J) {
     // species rows: concentration-space Jc[k][l] = d wdot_k / d C_l (stored in
     // Jv[1+k][1+l]) and dwdot_k/dT at fixed C (Jv[1+k][0]) -> (T, Y) space
-    const double Wbar = 1.0 / sumYW;
+    const S Wbar = 1.0 / sumYW;
 #pragma unroll 1
     for (int k = 0; k < NS; ++k) {
       const int row = (1 + k) * n;
-      double s = 0.0;
+      S s(0.0);
 #pragma unroll
       for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * C[l];
       const double Wk = mv.sp[SP_REC * k];
-      const double wk = wdot[k];
-      const double a = Wk * Wbar * invrho * (wk - s);
+      const S wk = wdot[k];
+      const S a = Wk * Wbar * invrho * (wk - s);
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
         const double iWi = mv.sp[SP_REC * i + 1];
@@ -253,7 +345,7 @@ __device__ __forceinline__ double eval_thread(const MechView& mv, const double p
       Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);
     }
     // temperature row: f_T = -sum_k h_k f_Yk / cp (h_k specific enthalpy)
-    double dcp = 0.0, cpf = 0.0;
+    S dcp(0.0), cpf(0.0);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const double* a = mv.sp + SP_REC * k + 2;
@@ -261,19 +353,20 @@ __device__ __forceinline__ double eval_thread(const MechView& mv, const double p
       dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
       cpf += cpR[k] * iW * f[1 + k];
     }
-    dcp *= RU;
-    cpf *= RU;
+    dcp = dcp * RU;
+    cpf = cpf * RU;
 #pragma unroll 1
     for (int jc = 0; jc < n; ++jc) {
-      double acc = 0.0;
+      S acc(0.0);
 #pragma unroll
       for (int k = 0; k < NS; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];
-      acc *= RU * T;
+      acc = acc * (RU * T);
       if (jc == 0) {
-        Jv[0] = -invcp * (acc + cpf) - f[0] * dcp * invcp;
+        Jv[0] = -(invcp * (acc + cpf)) - f[0] * dcp * invcp;
       } else {
-        const double cpj = RU * cpR[jc - 1] * mv.sp[SP_REC * (jc - 1) + 1];
-        Jv[jc] = -invcp * acc - f[0] * cpj * invcp;
+        const double iWj = mv.sp[SP_REC * (jc - 1) + 1];
+        const S cpj = RU * cpR[jc - 1] * iWj;
+        Jv[jc] = -(invcp * acc) - f[0] * cpj * invcp;
       }
     }
   }

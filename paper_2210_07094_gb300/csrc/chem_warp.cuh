@@ -1,0 +1,267 @@
+// Device chemistry for the one-cell-per-warp path (any N <= 64; used for the
+// 50-species mechanism).  The 32 lanes of a warp share one cell:
+//   thermo      - lanes over species,
+//   rates       - lanes over reactions (rate_one, same math as the thread path),
+//   wdot, J     - lanes over species rows, summing their reactions from a
+//                 species -> (reaction, nu) list (fixed order: deterministic,
+//                 no atomics),
+//   LU          - pivot search by warp reduction, trailing update over columns,
+//   solves      - column-oriented substitution, one __syncwarp per step.
+// All per-cell vectors and the dense (N+1)^2 matrix live in shared memory.
+#pragma once
+#include "chem_thread.cuh"
+
+namespace df {
+
+constexpr unsigned WFULL = 0xffffffffu;
+
+// plain shared-memory vector with the same indexing interface as SV
+struct PV {
+  double* p;
+  __device__ __forceinline__ double& operator[](int i) const { return p[i]; }
+};
+
+// per-warp workspace layout (offsets in doubles)
+struct WarpWS {
+  int y, ys, f, wdot, C, gRT, hRT, cpR, q, fk, rk, dT, dM, J, K, piv, total;
+};
+
+__host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
+  const int n = N + 1;
+  WarpWS w;
+  int o = 0;
+  w.y = o; o += n;
+  w.ys = o; o += n;
+  w.f = o; o += n;
+  w.wdot = o; o += N;
+  w.C = o; o += N;
+  w.gRT = o; o += N;
+  w.hRT = o; o += N;
+  w.cpR = o; o += N;
+  w.q = o; o += M;
+  w.fk = o; o += M;
+  w.rk = o; o += M;
+  w.dT = o; o += M;
+  w.dM = o; o += M;
+  w.J = o; o += n * n;
+  w.K = o; o += 6 * n;
+  w.piv = o; o += n;  // int storage in double slots
+  w.total = (o + 1) & ~1;
+  return w;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(WFULL, v, o);
+  return v;
+}
+
+// Evaluate f(y) (and J when WITH_J) for the state at ws + yoff.
+// csr: [N+1] row pointers, then (reaction, nu) pairs.  Returns qdot in erg/(cm^3 s).
+template <bool WITH_J>
+__device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc, double* ws, const WarpWS& L,
+                            int yoff) {
+  const int lane = threadIdx.x & 31;
+  const int n = N + 1;
+  const double* y = ws + yoff;
+  double* f = ws + L.f;
+  PV C{ws + L.C}, gRT{ws + L.gRT}, hRT{ws + L.hRT};
+  double* cpR = ws + L.cpR;
+  double* wdot = ws + L.wdot;
+  const double T = y[0];
+  const double lnT = log(T);
+  const double invT = 1.0 / T;
+  // thermo and sum Y/W
+  double sYW = 0.0;
+  for (int k = lane; k < N; k += 32) {
+    const double* a = mv.sp + SP_REC * k + 2;
+    cpR[k] = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    const double hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
+                      a[5] * invT;
+    const double sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    hRT[k] = hk;
+    gRT[k] = hk - sk;
+    sYW += y[1 + k] * mv.sp[SP_REC * k + 1];
+  }
+  const double sumYW = warp_sum(sYW);
+  const double rho = pc * invT / (RU * sumYW);
+  for (int k = lane; k < N; k += 32) C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
+  __syncwarp();
+  const double lnP0RT = LOG_PSTD_RU - lnT;
+  // reactions: one lane per reaction
+  for (int j = lane; j < mv.M; j += 32) {
+    RateOut ro;
+    rate_one<0, WITH_J>(mv, mv.rx + RX_REC * j, N, T, lnT, invT, lnP0RT, C, gRT, hRT, ro);
+    if (ro.active) {
+      ws[L.q + j] = ro.q;
+      if (WITH_J) {
+        ws[L.fk + j] = ro.fk;
+        ws[L.rk + j] = ro.rk;
+        ws[L.dT + j] = ro.dqdT;
+        ws[L.dM + j] = ro.dqdM;
+      }
+    } else {
+      ws[L.q + j] = 0.0;
+      if (WITH_J) {
+        ws[L.fk + j] = 0.0;
+        ws[L.rk + j] = 0.0;
+        ws[L.dT + j] = 0.0;
+        ws[L.dM + j] = 0.0;
+      }
+    }
+  }
+  __syncwarp();
+  // species production rates, cp, heat release
+  double cpp = 0.0, hwp = 0.0;
+  for (int k = lane; k < N; k += 32) {
+    double w = 0.0;
+    for (int e = csr[k]; e < csr[k + 1]; ++e) {
+      const int j = csr[N + 1 + 2 * e];
+      const int nu = csr[N + 2 + 2 * e];
+      w += nu * ws[L.q + j];
+    }
+    wdot[k] = w;
+    cpp += y[1 + k] * cpR[k] * mv.sp[SP_REC * k + 1];
+    hwp += hRT[k] * w;
+  }
+  const double cpm = RU * warp_sum(cpp);
+  const double Hw = RU * T * warp_sum(hwp);
+  const double invrho = 1.0 / rho;
+  const double invcp = 1.0 / cpm;
+  for (int k = lane; k < N; k += 32) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;
+  const double fT = -Hw * invrho * invcp;
+  if (lane == 0) f[0] = fT;
+  if (WITH_J) {
+    double* J = ws + L.J;
+    const double Wbar = 1.0 / sumYW;
+    for (int k = lane; k < N; k += 32) {
+      double* row = J + (1 + k) * n;
+      for (int c = 0; c < n; ++c) row[c] = 0.0;
+      // concentration-space row: sum over this species' reactions
+      for (int e = csr[k]; e < csr[k + 1]; ++e) {
+        const int j = csr[N + 1 + 2 * e];
+        const double nu = (double)csr[N + 2 + 2 * e];
+        const double* r = mv.rx + RX_REC * j;
+        const RxMeta mt = load_meta(r);
+        const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
+        const double fk = ws[L.fk + j], rk = ws[L.rk + j];
+        row[0] += nu * ws[L.dT + j];
+        const double c0 = C[mt.reac[0]], c1 = nr > 1 ? C[mt.reac[1]] : 1.0, c2 = nr > 2 ? C[mt.reac[2]] : 1.0;
+        row[1 + mt.reac[0]] += nu * fk * c1 * c2;
+        if (nr > 1) row[1 + mt.reac[1]] += nu * fk * c0 * c2;
+        if (nr > 2) row[1 + mt.reac[2]] += nu * fk * c0 * c1;
+        const double d0 = C[mt.prod[0]], d1 = np > 1 ? C[mt.prod[1]] : 1.0, d2 = np > 2 ? C[mt.prod[2]] : 1.0;
+        row[1 + mt.prod[0]] -= nu * rk * d1 * d2;
+        if (np > 1) row[1 + mt.prod[1]] -= nu * rk * d0 * d2;
+        if (np > 2) row[1 + mt.prod[2]] -= nu * rk * d0 * d1;
+        if ((mt.flags & 3) != 0) {
+          const double cM = nu * ws[L.dM + j];
+          const double* ef = mv.eff + N * load_slots(r).eff;
+          for (int l = 0; l < N; ++l) row[1 + l] += cM * ef[l];
+        }
+      }
+      // -> (T, Y) space
+      double s = 0.0;
+      for (int l = 0; l < N; ++l) s += row[1 + l] * C[l];
+      const double Wk = mv.sp[SP_REC * k];
+      const double wk = wdot[k];
+      const double a = Wk * Wbar * invrho * (wk - s);
+      for (int i = 0; i < N; ++i) row[1 + i] = (Wk * row[1 + i] + a) * mv.sp[SP_REC * i + 1];
+      row[0] = Wk * invrho * (row[0] + (wk - s) * invT);
+    }
+    __syncwarp();
+    // temperature row
+    double dcp = 0.0, cpf = 0.0;
+    for (int k = lane; k < N; k += 32) {
+      const double* a = mv.sp + SP_REC * k + 2;
+      const double iW = mv.sp[SP_REC * k + 1];
+      dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
+      cpf += cpR[k] * iW * f[1 + k];
+    }
+    dcp = RU * warp_sum(dcp);
+    cpf = RU * warp_sum(cpf);
+    for (int jc = lane; jc < n; jc += 32) {
+      double acc = 0.0;
+      for (int k = 0; k < N; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * J[(1 + k) * n + jc];
+      acc *= RU * T;
+      if (jc == 0) J[0] = -invcp * (acc + cpf) - fT * dcp * invcp;
+      else J[jc] = -invcp * acc - fT * RU * cpR[jc - 1] * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
+    }
+  }
+  __syncwarp();
+  return -Hw;
+}
+
+// LU with partial pivoting of the n x n row-major matrix A (shared memory),
+// whole rows swapped, reciprocal pivots on the diagonal.  Returns false if a
+// pivot is zero or not finite.
+__device__ bool warp_lu(double* A, int* piv, int n) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const double v = fabs(A[i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(WFULL, best, o);
+      const int oi = __shfl_xor_sync(WFULL, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    ok = ok && (best > 0.0) && (best < INFINITY);
+    if (lane == 0) piv[k] = bi;
+    if (bi != k) {
+      for (int j = lane; j < n; j += 32) {
+        const double t = A[k * n + j];
+        A[k * n + j] = A[bi * n + j];
+        A[bi * n + j] = t;
+      }
+    }
+    __syncwarp();
+    const double inv = 1.0 / A[k * n + k];
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) A[i * n + k] *= inv;
+    if (lane == 0) A[k * n + k] = inv;
+    __syncwarp();
+    for (int j = k + 1 + lane; j < n; j += 32) {
+      const double ukj = A[k * n + j];
+      for (int i = k + 1; i < n; ++i) A[i * n + j] -= A[i * n + k] * ukj;
+    }
+    __syncwarp();
+  }
+  return ok;
+}
+
+// x <- A^{-1} x with the factors of warp_lu (x in shared memory)
+__device__ void warp_solve(const double* A, const int* piv, double* x, int n) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const double t = x[k];
+        x[k] = x[p];
+        x[p] = t;
+      }
+    }
+  }
+  __syncwarp();
+  for (int k = 0; k < n; ++k) {
+    const double xk = x[k];
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) x[i] -= A[i * n + k] * xk;
+    __syncwarp();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double xk = x[k] * A[k * n + k];
+    __syncwarp();
+    if (lane == 0) x[k] = xk;
+    for (int i = lane; i < k; i += 32) x[i] -= A[i * n + k] * xk;
+    __syncwarp();
+  }
+}
+
+}  // namespace df

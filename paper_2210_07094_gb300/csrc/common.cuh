@@ -79,7 +79,9 @@ struct df_mech {
   df::MechDims dims;
   std::vector<double> blob_host;  // as parsed (lnA from the file)
   std::vector<double> lnA_file;
+  std::vector<int> csr_host;      // species -> (reaction, net nu) lists: [N+1] ptr, pairs
   double* blob_dev = nullptr;     // device copy (lnA may be overridden)
+  int* csr_dev = nullptr;
   int device = 0;
   // persistent-queue and statistics scratch (device): [0] work counter,
   // [1] accepted, [2] rejected, [3] error flag
@@ -108,4 +110,11 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st);
 int launch_set_lnA(df_mech* m, const double* lnA, cudaStream_t st);
+
+// adjoint (adjoint.cu)
+size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap);
+int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
+                   double dt, const df_integ_opts& o, int cap, const double* gT1, const double* gY1,
+                   const double* gQ1, double* gT0, double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
+                   void* ws, size_t ws_bytes, cudaStream_t st);
 }  // namespace df

@@ -16,84 +16,12 @@
 #include <algorithm>
 #include <cmath>
 
-#include "chem_thread.cuh"
+#include "chem_warp.cuh"
+#include "rosenbrock.cuh"
 
 namespace df {
 
-struct RosTab {
-  int s;
-  int elo;
-  double gamma;
-  double a[6][6];
-  double c[6][6];
-  double m[6];
-  double e[6];
-  int newf[6];
-};
-
-__constant__ RosTab c_tab[2];
-
-static RosTab make_rodas4() {
-  RosTab t;
-  memset(&t, 0, sizeof(t));
-  t.s = 6;
-  t.elo = 4;
-  t.gamma = 0.25;
-  const double A[15] = {1.544, 0.9466785280815826, 0.2557011698983284, 3.314825187068521,
-                        2.896124015972201, 0.9986419139977817, 1.221224509226641, 6.019134481288629,
-                        12.53708332932087, -0.6878860361058950, 1.221224509226641, 6.019134481288629,
-                        12.53708332932087, -0.6878860361058950, 1.0};
-  const double C[15] = {-5.6688, -2.430093356833875, -0.2063599157091915, -0.1073529058151375,
-                        -9.594562251023355, -20.47028614809616, 7.496443313967647, -10.24680431464352,
-                        -33.99990352819905, 11.70890893206160, 8.083246795921522, -7.981132988064893,
-                        -31.52159432874371, 16.31930543123136, -6.058818238834054};
-  int idx = 0;
-  for (int i = 1; i < 6; ++i)
-    for (int j = 0; j < i; ++j) {
-      t.a[i][j] = A[idx];
-      t.c[i][j] = C[idx];
-      ++idx;
-    }
-  t.m[0] = A[6];
-  t.m[1] = A[7];
-  t.m[2] = A[8];
-  t.m[3] = A[9];
-  t.m[4] = 1.0;
-  t.m[5] = 1.0;
-  t.e[5] = 1.0;
-  for (int i = 0; i < 6; ++i) t.newf[i] = 1;
-  return t;
-}
-
-static RosTab make_rodas3() {
-  RosTab t;
-  memset(&t, 0, sizeof(t));
-  t.s = 4;
-  t.elo = 3;
-  t.gamma = 0.5;
-  t.a[1][0] = 0.0;
-  t.a[2][0] = 2.0;
-  t.a[2][1] = 0.0;
-  t.a[3][0] = 2.0;
-  t.a[3][1] = 0.0;
-  t.a[3][2] = 1.0;
-  t.c[1][0] = 4.0;
-  t.c[2][0] = 1.0;
-  t.c[2][1] = -1.0;
-  t.c[3][0] = 1.0;
-  t.c[3][1] = -1.0;
-  t.c[3][2] = -8.0 / 3.0;
-  t.m[0] = 2.0;
-  t.m[1] = 0.0;
-  t.m[2] = 1.0;
-  t.m[3] = 1.0;
-  t.e[3] = 1.0;
-  t.newf[0] = 1;
-  t.newf[1] = 0;  // a[1][*] = 0: stage 2 reuses f(y)
-  t.newf[2] = 1;
-  t.newf[3] = 1;
-  return t;
-}
+static __constant__ RosTab c_tab[2];
 
 static bool g_tab_ready[64] = {false};
 
@@ -141,14 +69,16 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   const int tid = threadIdx.x;
   const int stride = blockDim.x;
   const double* blob = a.blob;
-  int boff = 0;
+  double2* etab = reinterpret_cast<double2*>(smem);
+  for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
+  int boff = 128;
   if (a.stage_blob) {
-    for (int i = tid; i < a.d.total; i += stride) smem[i] = a.blob[i];
-    blob = smem;
-    boff = blob_smem_doubles(a.d);
-    __syncthreads();
+    for (int i = tid; i < a.d.total; i += stride) smem[boff + i] = a.blob[i];
+    blob = smem + boff;
+    boff += blob_smem_doubles(a.d);
   }
-  const MechView mv = make_view(blob, a.d);
+  __syncthreads();
+  const MechView mv = make_view(blob, a.d, etab);
   double* ws = smem + boff + tid;
   SV C{ws, stride};
   SV wdot{ws + NS * stride, stride};
@@ -223,72 +153,11 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
       h = a.dt - t;
       last = true;
     }
-    // f(y) and J(y); W = I/(h gamma) - J factorised in place
-    double fs[n];
-    eval_thread<NS, true>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
-    const double hgi = 1.0 / (h * tb.gamma);
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-#pragma unroll
-      for (int j = 0; j < n; ++j) Jv[i * n + j] = (i == j ? hgi : 0.0) - Jv[i * n + j];
-    }
-    int piv[n];
-    bool ok = lu_factor<n>(Jv, piv);
-    const double ih = 1.0 / h;
     double ys[n];
-    for (int s = 0; s < tb.s; ++s) {
-      if (s > 0 && tb.newf[s]) {
-#pragma unroll
-        for (int i = 0; i < n; ++i) {
-          double acc = y[i];
-          for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
-          ys[i] = acc;
-        }
-        eval_thread<NS, false>(mv, pc, ys, fs, C, wdot, gRT, hRT, cpR, Jv);
-      }
-      // stage right-hand side, solved in place in the K slot of this stage
-      SV Ks{&Kv[s * n], stride};
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        double acc = fs[i];
-        for (int j = 0; j < s; ++j) acc += (tb.c[s][j] * ih) * Kv[j * n + i];
-        Ks[i] = acc;
-      }
-      lu_solve<n>(Jv, piv, Ks);
-    }
-    // new state and weighted RMS norm of the embedded error estimate
-    double en = 0.0;
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      double yn = y[i], e = 0.0;
-      for (int s = 0; s < tb.s; ++s) {
-        const double kv = Kv[s * n + i];
-        yn += tb.m[s] * kv;
-        e += tb.e[s] * kv;
-      }
-      ys[i] = yn;
-      const double sc = (i == 0 ? a.atolT : a.atolY) + a.rtol * fmax(fabs(y[i]), fabs(yn));
-      const double r = e / sc;
-      en += r * r;
-    }
-    en = sqrt(en / n);
-    ok = ok && isfinite(en);
-    if (ok && en <= 1.0) {
-#pragma unroll
-      for (int i = 0; i < n; ++i) y[i] = ys[i];
-      t = last ? a.dt : t + h;
-      ++nacc;
-      double fac = 0.9 * pow(fmax(en, 1e-10), -1.0 / tb.elo);
-      fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
-      h *= fac;
-      last_rej = false;
-      if (t >= a.dt) done = true;
-    } else {
-      ++nrej;
-      const double fac = ok ? fmax(0.2, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
-      h *= fac;
-      last_rej = true;
-    }
+    double en;
+    const bool ok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR, Jv, Kv,
+                                    stride, ys, en);
+    step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done);
     if (!done) {
       if (nacc + nrej >= a.max_sub) {
         status = DF_CELL_MAXSTEPS;
@@ -333,14 +202,16 @@ __global__ void __launch_bounds__(128) k_eval_thread(EvalArgs a) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, stride = blockDim.x;
   const double* blob = a.blob;
-  int boff = 0;
+  double2* etab = reinterpret_cast<double2*>(smem);
+  for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
+  int boff = 128;
   if (a.stage_blob) {
-    for (int i = tid; i < a.d.total; i += stride) smem[i] = a.blob[i];
-    blob = smem;
-    boff = blob_smem_doubles(a.d);
-    __syncthreads();
+    for (int i = tid; i < a.d.total; i += stride) smem[boff + i] = a.blob[i];
+    blob = smem + boff;
+    boff += blob_smem_doubles(a.d);
   }
-  const MechView mv = make_view(blob, a.d);
+  __syncthreads();
+  const MechView mv = make_view(blob, a.d, etab);
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + tid;
   if (c >= a.ncells) return;
   double* ws = smem + boff + tid;
@@ -364,13 +235,176 @@ __global__ void __launch_bounds__(128) k_eval_thread(EvalArgs a) {
 }
 
 // ----------------------------------------------------------------------------
+// one cell per warp (any N <= 64)
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const int* csr, WarpWS L) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* etab = reinterpret_cast<double2*>(smem);
+  for (int i = tid; i < 64; i += blockDim.x) etab[i] = g_exp2_tab[i];
+  int boff = 128;
+  const double* blob = a.blob;
+  if (a.stage_blob) {
+    for (int i = tid; i < a.d.total; i += blockDim.x) smem[boff + i] = a.blob[i];
+    blob = smem + boff;
+    boff += blob_smem_doubles(a.d);
+  }
+  __syncthreads();
+  const MechView mv = make_view(blob, a.d, etab);
+  const int N = a.d.N, n = N + 1;
+  double* ws = smem + boff + (size_t)warp * L.total;
+  double* y = ws + L.y;
+  double* ys = ws + L.ys;
+  double* f = ws + L.f;
+  double* J = ws + L.J;
+  double* K = ws + L.K;
+  int* piv = reinterpret_cast<int*>(ws + L.piv);
+  const RosTab& tb = c_tab[a.method];
+  unsigned long long tot_acc = 0, tot_rej = 0;
+
+  for (;;) {
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.counters[0], 1ull);
+    idx = __shfl_sync(WFULL, idx, 0);
+    if (idx >= (unsigned long long)a.ncells) break;
+    const int64_t cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
+    bool okin = true;
+    for (int i = lane; i < n; i += 32) {
+      const double v = i == 0 ? a.T[cell] : a.Y[(int64_t)(i - 1) * a.ncells + cell];
+      y[i] = v;
+      okin = okin && isfinite(v) && (i > 0 || v > 0.0);
+    }
+    const double pc = 10.0 * a.p[cell];
+    okin = __all_sync(WFULL, okin) && isfinite(pc) && pc > 0.0;
+    __syncwarp();
+    int status = okin ? DF_CELL_OK : DF_CELL_NONFINITE;
+    bool done = !okin || !(a.dt > 0.0);
+    double t = 0.0, h = fmin(a.h0, a.dt);
+    int nacc = 0, nrej = 0;
+    bool last_rej = false;
+    while (!done) {
+      bool last = false;
+      if (t + h >= a.dt) {
+        h = a.dt - t;
+        last = true;
+      }
+      warp_eval<true>(mv, csr, N, pc, ws, L, L.y);
+      const double hgi = 1.0 / (h * tb.gamma);
+      for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e - i * n;
+        J[e] = (i == j ? hgi : 0.0) - J[e];
+      }
+      __syncwarp();
+      bool ok = warp_lu(J, piv, n);
+      const double ih = 1.0 / h;
+      for (int s = 0; s < tb.s; ++s) {
+        if (s > 0 && tb.newf[s]) {
+          for (int i = lane; i < n; i += 32) {
+            double acc = y[i];
+            for (int j = 0; j < s; ++j) acc += tb.a[s][j] * K[j * n + i];
+            ys[i] = acc;
+          }
+          __syncwarp();
+          warp_eval<false>(mv, csr, N, pc, ws, L, L.ys);
+        }
+        for (int i = lane; i < n; i += 32) {
+          double acc = f[i];
+          for (int j = 0; j < s; ++j) acc += (tb.c[s][j] * ih) * K[j * n + i];
+          K[s * n + i] = acc;
+        }
+        __syncwarp();
+        warp_solve(J, piv, K + s * n, n);
+      }
+      double e2 = 0.0;
+      for (int i = lane; i < n; i += 32) {
+        double yn = y[i], e = 0.0;
+        for (int s = 0; s < tb.s; ++s) {
+          yn += tb.m[s] * K[s * n + i];
+          e += tb.e[s] * K[s * n + i];
+        }
+        ys[i] = yn;
+        const double sc = (i == 0 ? a.atolT : a.atolY) + a.rtol * fmax(fabs(y[i]), fabs(yn));
+        e2 += (e / sc) * (e / sc);
+      }
+      double en = sqrt(warp_sum(e2) / n);
+      ok = ok && isfinite(en);
+      __syncwarp();
+      if (ok && en <= 1.0) {
+        for (int i = lane; i < n; i += 32) y[i] = ys[i];
+        t = last ? a.dt : t + h;
+        ++nacc;
+        double fac = 0.9 * pow(fmax(en, 1e-10), -1.0 / tb.elo);
+        fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+        h *= fac;
+        last_rej = false;
+        if (t >= a.dt) done = true;
+      } else {
+        ++nrej;
+        const double fac = ok ? fmax(0.2, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
+        h *= fac;
+        last_rej = true;
+      }
+      if (!done) {
+        if (nacc + nrej >= a.max_sub) {
+          status = DF_CELL_MAXSTEPS;
+          done = true;
+        } else if (h < a.hmin) {
+          status = DF_CELL_HMIN;
+          done = true;
+        }
+      }
+      __syncwarp();
+    }
+    if (status == DF_CELL_OK) {
+      for (int i = lane; i < n; i += 32) {
+        if (i == 0) a.T[cell] = y[0];
+        else a.Y[(int64_t)(i - 1) * a.ncells + cell] = y[i];
+      }
+    }
+    if (lane == 0) {
+      a.status[cell] = status;
+      if (a.nsub) a.nsub[cell] = nacc;
+      tot_acc += nacc;
+      tot_rej += nrej;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&a.counters[1], tot_acc);
+    atomicAdd(&a.counters[2], tot_rej);
+  }
+}
+
+template <bool WITH_J>
+__global__ void __launch_bounds__(256) k_eval_warp(EvalArgs a, const int* csr, WarpWS L) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double2* etab = reinterpret_cast<double2*>(smem);
+  for (int i = tid; i < 64; i += blockDim.x) etab[i] = g_exp2_tab[i];
+  __syncthreads();
+  const MechView mv = make_view(a.blob, a.d, etab);
+  const int N = a.d.N, n = N + 1;
+  const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= a.ncells) return;
+  double* ws = smem + 128 + (size_t)warp * L.total;
+  for (int i = lane; i < n; i += 32) ws[L.y + i] = i == 0 ? a.T[c] : a.Y[(int64_t)(i - 1) * a.ncells + c];
+  __syncwarp();
+  const double q = warp_eval<WITH_J>(mv, csr, N, 10.0 * a.p[c], ws, L, L.y);
+  if (a.dydt)
+    for (int i = lane; i < n; i += 32) a.dydt[(int64_t)i * a.ncells + c] = ws[L.f + i];
+  if (a.qdot && lane == 0) a.qdot[c] = 0.1 * q;
+  if (WITH_J)
+    for (int e = lane; e < n * n; e += 32) a.J[c * n * n + e] = ws[L.J + e];
+}
+
+// ----------------------------------------------------------------------------
 // host launchers
 // ----------------------------------------------------------------------------
 namespace {
 
 template <int NS>
 size_t thread_smem_bytes(const MechDims& d, int threads, bool stage) {
-  return sizeof(double) * ((stage ? blob_smem_doubles(d) : 0) + (size_t)thread_ws_doubles<NS>() * threads);
+  return sizeof(double) * (128 + (stage ? blob_smem_doubles(d) : 0) + (size_t)thread_ws_doubles<NS>() * threads);
 }
 
 template <int NS>
@@ -429,6 +463,87 @@ int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int thr
 
 #define DF_THREAD_NS_LIST(X) X(3) X(9)
 
+static bool has_thread_kernel(int N) {
+  switch (N) {
+#define X(NS) case NS:
+    DF_THREAD_NS_LIST(X)
+#undef X
+    return true;
+    default:
+      return false;
+  }
+}
+
+namespace {
+
+// warp path launch shape: warps per block from the shared-memory budget
+int warp_shape(const df_mech* m, const WarpWS& L, bool want_stage, int max_warps, int* warps, int* stage,
+               size_t* smem) {
+  const size_t per_warp = sizeof(double) * (size_t)L.total;
+  const size_t fixed = sizeof(double) * 128;
+  const size_t blob = sizeof(double) * (size_t)blob_smem_doubles(m->dims);
+  for (int st = want_stage ? 1 : 0; st >= 0; --st) {
+    const size_t base = fixed + (st ? blob : 0);
+    if (base + per_warp > m->max_smem_optin) continue;
+    int w = (int)((m->max_smem_optin - base) / per_warp);
+    w = std::min(w, max_warps);
+    *warps = w;
+    *stage = st;
+    *smem = base + per_warp * w;
+    return DF_OK;
+  }
+  return set_error(DF_EUNSUPPORTED, "warp-path workspace exceeds shared memory");
+}
+
+int eval_warp_dispatch(const df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y,
+                       double* dydt, double* qdot, double* J, cudaStream_t st) {
+  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M);
+  int warps, stage;
+  size_t sm;
+  int rc = warp_shape(m, L, false, 4, &warps, &stage, &sm);
+  if (rc) return rc;
+  EvalArgs a{m->blob_dev, m->dims, ncells, T, p, Y, dydt, qdot, J, 0};
+  const int64_t blocks = (ncells + warps - 1) / warps;
+  if (J) {
+    auto kf = k_eval_warp<true>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kf<<<(unsigned)blocks, 32 * warps, sm, st>>>(a, m->csr_dev, L);
+  } else {
+    auto kf = k_eval_warp<false>;
+    cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kf<<<(unsigned)blocks, 32 * warps, sm, st>>>(a, m->csr_dev, L);
+  }
+  return cuda_check(cudaGetLastError(), "warp evaluation kernel");
+}
+
+int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads) {
+  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M);
+  int warps, stage;
+  size_t sm;
+  const int max_warps = threads > 0 ? threads / 32 : 8;
+  int rc = warp_shape(m, L, true, max_warps, &warps, &stage, &sm);
+  if (rc) return rc;
+  IntegArgs a = a0;
+  a.stage_blob = stage;
+  auto kf = k_integrate_warp;
+  rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                  "set warp integrator shared memory");
+  if (rc) return rc;
+  int occ = 0;
+  rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kf, 32 * warps, sm), "occupancy");
+  if (rc) return rc;
+  if (occ < 1) return set_error(DF_EUNSUPPORTED, "warp integrator does not fit on an SM");
+  int64_t blocks = (int64_t)m->num_sms * occ;
+  const int64_t need = (a.ncells + warps - 1) / warps;
+  if (blocks > need) blocks = std::max<int64_t>(1, need);
+  rc = cuda_check(cudaMemsetAsync(m->counters, 0, 4 * sizeof(unsigned long long), st), "reset work counter");
+  if (rc) return rc;
+  kf<<<(unsigned)blocks, 32 * warps, sm, st>>>(a, m->csr_dev, L);
+  return cuda_check(cudaGetLastError(), "warp integrator kernel launch");
+}
+
+}  // namespace
+
 int launch_rhs(const df_mech* m, int64_t ncells, const double* T, const double* p,
                const double* Y, double* dydt, double* qdot, cudaStream_t st) {
   switch (m->dims.N) {
@@ -438,7 +553,7 @@ int launch_rhs(const df_mech* m, int64_t ncells, const double* T, const double* 
     DF_THREAD_NS_LIST(X)
 #undef X
     default:
-      return set_error(DF_EUNSUPPORTED, "no kernel built for this species count");
+      return eval_warp_dispatch(m, ncells, T, p, Y, dydt, qdot, nullptr, st);
   }
 }
 
@@ -451,7 +566,7 @@ int launch_jacobian(const df_mech* m, int64_t ncells, const double* T, const dou
     DF_THREAD_NS_LIST(X)
 #undef X
     default:
-      return set_error(DF_EUNSUPPORTED, "no kernel built for this species count");
+      return eval_warp_dispatch(m, ncells, T, p, Y, nullptr, nullptr, J, st);
   }
 }
 
@@ -480,6 +595,10 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
   a.nsub = nsub;
   a.order = nullptr;
   a.counters = m->counters;
+  const bool thread_ok = has_thread_kernel(m->dims.N);
+  if (o.path == 1 && !thread_ok)
+    return set_error(DF_EUNSUPPORTED, "no thread-per-cell kernel built for this species count");
+  if (o.path == 2 || !thread_ok) return integrate_warp_dispatch(m, a, st, o.block_threads);
   const int threads = o.block_threads > 0 ? o.block_threads : 64;
   const int bps = o.blocks_per_sm;
   switch (m->dims.N) {

@@ -275,6 +275,24 @@ int parse_mechanism(const char* path, df_mech* m) {
   std::copy(troe.begin(), troe.end(), m->blob_host.begin() + d.off_tr);
   std::copy(eff.begin(), eff.end(), m->blob_host.begin() + d.off_eff);
   m->lnA_file = lnA;
+  // species -> (reaction, net stoichiometric coefficient nu''_kj - nu'_kj) lists
+  std::vector<std::vector<std::pair<int, int>>> lists(N);
+  for (int j = 0; j < M; ++j) {
+    RxMeta meta;
+    memcpy(&meta, &rec[RX_REC * j + 3], 8);
+    std::vector<int> nu(N, 0);
+    for (int i = 0; i < (meta.nrnp & 15); ++i) nu[meta.reac[i]] -= 1;
+    for (int i = 0; i < (meta.nrnp >> 4); ++i) nu[meta.prod[i]] += 1;
+    for (int k = 0; k < N; ++k)
+      if (nu[k] != 0) lists[k].emplace_back(j, nu[k]);
+  }
+  m->csr_host.assign(N + 1, 0);
+  for (int k = 0; k < N; ++k) m->csr_host[k + 1] = m->csr_host[k] + (int)lists[k].size();
+  for (int k = 0; k < N; ++k)
+    for (auto& e : lists[k]) {
+      m->csr_host.push_back(e.first);
+      m->csr_host.push_back(e.second);
+    }
   return DF_OK;
 }
 

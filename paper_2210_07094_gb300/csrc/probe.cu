@@ -3,6 +3,7 @@
 // of the integrator's FP64 roofline fraction.
 #include "common.cuh"
 #include "../../include/df_probe.h"
+#include "fastexp.cuh"
 
 namespace df {
 
@@ -17,9 +18,25 @@ __global__ void __launch_bounds__(256) k_dfma_chains(double* out, int iters, dou
   out[tid] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+__global__ void k_exp_probe(const double* x, double* y, long long n) {
+  __shared__ double2 tab[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = exp_tang(x[i], tab);
+}
+
 }  // namespace df
 
 using namespace df;
+
+extern "C" int df_probe_exp(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_exp: bad arguments");
+  if (n == 0) return DF_OK;
+  const int threads = 256;
+  k_exp_probe<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cuda_check(cudaGetLastError(), "exp probe kernel");
+}
 
 extern "C" int df_probe_fp64_peak(int iters, double* gflops, double* ms) {
   if (iters < 1 || !gflops) return set_error(DF_EINVAL, "df_probe_fp64_peak: iters >= 1 and gflops required");

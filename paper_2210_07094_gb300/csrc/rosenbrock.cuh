@@ -1,0 +1,172 @@
+// Rosenbrock schemes in the form of Sandu et al. (1997), "Benchmarking stiff
+// ODE solvers for atmospheric chemistry problems II: Rosenbrock solvers":
+//   (I/(h gamma) - J) K_i = f(y + sum_{j<i} a_ij K_j) + sum_{j<i} (c_ij/h) K_j
+//   y_new = y + sum_i m_i K_i,   err = sum_i e_i K_i
+// with the RODAS4 coefficients of Hairer & Wanner (Solving ODEs II, Sec. VI.4)
+// and the RODAS3 coefficients of Sandu et al. (1997).  One attempt of one cell
+// on the thread-per-cell path, and the step-size control shared by the
+// integrator and the adjoint's forward recomputation (so both follow the same
+// step sequence).
+#pragma once
+#include "chem_thread.cuh"
+
+namespace df {
+
+struct RosTab {
+  int s;
+  int elo;
+  double gamma;
+  double a[6][6];
+  double c[6][6];
+  double m[6];
+  double e[6];
+  int newf[6];
+};
+
+static RosTab make_rodas4() {
+  RosTab t;
+  memset(&t, 0, sizeof(t));
+  t.s = 6;
+  t.elo = 4;
+  t.gamma = 0.25;
+  const double A[15] = {1.544, 0.9466785280815826, 0.2557011698983284, 3.314825187068521,
+                        2.896124015972201, 0.9986419139977817, 1.221224509226641, 6.019134481288629,
+                        12.53708332932087, -0.6878860361058950, 1.221224509226641, 6.019134481288629,
+                        12.53708332932087, -0.6878860361058950, 1.0};
+  const double C[15] = {-5.6688, -2.430093356833875, -0.2063599157091915, -0.1073529058151375,
+                        -9.594562251023355, -20.47028614809616, 7.496443313967647, -10.24680431464352,
+                        -33.99990352819905, 11.70890893206160, 8.083246795921522, -7.981132988064893,
+                        -31.52159432874371, 16.31930543123136, -6.058818238834054};
+  int idx = 0;
+  for (int i = 1; i < 6; ++i)
+    for (int j = 0; j < i; ++j) {
+      t.a[i][j] = A[idx];
+      t.c[i][j] = C[idx];
+      ++idx;
+    }
+  t.m[0] = A[6];
+  t.m[1] = A[7];
+  t.m[2] = A[8];
+  t.m[3] = A[9];
+  t.m[4] = 1.0;
+  t.m[5] = 1.0;
+  t.e[5] = 1.0;
+  for (int i = 0; i < 6; ++i) t.newf[i] = 1;
+  return t;
+}
+
+static RosTab make_rodas3() {
+  RosTab t;
+  memset(&t, 0, sizeof(t));
+  t.s = 4;
+  t.elo = 3;
+  t.gamma = 0.5;
+  t.a[1][0] = 0.0;
+  t.a[2][0] = 2.0;
+  t.a[2][1] = 0.0;
+  t.a[3][0] = 2.0;
+  t.a[3][1] = 0.0;
+  t.a[3][2] = 1.0;
+  t.c[1][0] = 4.0;
+  t.c[2][0] = 1.0;
+  t.c[2][1] = -1.0;
+  t.c[3][0] = 1.0;
+  t.c[3][1] = -1.0;
+  t.c[3][2] = -8.0 / 3.0;
+  t.m[0] = 2.0;
+  t.m[1] = 0.0;
+  t.m[2] = 1.0;
+  t.m[3] = 1.0;
+  t.e[3] = 1.0;
+  t.newf[0] = 1;
+  t.newf[1] = 0;  // a[1][*] = 0: stage 2 reuses f(y)
+  t.newf[2] = 1;
+  t.newf[3] = 1;
+  return t;
+}
+
+
+// One Rosenbrock attempt from y over h: K stages in Kv (strided, s x n), the
+// factorised W = I/(h gamma) - J(y) left in Jv, the candidate state in ynew and
+// the weighted RMS norm of the embedded error estimate in en.
+template <int NS>
+__device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb, double pc, const double (&y)[NS + 1],
+                                            double h, double rtol, double atolY, double atolT, SV C, SV wdot,
+                                            SV gRT, SV hRT, SV cpR, SV Jv, SV Kv, int stride,
+                                            double (&ynew)[NS + 1], double& en, int* piv_out = nullptr) {
+  constexpr int n = NS + 1;
+  double fs[n];
+  eval_thread<NS, true>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  const double hgi = 1.0 / (h * tb.gamma);
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+#pragma unroll
+    for (int j = 0; j < n; ++j) Jv[i * n + j] = (i == j ? hgi : 0.0) - Jv[i * n + j];
+  }
+  int piv_l[n];
+  int* piv = piv_out ? piv_out : piv_l;
+  bool ok = lu_factor<n>(Jv, piv);
+  const double ih = 1.0 / h;
+  for (int s = 0; s < tb.s; ++s) {
+    if (s > 0 && tb.newf[s]) {
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double acc = y[i];
+        for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
+        ynew[i] = acc;
+      }
+      eval_thread<NS, false>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
+    }
+    // stage right-hand side, solved in place in the K slot of this stage
+    SV Ks{&Kv[s * n], stride};
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      double acc = fs[i];
+      for (int j = 0; j < s; ++j) acc += (tb.c[s][j] * ih) * Kv[j * n + i];
+      Ks[i] = acc;
+    }
+    lu_solve<n>(Jv, piv, Ks);
+  }
+  double e2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    double yn = y[i], e = 0.0;
+    for (int s = 0; s < tb.s; ++s) {
+      const double kv = Kv[s * n + i];
+      yn += tb.m[s] * kv;
+      e += tb.e[s] * kv;
+    }
+    ynew[i] = yn;
+    const double sc = (i == 0 ? atolT : atolY) + rtol * fmax(fabs(y[i]), fabs(yn));
+    const double r = e / sc;
+    e2 += r * r;
+  }
+  en = sqrt(e2 / n);
+  return ok && isfinite(en);
+}
+
+// accept / reject and the next step size (elementary controller with safety
+// factor 0.9, growth limits [0.2, 6], no growth right after a rejection)
+template <int n>
+__device__ __forceinline__ void step_control(const RosTab& tb, bool ok, double en, bool last, double dt,
+                                             double (&y)[n], const double (&ynew)[n], double& t, double& h,
+                                             int& nacc, int& nrej, bool& last_rej, bool& done) {
+  if (ok && en <= 1.0) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) y[i] = ynew[i];
+    t = last ? dt : t + h;
+    ++nacc;
+    double fac = 0.9 * pow(fmax(en, 1e-10), -1.0 / tb.elo);
+    fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+    h *= fac;
+    last_rej = false;
+    if (t >= dt) done = true;
+  } else {
+    ++nrej;
+    const double fac = ok ? fmax(0.2, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
+    h *= fac;
+    last_rej = true;
+  }
+}
+
+}  // namespace df

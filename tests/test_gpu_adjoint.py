@@ -1,0 +1,151 @@
+"""GPU discrete adjoint against (a) the oracle's complex-step derivative of the
+same discrete map (RODAS4 replayed with the GPU's accepted step sequence, read
+from the checkpoints) and (b) central finite differences of that map."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2210_07094_gb300 as df  # noqa: E402
+from oracle.oracle import Mech  # noqa: E402
+from paper_2210_07094_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def setup():
+    mech = synth.h2_air_mechanism()
+    return mech, df.Mechanism(mech), Mech(mech)
+
+
+def _dev(f):
+    return (torch.tensor(f["T"], device=DEV), torch.tensor(f["p"], device=DEV),
+            torch.tensor(np.ascontiguousarray(f["Y"]), device=DEV))
+
+
+def _run(setup, cfg, ncells, seed, opts=None):
+    mech, m, o = setup
+    f = synth.field(cfg, mech, ncells, seed=seed)
+    T, p, Y = _dev(f)
+    N = m.n_species
+    rng = np.random.default_rng(seed)
+    gT = rng.standard_normal(ncells)
+    gY = rng.standard_normal((N, ncells))
+    gQ = rng.standard_normal(ncells) * 1e-9
+    r = df.adjoint(m, T, p, Y, f["dt"], torch.tensor(gT, device=DEV), torch.tensor(gY, device=DEV),
+                   torch.tensor(gQ, device=DEV), opts=opts)
+    return f, gT, gY, gQ, r
+
+
+def _steps(r, N, c, max_steps=64):
+    ns = int(r["nsub"][c])
+    ck = r["workspace"][: r["nsub"].numel() * max_steps * (N + 2) * 8].view(torch.float64)
+    ck = ck.view(-1, max_steps, N + 2)[c, :ns].cpu().numpy()
+    return ck[:, -1]
+
+
+@pytest.mark.parametrize("cfg", [1, 3])
+def test_adjoint_matches_oracle_complex_step(setup, cfg):
+    mech, m, o = setup
+    n = 48
+    f, gT, gY, gQ, r = _run(setup, cfg, n, 100 + cfg)
+    assert int(r["status"].abs().sum()) == 0
+    gT0, gY0, glnA = r["gT0"].cpu().numpy(), r["gY0"].cpu().numpy(), r["g_lnA"].cpu().numpy()
+    rng = np.random.default_rng(7)
+    dlnA = rng.standard_normal(m.n_reactions)
+    tot_gpu_A, tot_or_A = glnA @ dlnA, 0.0
+    for c in range(n):
+        hs = _steps(r, m.n_species, c)
+        y0 = np.concatenate([[f["T"][c]], f["Y"][:, c]])
+        dy0 = rng.standard_normal(m.n_species + 1) * np.r_[1.0, np.full(m.n_species, 1e-4)]
+        d_or = o.ros_replay_dir(f["p"][c], y0, hs, wT=gT[c], wY=gY[:, c], wQ=gQ[c], dy0=dy0)
+        d_gpu = gT0[c] * dy0[0] + gY0[:, c] @ dy0[1:]
+        assert abs(d_gpu - d_or) <= 1e-6 * max(abs(d_or), 1e-12), (c, d_gpu, d_or)
+        tot_or_A += o.ros_replay_dir(f["p"][c], y0, hs, wT=gT[c], wY=gY[:, c], wQ=gQ[c], dlnA=dlnA)
+    assert abs(tot_gpu_A - tot_or_A) <= 1e-6 * abs(tot_or_A)
+
+
+def test_adjoint_matches_central_differences(setup):
+    """Central differences (step 1e-6 relative) of the replayed RODAS4 map."""
+    mech, m, o = setup
+    n = 8
+    f, gT, gY, gQ, r = _run(setup, 1, n, 31)
+    gT0, gY0, glnA = r["gT0"].cpu().numpy(), r["gY0"].cpu().numpy(), r["g_lnA"].cpu().numpy()
+
+    def L(c, y0, mm):
+        hs = _steps(r, m.n_species, c)
+        y = mm.ros_replay(f["p"][c], y0, hs)
+        return gT[c] * y[0] + gY[:, c] @ y[1:] + gQ[c] * mm.rhs(f["p"][c], y)[1]
+
+    for c in range(n):
+        y0 = np.concatenate([[f["T"][c]], f["Y"][:, c]])
+        eps = 1e-6 * y0[0]
+        e = np.zeros_like(y0)
+        e[0] = eps
+        fd = (L(c, y0 + e, o) - L(c, y0 - e, o)) / (2 * eps)
+        assert abs(gT0[c] - fd) <= 1e-5 * max(abs(fd), 1e-6 * abs(gT[c])), (c, gT0[c], fd)
+    # ln A of the most sensitive reactions, summed over the cells.  The loss
+    # weighs Y only: a T term (T ~ 2000 K, rounding ~4e-13 K) would drown a
+    # 1e-6 central difference in rounding noise.
+    T, p, Y = _dev(f)
+    r2 = df.adjoint(m, T, p, Y, f["dt"], gY1=torch.tensor(gY, device=DEV))
+    glnA = r2["g_lnA"].cpu().numpy()
+
+    def LY(c, y0, mm):
+        hs = _steps(r2, m.n_species, c)
+        return gY[:, c] @ mm.ros_replay(f["p"][c], y0, hs)[1:]
+
+    for j in np.argsort(-np.abs(glnA))[:3]:
+        eps = 1e-6
+        tot = 0.0
+        for sgn in (1, -1):
+            mm = Mech(mech)
+            mm.A[j] *= np.exp(sgn * eps)
+            mm.A0[j] *= np.exp(sgn * eps)
+            tot += sgn * sum(LY(c, np.concatenate([[f["T"][c]], f["Y"][:, c]]), mm) for c in range(n))
+        fd = tot / (2 * eps)
+        assert abs(glnA[j] - fd) <= 1e-5 * abs(fd), (j, glnA[j], fd)
+
+
+def test_adjoint_deterministic_and_full_size(setup):
+    """65536 cells (the adjoint workload): all cells OK, ln A gradient bitwise
+    reproducible across calls."""
+    mech, m, o = setup
+    f = synth.field(3, mech)
+    T, p, Y = _dev(f)
+    gT = torch.ones_like(T)
+    r1 = df.adjoint(m, T, p, Y, f["dt"], gT1=gT)
+    r2 = df.adjoint(m, T, p, Y, f["dt"], gT1=gT)
+    assert int(r1["status"].abs().sum()) == 0
+    assert torch.equal(r1["g_lnA"], r2["g_lnA"]) and torch.equal(r1["gY0"], r2["gY0"])
+    assert torch.isfinite(r1["g_lnA"]).all()
+
+
+def test_autograd_function(setup):
+    mech, m, o = setup
+    f = synth.field(0, mech, 64)
+    T0, p, Y0 = _dev(f)
+    T0.requires_grad_(True)
+    Y0.requires_grad_(True)
+    lnA = torch.tensor(np.log([r["A"] for r in mech["reactions"]]), device=DEV, requires_grad=True)
+    T, Y, q, st = df.chem_step(m, T0, p, Y0, lnA, f["dt"])
+    loss = T.sum() + 1e-9 * q.sum()
+    loss.backward()
+    r = df.adjoint(m, T0.detach(), p, Y0.detach(), f["dt"], gT1=torch.ones_like(T),
+                   gQ1=torch.full_like(T, 1e-9))
+    assert torch.allclose(T0.grad, r["gT0"], rtol=1e-12, atol=0)
+    assert torch.allclose(lnA.grad, r["g_lnA"], rtol=1e-12, atol=1e-300)
+    # a finite-difference look at the adaptive map itself (its step sequence does
+    # not change for a 1e-6 change of ln A on these cells)
+    j = int(torch.argmax(lnA.grad.abs()))
+    vals = []
+    for sgn in (1, -1):
+        la = lnA.detach().clone()
+        la[j] += sgn * 1e-6
+        T2, Y2, q2, _ = df.chem_step(m, T0.detach(), p, Y0.detach(), la, f["dt"])
+        vals.append((T2.sum() + 1e-9 * q2.sum()).item())
+    fd = (vals[0] - vals[1]) / 2e-6
+    assert abs(fd - lnA.grad[j].item()) <= 1e-3 * abs(fd) + 1e-9
+    m.set_lnA(None)

@@ -134,6 +134,7 @@ def test_max_substeps_is_reported(h2):
     T, p, Y = _dev(f)
     opts = df.default_opts()
     opts.max_substeps = 2
+    opts.h0 = 1e-12
     status, nsub = df.integrate(m, T, p, Y, f["dt"], opts)
     assert np.all(status.cpu().numpy() == df._lib.CELL_MAXSTEPS)
 
@@ -192,3 +193,72 @@ def test_set_lnA_matches_scaled_mechanism(h2):
     df.integrate(m, T, p, Y, f["dt"])
     To, Yo, _, _ = Mech(mech).integrate(f["T"], f["p"], f["Y"], f["dt"])
     _assert_parity(T.cpu().numpy(), Y.cpu().numpy(), To, Yo)
+
+
+# ---------------------------------------------------------------------------
+# warp-per-cell path: the 9-species mechanism forced onto it, and the
+# 50-species / 300-reaction mechanism that only it runs
+# ---------------------------------------------------------------------------
+
+def test_warp_path_9_species(h2):
+    mech, m, o = h2
+    f = synth.field(1, mech, 600)
+    T, p, Y = _dev(f)
+    opts = df.default_opts()
+    opts.path = 2
+    status, nsub = df.integrate(m, T, p, Y, f["dt"], opts)
+    To, Yo, so, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"])
+    assert int(status.abs().sum()) == 0
+    _assert_parity(T.cpu().numpy(), Y.cpu().numpy(), To, Yo)
+    # same method, same cell: the two paths agree far inside the tolerance
+    T2, p2, Y2 = _dev(f)
+    opts.path = 1
+    df.integrate(m, T2, p2, Y2, f["dt"], opts)
+    assert torch.max(torch.abs(T2 - T)).item() <= 1e-6
+    assert torch.max(torch.abs(Y2 - Y)).item() <= 1e-10
+
+
+@pytest.fixture(scope="module")
+def chon():
+    mech = synth.hydrocarbon_mechanism()
+    return mech, df.Mechanism(mech), Mech(mech)
+
+
+def test_chon_rhs_and_jacobian(chon):
+    mech, m, o = chon
+    f = synth.field(2, mech, 70)
+    T, p, Y = _dev(f)
+    dydt, qdot = df.rhs(m, T, p, Y)
+    J = df.jacobian(m, T, p, Y).cpu().numpy()
+    dydt = dydt.cpu().numpy()
+    for c in range(0, 70, 9):
+        y = np.concatenate([[f["T"][c]], f["Y"][:, c]])
+        fo, _ = o.rhs(f["p"][c], y)
+        assert np.max(np.abs(dydt[:, c] - fo)) <= 1e-12 * np.abs(fo).max()
+        Jo = o.jac(f["p"][c], y)
+        scale = np.abs(Jo).max(axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(J[c] - Jo) / scale) <= 1e-10
+
+
+def test_chon_integrate_small_all_cells(chon):
+    mech, m, o = chon
+    f = synth.field(2, mech, 45)
+    T, p, Y = _dev(f)
+    status, _ = df.integrate(m, T, p, Y, f["dt"])
+    To, Yo, so, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"])
+    assert int(status.abs().sum()) == 0 and np.all(so == 0)
+    _assert_parity(T.cpu().numpy(), Y.cpu().numpy(), To, Yo)
+
+
+def test_chon_integrate_full_size_sampled(chon):
+    """262144 cells of the 50-species field in one launch; 32 sampled cells
+    against the oracle."""
+    mech, m, o = chon
+    f = synth.field(2, mech)
+    T, p, Y = _dev(f)
+    status, nsub = df.integrate(m, T, p, Y, f["dt"])
+    assert int(status.abs().sum()) == 0
+    idx = np.random.default_rng(11).choice(f["T"].shape[0], 32, replace=False)
+    To, Yo, so, _ = o.integrate(f["T"][idx], f["p"][idx], f["Y"][:, idx], f["dt"])
+    assert np.all(so == 0)
+    _assert_parity(T.cpu().numpy()[idx], Y.cpu().numpy()[:, idx], To, Yo)
