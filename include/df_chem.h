@@ -178,6 +178,88 @@ int df_chem_last_stats(const df_mech* mech, int64_t* accepted, int64_t* rejected
                        df_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * DNN chemistry integrator (Sec. 2.3 and Sec. 3.2 DNNInferencer): a fully
+ * connected network with three hidden layers maps x = {T, p, F(Y_1..Y_N)} to the
+ * change u of F(Y) over dt, F the Box-Cox transform F(Y) = (max(Y,0)^lambda - 1)
+ * / lambda.  Inference follows the three stages of DNNInferencer.inference:
+ * (1) Box-Cox + normalisation of (p, T, Y), (2) the network, (3) the inverse
+ * transform to Y(t + dt); then T(t + dt) from h(T', Y') = h(T, Y) at fixed p
+ * (correctThermo, Sec. 3.2).  Cells outside the training range are advanced
+ * by df_chem_integrate instead (FP64 fallback).
+ *
+ * Network: BF16 weights and activations, FP32 accumulation on the tensor
+ * cores, FP32 bias + exact-erf GELU, then rounding to BF16 (the rounding
+ * points of every layer); FP32 master weights and Adam moments for training.
+ * ------------------------------------------------------------------------- */
+typedef struct df_dnn df_dnn;
+
+typedef struct df_dnn_opts {
+  int32_t n_species;   /* N: 2 + N inputs (<= 16), N outputs (<= 16)               */
+  int32_t width[3];    /* hidden widths, multiples of 8 (default 1600, 800, 400)   */
+  double lambda;       /* Box-Cox lambda (default 0.1); 1/lambda must be an integer */
+  int32_t batch;       /* rows per training step (default 4096)                    */
+  int32_t infer_chunk; /* cells per inference chunk (default 262144)               */
+  double beta1, beta2, adam_eps; /* Adam (0.9, 0.999, 1e-8)                        */
+  double range_margin; /* fraction of the training range accepted outside it (0)  */
+  int32_t reserved[4];
+} df_dnn_opts;
+
+void df_dnn_opts_default(df_dnn_opts* opts);
+
+/* Create a network with Glorot-uniform weights drawn from `seed` (the library's
+ * own counter-based generator) and zero biases; normalisation identity. */
+int df_dnn_create(const df_dnn_opts* opts, uint64_t seed, df_dnn** out);
+void df_dnn_free(df_dnn* dnn);
+
+/* Normalisation and range statistics (host arrays): mean_in, std_in, in_min,
+ * in_max have 2 + N entries (T, p, F(Y_1..N)); mean_out, std_out have N
+ * entries (the change of F(Y) over dt).  Any pointer may be NULL (keep). */
+int df_dnn_set_norm(df_dnn* dnn, const float* mean_in, const float* std_in, const float* mean_out,
+                    const float* std_out, const float* in_min, const float* in_max);
+int df_dnn_get_norm(const df_dnn* dnn, float* mean_in, float* std_in, float* mean_out, float* std_out,
+                    float* in_min, float* in_max);
+
+/* Compute the statistics above from n training pairs (T, p, Y) -> Y_next on the
+ * device (FP64 accumulation, fixed summation order) and store them in the
+ * handle.  Device arrays, SoA as for the integrator.  Synchronises `stream`. */
+int df_dnn_fit_norm(df_dnn* dnn, int64_t n, const double* T, const double* p, const double* Y,
+                    const double* Y_next, df_stream_t stream);
+
+/* One Adam step on a batch of n pairs (n <= opts.batch): loss = mean over rows
+ * and the N outputs of the squared error of the normalised change of F(Y).
+ * lr: learning rate of this step.  loss_out (host, may be NULL): the batch loss
+ * before the update (synchronises `stream`). */
+int df_dnn_train_step(df_dnn* dnn, int64_t n, const double* T, const double* p, const double* Y,
+                      const double* Y_next, float lr, float* loss_out, df_stream_t stream);
+
+/* Advance ncells cells over dt with the network (T, Y in/out, device).  Cells
+ * whose inputs leave the training range [in_min, in_max] (widened by
+ * range_margin) are advanced by df_chem_integrate with fallback_opts (NULL =
+ * defaults) on `mech`.  used_fallback [ncells] (device, may be NULL): 1 for
+ * those cells.  n_fallback (host, may be NULL): their count.  status [ncells]
+ * (device, may be NULL): DF_CELL_* (network cells are DF_CELL_OK).
+ * Synchronises `stream` once (to size the fallback launch). */
+int df_dnn_infer(df_dnn* dnn, const df_mech* mech, int64_t ncells, double* T, const double* p, double* Y,
+                 double dt, const df_integ_opts* fallback_opts, int32_t* used_fallback, int64_t* n_fallback,
+                 int32_t* status, df_stream_t stream);
+
+/* The network's raw output for prepared inputs: X [n][16] bf16 features as the
+ * network sees them (device), U [n][16] f32 (device).  For checking the layers. */
+int df_dnn_forward_raw(df_dnn* dnn, int64_t n, const void* X, float* U, df_stream_t stream);
+
+/* FP32 master parameters in the order W1[w1][16], b1[w1], W2[w2][w1], b2, W3[w3][w2],
+ * b3, W4[16][w3], b4[16] (host buffer of df_dnn_param_count() floats).  get_grads
+ * copies the gradients of the last training step in the same layout. */
+int64_t df_dnn_param_count(const df_dnn* dnn);
+int df_dnn_get_params(const df_dnn* dnn, float* host);
+int df_dnn_set_params(df_dnn* dnn, const float* host);
+int df_dnn_get_grads(const df_dnn* dnn, float* host);
+
+/* Save / load options, normalisation and parameters (binary file). */
+int df_dnn_save(const df_dnn* dnn, const char* path);
+int df_dnn_load(const char* path, df_dnn** out);
+
+/* ---------------------------------------------------------------------------
  * errors
  * ------------------------------------------------------------------------- */
 const char* df_strerror(int code);

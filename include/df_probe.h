@@ -22,6 +22,15 @@ int df_probe_fp64_peak(int iters, double* gflops, double* ms);
  * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */
 int df_probe_exp(const double* x, double* y, long long n, void* stream);
 
+/* C = A . B^T with the library's tcgen05 BF16 GEMM (the kernel under the DNN
+ * integrator's layers), FP32 result without bias or activation, so that it can be
+ * checked against a reference matmul.  A [M][K], B [N][K] bf16 (device, 16-byte
+ * aligned, K a multiple of 8), C [M][N] f32 (device), N a multiple of 8; bn: output
+ * tile width 64, 128 or 256 (0 = choose).  err_flag (device int, may be NULL) is
+ * set to 1 if a bounded pipeline wait ran out.  Asynchronous on `stream`. */
+int df_probe_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int bn, int* err_flag,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

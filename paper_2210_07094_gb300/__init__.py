@@ -17,7 +17,7 @@ import tempfile
 from . import _lib
 
 __all__ = ["Mechanism", "rhs", "jacobian", "integrate", "adjoint", "chem_step", "IntegOpts",
-           "default_opts"]
+           "default_opts", "Dnn", "DnnOpts", "dnn_default_opts"]
 
 IntegOpts = _lib.IntegOpts
 default_opts = _lib.default_opts
@@ -227,3 +227,137 @@ def chem_step(mech: Mechanism, T0, p, Y0, lnA, dt: float, opts: IntegOpts | None
     if _chem_step is None:
         _chem_step = _make_chem_step()
     return _chem_step.apply(T0, p, Y0, lnA, mech, dt, opts, max_steps)
+
+
+DnnOpts = _lib.DnnOpts
+
+
+def dnn_default_opts() -> DnnOpts:
+    o = DnnOpts()
+    _lib.load().df_dnn_opts_default(C.byref(o))
+    return o
+
+
+class Dnn:
+    """DNN chemistry integrator (Box-Cox features, 3 GELU hidden layers on the
+    tensor cores, FP64 fallback to the integrator outside the training range)."""
+
+    def __init__(self, opts: DnnOpts | None = None, seed: int = 22, _handle=None, n_species=None):
+        lib = _lib.load()
+        self._n_species = n_species if n_species is not None else (opts.n_species if opts is not None else 9)
+        if _handle is not None:
+            self._h = _handle
+        else:
+            h = C.c_void_p()
+            _lib.check(lib.df_dnn_create(C.byref(opts) if opts is not None else None, int(seed), C.byref(h)),
+                       "df_dnn_create")
+            self._h = h
+        self.n_params = lib.df_dnn_param_count(self._h)
+
+    @classmethod
+    def load(cls, path: str):
+        import struct
+        with open(path, "rb") as f:
+            f.read(8)
+            n_species = struct.unpack("<i", f.read(4))[0]
+        h = C.c_void_p()
+        _lib.check(_lib.load().df_dnn_load(os.fsencode(path), C.byref(h)), "df_dnn_load")
+        return cls(_handle=h, n_species=n_species)
+
+    def save(self, path: str):
+        _lib.check(_lib.load().df_dnn_save(self._h, os.fsencode(path)), "df_dnn_save")
+
+    def fit_norm(self, T, p, Y, Y_next, stream=None):
+        torch = _torch()
+        n = T.numel()
+        _lib.check(_lib.load().df_dnn_fit_norm(self._h, n, _dptr(T, "T", torch.float64), _dptr(p, "p"),
+                                               _dptr(Y, "Y"), _dptr(Y_next, "Y_next"), _stream_ptr(stream)),
+                   "df_dnn_fit_norm")
+
+    def norm(self):
+        import numpy as np
+        o = self.opts_n()
+        arrs = [np.zeros(o + 2, np.float32), np.zeros(o + 2, np.float32), np.zeros(o, np.float32),
+                np.zeros(o, np.float32), np.zeros(o + 2, np.float32), np.zeros(o + 2, np.float32)]
+        ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs]
+        _lib.check(_lib.load().df_dnn_get_norm(self._h, *ptrs), "df_dnn_get_norm")
+        keys = ["mean_in", "std_in", "mean_out", "std_out", "in_min", "in_max"]
+        return dict(zip(keys, arrs))
+
+    def set_norm(self, **kw):
+        import numpy as np
+        keys = ["mean_in", "std_in", "mean_out", "std_out", "in_min", "in_max"]
+        arrs = [None if kw.get(k) is None else np.ascontiguousarray(kw[k], np.float32) for k in keys]
+        ptrs = [None if a is None else a.ctypes.data_as(C.c_void_p) for a in arrs]
+        _lib.check(_lib.load().df_dnn_set_norm(self._h, *ptrs), "df_dnn_set_norm")
+
+    def opts_n(self):
+        # number of species, from the parameter layout
+        return self._n_species
+
+    def train_step(self, T, p, Y, Y_next, lr: float, want_loss: bool = True, stream=None):
+        torch = _torch()
+        n = T.numel()
+        loss = C.c_float()
+        _lib.check(_lib.load().df_dnn_train_step(self._h, n, _dptr(T, "T", torch.float64), _dptr(p, "p"),
+                                                 _dptr(Y, "Y"), _dptr(Y_next, "Y_next"), float(lr),
+                                                 C.byref(loss) if want_loss else None, _stream_ptr(stream)),
+                   "df_dnn_train_step")
+        return loss.value if want_loss else None
+
+    def infer(self, mech: Mechanism, T, p, Y, dt: float, fallback_opts: IntegOpts | None = None,
+              used_fallback=None, status=None, stream=None):
+        """Advance cells in place with the network; returns (n_fallback, used_fallback, status)."""
+        torch = _torch()
+        n = T.numel()
+        if used_fallback is None:
+            used_fallback = torch.empty(n, dtype=torch.int32, device=T.device)
+        if status is None:
+            status = torch.empty(n, dtype=torch.int32, device=T.device)
+        nfb = C.c_int64()
+        _lib.check(_lib.load().df_dnn_infer(self._h, mech.handle, n, _dptr(T, "T", torch.float64),
+                                            _dptr(p, "p", torch.float64, n),
+                                            _dptr(Y, "Y", torch.float64, mech.n_species * n), float(dt),
+                                            C.byref(fallback_opts) if fallback_opts is not None else None,
+                                            _dptr(used_fallback, "used_fallback", torch.int32, n), C.byref(nfb),
+                                            _dptr(status, "status", torch.int32, n), _stream_ptr(stream)),
+                   "df_dnn_infer")
+        return nfb.value, used_fallback, status
+
+    def forward_raw(self, X, stream=None):
+        """Network output U [n, 16] f32 for prepared bf16 features X [n, 16]."""
+        torch = _torch()
+        n = X.shape[0]
+        U = torch.empty((n, 16), dtype=torch.float32, device=X.device)
+        _lib.check(_lib.load().df_dnn_forward_raw(self._h, n, _dptr(X, "X", torch.bfloat16, n * 16),
+                                                  _dptr(U, "U"), _stream_ptr(stream)), "df_dnn_forward_raw")
+        return U
+
+    def params(self):
+        import numpy as np
+        a = np.zeros(self.n_params, np.float32)
+        _lib.check(_lib.load().df_dnn_get_params(self._h, a.ctypes.data_as(C.c_void_p)), "df_dnn_get_params")
+        return a
+
+    def grads(self):
+        import numpy as np
+        a = np.zeros(self.n_params, np.float32)
+        _lib.check(_lib.load().df_dnn_get_grads(self._h, a.ctypes.data_as(C.c_void_p)), "df_dnn_get_grads")
+        return a
+
+    def set_params(self, a):
+        import numpy as np
+        a = np.ascontiguousarray(a, np.float32)
+        assert a.size == self.n_params
+        _lib.check(_lib.load().df_dnn_set_params(self._h, a.ctypes.data_as(C.c_void_p)), "df_dnn_set_params")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().df_dnn_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,6 +25,13 @@ class IntegOpts(C.Structure):
                 ("order_by_T", C.c_int32), ("path", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
+class DnnOpts(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("width", C.c_int32 * 3), ("lambda_", C.c_double),
+                ("batch", C.c_int32), ("infer_chunk", C.c_int32), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("adam_eps", C.c_double), ("range_margin", C.c_double),
+                ("reserved", C.c_int32 * 4)]
+
+
 class DFError(RuntimeError):
     def __init__(self, code: int, fn: str, detail: str):
         super().__init__(f"{fn} failed: {ERRORS.get(code, code)}: {detail}")
@@ -48,10 +55,26 @@ SIGNATURES = [
     ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),
     ("df_chem_adjoint", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
                              _p, _sz, _p]),
+    ("df_dnn_opts_default", None, [_p]),
+    ("df_dnn_create", _i, [_p, C.c_uint64, _p]),
+    ("df_dnn_free", None, [_p]),
+    ("df_dnn_set_norm", _i, [_p, _p, _p, _p, _p, _p, _p]),
+    ("df_dnn_get_norm", _i, [_p, _p, _p, _p, _p, _p, _p]),
+    ("df_dnn_fit_norm", _i, [_p, _i64, _p, _p, _p, _p, _p]),
+    ("df_dnn_train_step", _i, [_p, _i64, _p, _p, _p, _p, C.c_float, _p, _p]),
+    ("df_dnn_infer", _i, [_p, _p, _i64, _p, _p, _p, _d, _p, _p, _p, _p, _p]),
+    ("df_dnn_forward_raw", _i, [_p, _i64, _p, _p, _p]),
+    ("df_dnn_param_count", _i64, [_p]),
+    ("df_dnn_get_params", _i, [_p, _p]),
+    ("df_dnn_set_params", _i, [_p, _p]),
+    ("df_dnn_get_grads", _i, [_p, _p]),
+    ("df_dnn_save", _i, [_p, C.c_char_p]),
+    ("df_dnn_load", _i, [C.c_char_p, _p]),
     ("df_strerror", C.c_char_p, [_i]),
     ("df_get_last_error_detail", _i, [C.c_char_p, _sz]),
     ("df_probe_fp64_peak", _i, [_i, _p, _p]),
     ("df_probe_exp", _i, [_p, _p, C.c_longlong, _p]),
+    ("df_probe_gemm_bf16", _i, [_p, _p, _p, _i, _i, _i, _i, _p, _p]),
 ]
 
 

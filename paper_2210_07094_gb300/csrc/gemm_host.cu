@@ -1,0 +1,114 @@
+// Host side of the tcgen05 GEMM: TMA tensor maps (cuTensorMapEncodeTiled reached
+// through the runtime's driver entry point, so the library does not link the
+// driver library) and the launch.
+#include <cuda.h>
+
+#include "common.cuh"
+#include "gemm_host.cuh"
+#include "tc_gemm.cuh"
+#include "../../include/df_probe.h"
+
+namespace df {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2D bf16 tensor [rows][K] (K contiguous), tiles of 64 (K) x box_rows, 128-byte swizzle
+static int make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(DF_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  if (ld == 0) ld = K;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || (K % 8) != 0 || (ld % 8) != 0 || ld < K || rows < 1 ||
+      K < 1)
+    return set_error(DF_EINVAL, "GEMM operand must be 16-byte aligned with K and its row pitch multiples of 8");
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)GEMM_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(DF_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return DF_OK;
+}
+
+constexpr int GEMM_STAGES = 3;
+
+template <int BN>
+static size_t gemm_smem() {
+  return (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
+}
+
+template <int BN>
+static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
+  if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
+  if (rc) return rc;
+  auto kf = k_gemm_tc<BN, GEMM_STAGES>;
+  const size_t sm = gemm_smem<BN>();
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                    "set GEMM shared memory");
+    if (rc) return rc;
+    attr_set[dev] = true;
+  }
+  dim3 grid((P.N + BN - 1) / BN, (P.M + GEMM_BM - 1) / GEMM_BM);
+  if (grid.y > 65535) return set_error(DF_EUNSUPPORTED, "GEMM M too large for one launch");
+  kf<<<grid, 128, sm, st>>>(ta, tb, P);
+  return cuda_check(cudaGetLastError(), "GEMM launch");
+}
+
+int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st, int bn) {
+  if (P.M < 1 || P.N < 1 || P.K < 1 || (P.N % 8) != 0)
+    return set_error(DF_EINVAL, "GEMM sizes: M, N, K >= 1 and N a multiple of 8");
+  if (bn == 0) bn = P.N <= 64 ? 64 : 128;
+  switch (bn) {
+    case 64:
+      return gemm_launch_bn<64>(A, B, P, st);
+    case 128:
+      return gemm_launch_bn<128>(A, B, P, st);
+    case 256:
+      return gemm_launch_bn<256>(A, B, P, st);
+    default:
+      return set_error(DF_EINVAL, "GEMM tile width must be 64, 128 or 256");
+  }
+}
+
+}  // namespace df
+
+using namespace df;
+
+extern "C" int df_probe_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int bn,
+                                  int* err_flag, void* stream) {
+  if (!A || !B || !C) return set_error(DF_EINVAL, "df_probe_gemm_bf16: null pointer");
+  GemmParams P;
+  memset(&P, 0, sizeof(P));
+  P.M = M;
+  P.N = N;
+  P.K = K;
+  P.mode = EPI_F32;
+  P.out0 = C;
+  P.ld0 = N;
+  P.err = err_flag;
+  return gemm_bf16(A, B, P, (cudaStream_t)stream, bn);
+}

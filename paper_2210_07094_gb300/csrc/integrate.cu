@@ -47,7 +47,8 @@ struct IntegArgs {
   int method;
   int32_t* status;
   int32_t* nsub;
-  const int32_t* order;            // optional permutation of cell indices
+  const int32_t* order;            // optional list of the cell indices to advance
+  int64_t nwork;                   // number of cells to advance (entries of order)
   unsigned long long* counters;    // [0] next cell, [1] accepted, [2] rejected
   int stage_blob;                  // 1: copy the blob into shared memory
 };
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
       base = __shfl_sync(FULL, base, leader);
       if (want) {
         const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-        if (idx < (unsigned long long)a.ncells) {
+        if (idx < (unsigned long long)a.nwork) {
           cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
           y[0] = a.T[cell];
           bool ok = isfinite(y[0]) && y[0] > 0.0;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&a.counters[0], 1ull);
     idx = __shfl_sync(WFULL, idx, 0);
-    if (idx >= (unsigned long long)a.ncells) break;
+    if (idx >= (unsigned long long)a.nwork) break;
     const int64_t cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
     bool okin = true;
     for (int i = lane; i < n; i += 32) {
@@ -451,7 +452,7 @@ int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int thr
   if (occ < 1) return set_error(DF_EUNSUPPORTED, "integrator launch shape does not fit on an SM");
   const int per_sm = bps > 0 ? std::min(bps, occ) : occ;
   int64_t blocks = (int64_t)m->num_sms * per_sm;
-  const int64_t need = (a.ncells + threads - 1) / threads;
+  const int64_t need = (a.nwork + threads - 1) / threads;
   if (blocks > need) blocks = std::max<int64_t>(1, need);
   rc = cuda_check(cudaMemsetAsync(m->counters, 0, 4 * sizeof(unsigned long long), st), "reset work counter");
   if (rc) return rc;
@@ -534,7 +535,7 @@ int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, in
   if (rc) return rc;
   if (occ < 1) return set_error(DF_EUNSUPPORTED, "warp integrator does not fit on an SM");
   int64_t blocks = (int64_t)m->num_sms * occ;
-  const int64_t need = (a.ncells + warps - 1) / warps;
+  const int64_t need = (a.nwork + warps - 1) / warps;
   if (blocks > need) blocks = std::max<int64_t>(1, need);
   rc = cuda_check(cudaMemsetAsync(m->counters, 0, 4 * sizeof(unsigned long long), st), "reset work counter");
   if (rc) return rc;
@@ -573,6 +574,12 @@ int launch_jacobian(const df_mech* m, int64_t ncells, const double* T, const dou
 int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, double* Y,
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st) {
+  return launch_integrate_list(m, ncells, T, p, Y, dt, o, status, nsub, nullptr, ncells, st);
+}
+
+int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                          const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
+                          int64_t nwork, cudaStream_t st) {
   int rc = ensure_tables(m->device);
   if (rc) return rc;
   IntegArgs a;
@@ -593,7 +600,8 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
   a.method = o.method;
   a.status = status;
   a.nsub = nsub;
-  a.order = nullptr;
+  a.order = order;
+  a.nwork = nwork;
   a.counters = m->counters;
   const bool thread_ok = has_thread_kernel(m->dims.N);
   if (o.path == 1 && !thread_ok)

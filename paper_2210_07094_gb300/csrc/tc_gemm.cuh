@@ -1,0 +1,262 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05) with
+// TMA loads and the accumulator in tensor memory, for the MLP of the DNN
+// chemistry integrator (Sec. 2.3: a fully connected network with three hidden
+// layers).
+//
+//   C[m, n] = sum_k A[m, k] B[n, k]     A: [M][K], B: [N][K], both K-contiguous
+//
+// One 128 x BN output tile per CTA (4 warps).  Warp 0 lane 0 issues the TMA
+// loads of 128x64 (A) and BNx64 (B) bf16 tiles (128-byte swizzle) into a
+// STAGES-deep ring guarded by mbarriers; warp 1 lane 0 issues tcgen05.mma
+// (M = 128, N = BN, K = 16 per instruction) into a TMEM accumulator of BN fp32
+// columns and releases each ring slot with tcgen05.commit; then all four warps
+// read their 32 TMEM lanes (tcgen05.ld) and run the epilogue.  Every mbarrier
+// wait is bounded: on timeout the kernel records an error code and still frees
+// its tensor memory before it returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace df {
+
+enum EpiMode : int {
+  EPI_F32 = 0,        // out0 f32 [M][ld0] = acc (+ bias)
+  EPI_GELU_BF16 = 1,  // out1 bf16 [M][ld1] = gelu(acc + bias)
+  EPI_TRAIN_FWD = 2,  // out0 f32 Z = acc + bias; out1 bf16 gelu(Z); out2 bf16 gelu(Z)^T [N][ld2]
+  EPI_BWD_DZ = 3,     // dZ = acc * gelu'(aux [M][lda]); out1 bf16 dZ; out2 bf16 dZ^T [N][ld2]
+};
+
+struct GemmParams {
+  int M, N, K;
+  int ldA, ldB;  // leading dimensions (elements) of the A and B operands (0: K)
+  int mode;
+  const float* bias;  // [N] or null
+  const float* aux;   // EPI_BWD_DZ: pre-activation of the layer input
+  int lda;
+  float* out0;
+  __nv_bfloat16* out1;
+  __nv_bfloat16* out2;
+  int ld0, ld1, ld2;
+  int* err;           // device error flag (0 = ok)
+};
+
+constexpr int GEMM_BM = 128;
+constexpr int GEMM_BK = 64;
+constexpr long long GEMM_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase of the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > GEMM_WAIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (tile base 1024-byte aligned)
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmParams P) {
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int A_BYTES = GEMM_BM * GEMM_BK * 2;
+  constexpr int B_BYTES = BN * GEMM_BK * 2;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);  // full[S], empty[S], done
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *tslot;
+  const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
+  const int nk = (P.K + GEMM_BK - 1) / GEMM_BK;
+  bool timed_out = false;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1)) {
+        timed_out = true;
+        break;
+      }
+      mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+      tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, kb * GEMM_BK, m0, full0 + 8 * s);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, kb * GEMM_BK, n0, full0 + 8 * s);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(GEMM_BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(full0 + 8 * s, ph)) {
+        timed_out = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
+        const uint64_t ad = sdesc_sw128(a0 + kk * 32), bd = sdesc_sw128(b0 + kk * 32);
+        const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       empty0 + 8 * s)
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
+                 : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator rows (TMEM lanes) 32w .. 32w + 31
+  const bool ok_done = mbar_wait(done, 0);
+  if (!ok_done) timed_out = true;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+  if (ok_done) {
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+          "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(ta));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int nb = n0 + c0;
+      if (nb >= P.N) continue;
+      const bool rok = row < P.M;
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+      if (P.bias) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += (nb + j < P.N) ? P.bias[nb + j] : 0.0f;
+      }
+      if (P.mode == EPI_F32) {
+        if (rok) {
+          float* o = P.out0 + (size_t)row * P.ld0 + nb;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+      } else {
+        if (P.mode == EPI_TRAIN_FWD && rok) {
+          float* o = P.out0 + (size_t)row * P.ld0 + nb;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (P.mode == EPI_BWD_DZ) {
+          const float* az = P.aux + (size_t)(rok ? row : 0) * P.lda + nb;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = (rok && nb + j < P.N) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = gelu_f(v[j]);
+        }
+        __nv_bfloat16 hb[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) hb[j] = __float2bfloat16_rn(v[j]);
+        if (P.out1 && rok) {
+          __nv_bfloat16* o = P.out1 + (size_t)row * P.ld1 + nb;
+#pragma unroll
+          for (int j = 0; j < 32; j += 8)
+            if (nb + j < P.N) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(hb + j);
+        }
+        if (P.out2 && rok) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (nb + j < P.N) P.out2[(size_t)(nb + j) * P.ld2 + row] = hb[j];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(BN) : "memory");
+  }
+  if (timed_out && P.err) atomicExch(P.err, 1);
+}
+
+}  // namespace df

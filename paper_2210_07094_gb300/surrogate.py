@@ -1,0 +1,105 @@
+"""Training data, training loop and evaluation of the DNN chemistry integrator.
+
+The network learns the map the FP64 integrator computes (Sec. 2.3: the output
+is the change of the Box-Cox-transformed input over one step dt, and the DNN
+"can be regarded as an ODE integrator").  Training pairs are states along
+integrator trajectories started from the uneven-stiffness field (bimodal T,
+p 1-10 atm): each trajectory is advanced dt at a time by df_chem_integrate and
+every (state, next state) pair is kept.  All arithmetic runs in the library's
+kernels; this module only orchestrates calls.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import Dnn, Mechanism, dnn_default_opts, integrate, synth
+
+
+def trajectories(mech: Mechanism, mech_json: dict, n_init: int, n_steps: int, dt: float = 1e-6,
+                 seed: int = synth.TRAIN_SEED, device="cuda"):
+    """States along integrator trajectories: returns device tensors T, p, Y of
+    n_init * (n_steps + 1) states, trajectory-major in time (block s holds step s)."""
+    import torch
+    f = synth.field(1, mech_json, n_init, seed=seed)
+    T = torch.tensor(f["T"], device=device)
+    p = torch.tensor(f["p"], device=device)
+    Y = torch.tensor(f["Y"], device=device)
+    Ts, Ys = [T.clone()], [Y.clone()]
+    for _ in range(n_steps):
+        st, _ = integrate(mech, T, p, Y, dt)
+        if int((st != 0).sum()) != 0:
+            raise RuntimeError("integrator failed while generating training data")
+        Ts.append(T.clone())
+        Ys.append(Y.clone())
+    return Ts, p, Ys
+
+
+def pairs(Ts, p, Ys):
+    """(state, next state) pairs from trajectory blocks: SoA device tensors."""
+    import torch
+    T0 = torch.cat(Ts[:-1])
+    T1 = torch.cat(Ts[1:])
+    P = p.repeat(len(Ts) - 1)
+    Y0 = torch.cat(Ys[:-1], dim=1).contiguous()
+    Y1 = torch.cat(Ys[1:], dim=1).contiguous()
+    return T0, P, Y0, T1, Y1
+
+
+def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, seed=0, time_budget=None,
+          log=None):
+    """Adam with a cosine learning-rate schedule over shuffled mini-batches."""
+    import torch
+    n = T.numel()
+    steps_per_epoch = max(1, n // batch)
+    total = max(1, int(epochs * steps_per_epoch))
+    g = torch.Generator(device=T.device).manual_seed(seed)
+    losses = []
+    t0 = time.time()
+    perm = None
+    for s in range(total):
+        if s % steps_per_epoch == 0:
+            perm = torch.randperm(n, device=T.device, generator=g)
+        idx = perm[(s % steps_per_epoch) * batch:(s % steps_per_epoch + 1) * batch]
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * s / total))
+        want = (s % 50 == 0) or s == total - 1
+        loss = dnn.train_step(T[idx].contiguous(), p[idx].contiguous(), Y[:, idx].contiguous(),
+                              Yn[:, idx].contiguous(), lr, want_loss=want)
+        if want:
+            losses.append((s, loss))
+            if log:
+                log(f"step {s}/{total} lr {lr:.2e} loss {loss:.4e}")
+        if time_budget is not None and time.time() - t0 > time_budget:
+            break
+    return losses
+
+
+def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6):
+    """Per-species error of the network against the integrator on the same states
+    (in-range cells only), and the error of a frozen composition (Y(t+dt) = Y(t))
+    for scale."""
+    import torch
+    Ti, Yi = T.clone(), Y.clone()
+    st, _ = integrate(mech, Ti, p, Yi, dt)
+    Td, Yd = T.clone(), Y.clone()
+    nfb, used, _ = dnn.infer(mech, Td, p, Yd, dt)
+    ok = used == 0
+    err_Y = (Yd - Yi).abs()[:, ok]
+    frozen = (Y - Yi).abs()[:, ok]
+    # coefficient of determination of the predicted change of F(Y) per species
+    lam = 0.1
+    bct = lambda a: (a.clamp(min=0.0) ** lam - 1.0) / lam  # noqa: E731
+    du_t = (bct(Yi) - bct(Y))[:, ok]
+    du_p = (bct(Yd) - bct(Y))[:, ok]
+    var = du_t.var(dim=1)
+    r2 = 1.0 - ((du_p - du_t) ** 2).mean(dim=1) / torch.where(var > 0, var, torch.ones_like(var))
+    return {
+        "r2_dF": r2.cpu().numpy(), "var_dF": var.cpu().numpy(),
+        "n": int(T.numel()), "n_network": int(ok.sum()), "n_fallback": int(nfb),
+        "mae_Y": err_Y.mean(dim=1).cpu().numpy(), "max_Y": err_Y.max(dim=1).values.cpu().numpy(),
+        "mae_T": float((Td - Ti).abs()[ok].mean()), "max_T": float((Td - Ti).abs()[ok].max()),
+        "frozen_mae_Y": frozen.mean(dim=1).cpu().numpy(),
+        "frozen_mae_T": float((T - Ti).abs()[ok].mean()),
+    }
