@@ -106,7 +106,8 @@ def test_adjoint_matches_central_differences(setup):
             mm.A0[j] *= np.exp(sgn * eps)
             tot += sgn * sum(LY(c, np.concatenate([[f["T"][c]], f["Y"][:, c]]), mm) for c in range(n))
         fd = tot / (2 * eps)
-        assert abs(glnA[j] - fd) <= 1e-5 * abs(fd), (j, glnA[j], fd)
+        # rounding noise of the difference: ~ulp(L) * sqrt(cells) / (2 eps) ~ 3e-10
+        assert abs(glnA[j] - fd) <= 1e-5 * abs(fd) + 5e-10, (j, glnA[j], fd)
 
 
 def test_adjoint_deterministic_and_full_size(setup):
@@ -140,12 +141,13 @@ def test_autograd_function(setup):
     # a finite-difference look at the adaptive map itself (its step sequence does
     # not change for a 1e-6 change of ln A on these cells)
     j = int(torch.argmax(lnA.grad.abs()))
+    # (step 1e-4: sum(T) ~ 8e4 K carries ~1e-11 K of rounding, too much for 1e-6)
     vals = []
     for sgn in (1, -1):
         la = lnA.detach().clone()
-        la[j] += sgn * 1e-6
+        la[j] += sgn * 1e-4
         T2, Y2, q2, _ = df.chem_step(m, T0.detach(), p, Y0.detach(), la, f["dt"])
         vals.append((T2.sum() + 1e-9 * q2.sum()).item())
-    fd = (vals[0] - vals[1]) / 2e-6
+    fd = (vals[0] - vals[1]) / 2e-4
     assert abs(fd - lnA.grad[j].item()) <= 1e-3 * abs(fd) + 1e-9
     m.set_lnA(None)
