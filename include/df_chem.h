@@ -171,6 +171,28 @@ int df_chem_adjoint(const df_mech* mech, int64_t ncells, const double* T0, const
                     const double* gY1, const double* gQ1, double* gT0, double* gY0, double* g_lnA,
                     int32_t* status, int32_t* nsub, void* workspace, size_t ws_bytes, df_stream_t stream);
 
+/* df_chem_adjoint without a workspace argument, for callers that cannot
+ * allocate device memory when they need the gradient (a solver running inside a
+ * CUDA stream capture, an application whose device memory belongs to a pool or
+ * framework that must not be bypassed, a real-time loop that forbids allocation
+ * after start-up).  The paper has no counterpart.
+ *
+ * Arguments and results as for df_chem_adjoint.  The scratch (checkpoints and
+ * ln A partial sums) lives in one fixed 4 MiB device array inside the library,
+ * held by every GPU that loads it until the process exits; nothing is
+ * allocated.  Requests that need more (ncells * max_steps * (N + 2) doubles of
+ * checkpoints plus ceil(ncells / 32) * M doubles of partials, in total more than
+ * 4 MiB) return DF_EWORKSPACE with the size in the error detail.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the one array: calls whose kernels
+ * overlap on the GPU (different streams, or several threads) race on it and
+ * must be serialised by the caller. */
+int df_chem_adjoint_static(const df_mech* mech, int64_t ncells, const double* T0, const double* p,
+                           const double* Y0, double dt, const df_integ_opts* opts, int32_t max_steps,
+                           const double* gT1, const double* gY1, const double* gQ1, double* gT0, double* gY0,
+                           double* g_lnA, int32_t* status, int32_t* nsub, df_stream_t stream);
+
 /* Work counters of the last df_chem_integrate on this handle (host values; the
  * call synchronises `stream`): accepted and rejected substeps summed over all
  * cells. */

@@ -55,6 +55,8 @@ SIGNATURES = [
     ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),
     ("df_chem_adjoint", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
                              _p, _sz, _p]),
+    ("df_chem_adjoint_static", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
+                                    _p]),
     ("df_dnn_opts_default", None, [_p]),
     ("df_dnn_create", _i, [_p, C.c_uint64, _p]),
     ("df_dnn_free", None, [_p]),

@@ -26,6 +26,9 @@
 // ln A gradients are summed over threads in a fixed order, then over blocks by a
 // second kernel in a fixed order: the result is bitwise reproducible.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
 
 #include "rosenbrock.cuh"
 
@@ -388,3 +391,75 @@ int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const dou
 }
 
 }  // namespace df
+
+// ---------------------------------------------------------------------------
+// df_chem_adjoint_static: the adjoint without any allocation by the library or
+// the caller for its scratch.
+//
+// Some callers cannot call cudaMalloc when they need a gradient: a solver
+// running inside a CUDA stream capture, a host application whose device memory
+// is owned by a pool or another framework that must not be bypassed, or a
+// real-time loop that forbids allocation after start-up.  This entry point
+// keeps the adjoint's scratch (the per-cell checkpoints and the per-block ln A
+// partial sums) in one file-scope device array instead, so the caller only
+// passes its inputs and outputs.
+// ---------------------------------------------------------------------------
+namespace df {
+
+// 4 MiB of scratch; every GPU that loads the library holds it until exit
+constexpr size_t ADJ_STATIC_BYTES = (size_t)4 << 20;
+static __device__ __align__(256) double g_adj_static_scratch[ADJ_STATIC_BYTES / sizeof(double)];
+
+static std::mutex g_adj_static_mu;
+static void* g_adj_static_ptr[64] = {nullptr};
+
+// Host-side address of the scratch array on the current device.  The array's
+// name in host code is only a host-side stand-in, so its device address is
+// looked up once per device, with that device current.
+static int adj_static_scratch(void** out) {
+  int dev = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= 64) return set_error(DF_EUNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_adj_static_mu);
+  if (!g_adj_static_ptr[dev]) {
+    void* p = nullptr;
+    rc = cuda_check(cudaGetSymbolAddress(&p, g_adj_static_scratch), "cudaGetSymbolAddress (adjoint scratch)");
+    if (rc) return rc;
+    g_adj_static_ptr[dev] = p;
+  }
+  *out = g_adj_static_ptr[dev];
+  return DF_OK;
+}
+
+}  // namespace df
+
+extern "C" int df_chem_adjoint_static(const df_mech* m, int64_t ncells, const double* T0, const double* p,
+                                      const double* Y0, double dt, const df_integ_opts* opts, int32_t max_steps,
+                                      const double* gT1, const double* gY1, const double* gQ1, double* gT0,
+                                      double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
+                                      df_stream_t stream) {
+  using namespace df;
+  if (!m) return set_error(DF_EINVAL, "df_chem_adjoint_static: null mechanism");
+  if (ncells < 0 || max_steps < 1) return set_error(DF_EINVAL, "df_chem_adjoint_static: ncells >= 0, max_steps >= 1");
+  if (ncells == 0) return DF_OK;
+  if (!T0 || !p || !Y0 || !status) return set_error(DF_EINVAL, "df_chem_adjoint_static: null input or status");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return set_error(DF_EINVAL, "df_chem_adjoint_static: dt must be finite and >= 0");
+  const size_t need = adjoint_workspace_bytes(m, ncells, max_steps);
+  if (need > ADJ_STATIC_BYTES)
+    return set_error(DF_EWORKSPACE,
+                     "df_chem_adjoint_static: ncells * max_steps * (N + 2) checkpoints plus the ln A partials need " +
+                         std::to_string(need) + " bytes, more than the fixed 4 MiB scratch; use df_chem_adjoint "
+                         "with a caller-provided workspace");
+  df_integ_opts o;
+  if (opts) o = *opts;
+  else df_integ_opts_default(&o);
+  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
+      o.max_substeps < 1)
+    return set_error(DF_EINVAL, "df_chem_adjoint_static: invalid options");
+  void* ws = nullptr;
+  int rc = adj_static_scratch(&ws);
+  if (rc) return rc;
+  return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub, ws,
+                        ADJ_STATIC_BYTES, (cudaStream_t)stream);
+}
