@@ -150,6 +150,66 @@ def run_reference(args):
     return 0
 
 
+def profile_case(args):
+    """gemm-l2: one launch of the MLP's largest layer (262144 x 800 x 1600, the
+    second hidden layer of an inference chunk) after one warm-up launch.
+    dnn-infer: two inference passes of an (untrained) network over 2^22 cells of
+    the uneven-stiffness field with 2% of them above the training T range."""
+    import ctypes as C
+    import torch
+    from paper_2210_07094_gb300 import _lib
+    if args.profile_case == "dnn-infer":
+        import paper_2210_07094_gb300 as df
+        from paper_2210_07094_gb300 import surrogate, synth
+        mech = synth.h2_air_mechanism()
+        m = df.Mechanism(mech)
+        Ts, p, Ys = surrogate.trajectories(m, mech, 4096, 4)
+        dnn = df.Dnn(df.dnn_default_opts(), seed=1)
+        T0, P0, Y0, T1, Y1 = surrogate.pairs(Ts, p, Ys)
+        dnn.fit_norm(T0, P0, Y0, Y1)
+        f = synth.field(1, mech, 1 << 22, seed=5)
+        T = torch.tensor(f["T"], device="cuda").clamp(float(T0.min()), float(T0.max()))
+        n_oor = (1 << 22) // 50
+        T[:n_oor] = float(T0.max()) + 100.0
+        p = torch.tensor(f["p"], device="cuda")
+        Y = torch.tensor(f["Y"], device="cuda")
+        Tw, Yw = T.clone(), Y.clone()
+        for rep in range(2):
+            Tw.copy_(T)
+            Yw.copy_(Y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            nfb, _, _ = dnn.infer(m, Tw, p, Yw, 1e-6)
+            e1.record()
+            torch.cuda.synchronize()
+            print(json.dumps({"case": "dnn-infer", "rep": rep, "cells": 1 << 22, "n_fallback": nfb,
+                              "ms": e0.elapsed_time(e1)}))
+        return 0
+    M, N, K = 262144, 800, 1600
+    g = torch.Generator(device="cuda").manual_seed(0)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    Cm = torch.empty(M, N, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = _lib.load()
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _lib.check(L.df_probe_gemm_bf16(C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()),
+                                        C.c_void_p(Cm.data_ptr()), M, N, K, 0, C.c_void_p(err.data_ptr()), st),
+                   "df_probe_gemm_bf16")
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = min(times[1:])
+    print(json.dumps({"case": "gemm-l2", "M": M, "N": N, "K": K, "ms": ms,
+                      "tflops": 2.0 * M * N * K / (ms * 1e-3) / 1e12, "err": int(err.item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,11 +219,17 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=4096)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dnn", action="store_true", help="skip the learned-surrogate workload")
+    ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
+    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer"],
+                    help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
 
     import torch
     import paper_2210_07094_gb300 as df
@@ -297,6 +363,13 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
+    if rank == 0 and not args.no_dnn and ncells == NCELLS:
+        # learned surrogate (BF16 tensor-core MLP) on the same GPU and cell distribution
+        from paper_2210_07094_gb300 import surrogate
+        dn = surrogate.experiment(mech, train_seconds=args.dnn_train_seconds)
+        flop_cell = 2 * (16 * 1600 + 1600 * 800 + 800 * 400 + 400 * 16)
+        dn["mlp_tflops_achieved"] = flop_cell * dn["infer_cells_per_s"] / 1e12
+        line["dnn"] = dn
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample, os.cpu_count() or 1)
     if rank == 0:

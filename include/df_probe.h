@@ -26,7 +26,8 @@ int df_probe_exp(const double* x, double* y, long long n, void* stream);
  * integrator's layers), FP32 result without bias or activation, so that it can be
  * checked against a reference matmul.  A [M][K], B [N][K] bf16 (device, 16-byte
  * aligned, K a multiple of 8), C [M][N] f32 (device), N a multiple of 8; bn: output
- * tile width 64, 128 or 256 (0 = choose).  err_flag (device int, may be NULL) is
+ * tile width 64, 128 or 256 of the one-tile-per-CTA kernel, or -128, -160, -208,
+ * -256 for the persistent kernel with a double-buffered accumulator (0 = choose).  err_flag (device int, may be NULL) is
  * set to 1 if a bounded pipeline wait ran out.  Asynchronous on `stream`. */
 int df_probe_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int bn, int* err_flag,
                        void* stream);

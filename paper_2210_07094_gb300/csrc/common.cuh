@@ -110,9 +110,11 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st);
 int launch_set_lnA(df_mech* m, const double* lnA, cudaStream_t st);
+// advance the cells order[0 .. nwork) (nwork read from nwork_dev on the device
+// when given; nwork is then an upper bound used to size the launch)
 int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
                           const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
-                          int64_t nwork, cudaStream_t st);
+                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev = nullptr);
 
 // adjoint (adjoint.cu)
 size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap);

@@ -75,10 +75,15 @@ struct df_dnn {
   __nv_bfloat16 *iX = nullptr, *iH[3] = {nullptr, nullptr, nullptr};
   float* iU = nullptr;
   int32_t* imask = nullptr;
-  // fallback list and status scratch (grown on demand)
+  double* iYl = nullptr;  // [16][chunk] Y^lambda of the chunk (features -> post)
+  double* rawb = nullptr;  // raw-variable range bounds: lo[16], hi[16] (T, p, Y_k)
+  // fallback list, per-cell flags and status scratch (grown on demand)
   int64_t list_cap = 0;
   int32_t* list = nullptr;
   int32_t* fb_status = nullptr;
+  uint8_t* fb_flag = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_ranged = nullptr, ev_fallback = nullptr;
   unsigned long long* counter = nullptr;
   int* err = nullptr;
 };
@@ -150,6 +155,8 @@ struct FeatArgs {
   int64_t ldT;
   float* tgt;         // [n][16] or null (normalised change of F(Y))
   int32_t* mask;      // [n] in-range flag or null
+  double* Yl;         // [N][ldYl] Y^lambda (FP64) or null
+  int64_t ldYl;
 };
 
 __global__ void k_dnn_features(FeatArgs a) {
@@ -174,6 +181,7 @@ __global__ void k_dnn_features(FeatArgs a) {
   for (int k = 0; k < a.N; ++k) {
     yl[k] = ylam(a.Y[(int64_t)k * a.ncells + c], a.lam, tab);
     f[2 + k] = (float)((yl[k] - 1.0) / a.lam);
+    if (a.Yl) a.Yl[(int64_t)k * a.ldYl + i] = yl[k];
   }
   bool in_range = true;
   __nv_bfloat16 xb[DNN_IN];
@@ -204,6 +212,24 @@ __global__ void k_dnn_features(FeatArgs a) {
       t[k] = (float)((du - mean_out[k]) / std_out[k]);
     }
   }
+}
+
+// Training-range test on the raw variables: the Box-Cox transform is monotonic,
+// so [min, max] of F(Y_k) maps to bounds on Y_k; cells outside any bound are
+// flagged and appended to the fallback list (one atomic per cell outside).
+__global__ void k_dnn_range(int64_t ncells, int N, const double* T, const double* p, const double* Y,
+                            const double* rawb, uint8_t* flag, int32_t* list, unsigned long long* counter) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const double* lo = rawb;
+  const double* hi = rawb + DNN_IN;
+  bool in = T[c] >= lo[0] && T[c] <= hi[0] && p[c] >= lo[1] && p[c] <= hi[1];
+  for (int k = 0; k < N; ++k) {
+    const double y = fmax(Y[(int64_t)k * ncells + c], 0.0);
+    in = in && y >= lo[2 + k] && y <= hi[2 + k];
+  }
+  flag[c] = in ? 0 : 1;
+  if (!in) list[atomicAdd(counter, 1ull)] = (int32_t)c;
 }
 
 // zero the rows [n, nrows) of a padded batch (features and their transpose)
@@ -295,7 +321,9 @@ struct PostArgs {
   double* Y;
   const float* U;  // [n][16] normalised network output
   const float* norm;
-  const int32_t* mask;
+  const uint8_t* flag;  // [ncells] 1: advanced by the fallback
+  const double* Yl;     // [N][ldYl] Y^lambda of the chunk
+  int64_t ldYl;
   int32_t* used_fallback;
   int32_t* status;
   int32_t* list;
@@ -321,9 +349,7 @@ __global__ void k_dnn_post(PostArgs a) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const int64_t c = a.c0 + i;
-  if (!a.mask[i]) {
-    const unsigned long long s = atomicAdd(a.counter, 1ull);
-    a.list[s] = (int32_t)c;
+  if (a.flag[c]) {
     if (a.used_fallback) a.used_fallback[c] = 1;
     return;
   }
@@ -335,7 +361,8 @@ __global__ void k_dnn_post(PostArgs a) {
   for (int k = 0; k < a.N; ++k) {
     const double y = a.Y[(int64_t)k * a.ncells + c];
     const double u = (double)a.U[i * DNN_OUT + k] * std_out[k] + mean_out[k];
-    const double z = ylam(y, a.lam, tab) + a.lam * u;  // lambda F(Y') + 1
+    const double z = a.Yl[(int64_t)k * a.ldYl + i] + a.lam * u;  // lambda F(Y') + 1
+    (void)y;
     const double yn = z > 0.0 ? ipow(z, a.inv_lam) : 0.0;
     Yn[k] = yn;
     s += yn;
@@ -371,9 +398,11 @@ __global__ void k_dnn_post(PostArgs a) {
   if (a.status) a.status[c] = DF_CELL_OK;
 }
 
-__global__ void k_copy_status(const int32_t* list, int64_t n, const int32_t* src, int32_t* dst) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[list[i]] = src[list[i]];
+__global__ void k_copy_status(const int32_t* list, const unsigned long long* count, const int32_t* src,
+                              int32_t* dst) {
+  const int64_t n = (int64_t)*count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[list[i]] = src[list[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -487,6 +516,7 @@ static int dnn_alloc(df_dnn* d) {
     if (!rc) rc = dev_alloc((void**)&d->wtb[l], n * 2);
   }
   rc = rc ? rc : dev_alloc((void**)&d->norm, sizeof(d->norm_host));
+  rc = rc ? rc : dev_alloc((void**)&d->rawb, 2 * DNN_IN * sizeof(double));
   rc = rc ? rc : dev_alloc((void**)&d->counter, 16);
   rc = rc ? rc : dev_alloc((void**)&d->err, 16);
   if (rc) return rc;
@@ -527,8 +557,47 @@ static int dnn_infer_buffers(df_dnn* d) {
   int rc = dev_alloc((void**)&d->iX, C * DNN_IN * 2);
   for (int l = 0; l < 3 && !rc; ++l) rc = dev_alloc((void**)&d->iH[l], C * d->L.w[l] * 2);
   rc = rc ? rc : dev_alloc((void**)&d->iU, C * DNN_OUT * 4);
-  rc = rc ? rc : dev_alloc((void**)&d->imask, C * 4);
+  rc = rc ? rc : dev_alloc((void**)&d->iYl, C * DNN_OUT * 8);
+  if (!rc && !d->side)
+    rc = cuda_check(cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking), "fallback stream");
+  if (!rc && !d->ev_ranged) rc = cuda_check(cudaEventCreateWithFlags(&d->ev_ranged, cudaEventDisableTiming), "event");
+  if (!rc && !d->ev_fallback)
+    rc = cuda_check(cudaEventCreateWithFlags(&d->ev_fallback, cudaEventDisableTiming), "event");
   return rc;
+}
+
+// Bounds of the raw variables equivalent to the feature range [in_min, in_max]
+// widened by range_margin: T and p directly, Y_k through the inverse Box-Cox
+// transform F^{-1}(z) = max(1 + lambda z, 0)^{1/lambda} (monotonic).
+static int update_raw_bounds(df_dnn* d) {
+  double b[2 * DNN_IN];
+  const float* lo = d->norm_host + 2 * DNN_IN;
+  const float* hi = d->norm_host + 3 * DNN_IN;
+  const double lam = d->o.lambda, mg = d->o.range_margin;
+  for (int k = 0; k < DNN_IN; ++k) {
+    // the bounds are stored in FP32: widen each by one FP32 ulp so a training
+    // value that the rounding moved past its bound still counts as inside
+    double l = std::nextafter(lo[k], -INFINITY), h = std::nextafter(hi[k], INFINITY);
+    if (std::isfinite(l) && std::isfinite(h)) {
+      const double w = h - l;
+      l -= mg * w;
+      h += mg * w;
+    }
+    if (k >= 2) {
+      auto inv = [&](double z) -> double {
+        if (z == INFINITY) return INFINITY;
+        const double a = 1.0 + lam * z;
+        return a > 0.0 ? std::pow(a, 1.0 / lam) : 0.0;
+      };
+      const double yl = inv(l), yh = inv(h);
+      // a lower bound at F(0) = -1/lambda admits Y = 0 exactly
+      l = (1.0 + lam * l <= 0.0) ? -INFINITY : yl;
+      h = yh;
+    }
+    b[k] = l;
+    b[DNN_IN + k] = h;
+  }
+  return cuda_check(cudaMemcpy(d->rawb, b, sizeof(b), cudaMemcpyHostToDevice), "range bounds");
 }
 
 static int gemm(df_dnn* d, const void* A, int ldA, const void* B, int ldB, int M, int N, int K, int mode,
@@ -583,10 +652,6 @@ static int check_err_flag(df_dnn* d, cudaStream_t st) {
   }
   return rc;
 }
-
-int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
-                          const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
-                          int64_t nwork, cudaStream_t st);
 
 }  // namespace df
 
@@ -658,6 +723,7 @@ int df_dnn_create(const df_dnn_opts* opts, uint64_t seed, df_dnn** out) {
   }
   if (!rc)
     rc = cuda_check(cudaMemcpy(d->norm, d->norm_host, sizeof(d->norm_host), cudaMemcpyHostToDevice), "norm");
+  if (!rc) rc = update_raw_bounds(d);
   if (!rc) rc = cuda_check(cudaDeviceSynchronize(), "DNN create");
   if (rc) {
     df_dnn_free(d);
@@ -670,7 +736,11 @@ int df_dnn_create(const df_dnn_opts* opts, uint64_t seed, df_dnn** out) {
 void df_dnn_free(df_dnn* d) {
   if (!d) return;
   void* ptrs[] = {d->params, d->m1, d->m2, d->grads, d->norm, d->X, d->XT, d->U, d->tgt, d->dU, d->dUT,
-                  d->loss_part, d->iX, d->iU, d->imask, d->list, d->fb_status, d->counter, d->err};
+                  d->loss_part, d->iX, d->iU, d->imask, d->list, d->fb_status, d->counter, d->err, d->iYl,
+                  d->rawb, d->fb_flag};
+  if (d->side) cudaStreamDestroy(d->side);
+  if (d->ev_ranged) cudaEventDestroy(d->ev_ranged);
+  if (d->ev_fallback) cudaEventDestroy(d->ev_fallback);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int l = 0; l < 4; ++l) {
@@ -699,7 +769,9 @@ int df_dnn_set_norm(df_dnn* d, const float* mean_in, const float* std_in, const 
       d->norm_host[off[a] + k] = src[a][k];
     }
   }
-  return cuda_check(cudaMemcpy(d->norm, d->norm_host, sizeof(d->norm_host), cudaMemcpyHostToDevice), "norm");
+  int rc = cuda_check(cudaMemcpy(d->norm, d->norm_host, sizeof(d->norm_host), cudaMemcpyHostToDevice), "norm");
+  if (!rc) rc = update_raw_bounds(d);
+  return rc;
 }
 
 int df_dnn_get_norm(const df_dnn* d, float* mean_in, float* std_in, float* mean_out, float* std_out,
@@ -729,6 +801,7 @@ int df_dnn_fit_norm(df_dnn* d, int64_t n, const double* T, const double* p, cons
                     "read norm");
   cudaFreeAsync(part, st);
   if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "synchronise");
+  if (!rc) rc = update_raw_bounds(d);
   return rc;
 }
 
@@ -842,15 +915,38 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
   if (d->list_cap < ncells) {
     if (d->list) cudaFree(d->list);
     if (d->fb_status) cudaFree(d->fb_status);
+    if (d->fb_flag) cudaFree(d->fb_flag);
     d->list = nullptr;
     d->fb_status = nullptr;
+    d->fb_flag = nullptr;
     rc = dev_alloc((void**)&d->list, ncells * 4);
     if (!rc) rc = dev_alloc((void**)&d->fb_status, ncells * 4);
+    if (!rc) rc = dev_alloc((void**)&d->fb_flag, ncells);
     if (rc) return rc;
     d->list_cap = ncells;
   }
+  // 1. training-range test over all cells -> fallback list (device count)
   rc = cuda_check(cudaMemsetAsync(d->counter, 0, 8, st), "reset fallback counter");
   if (rc) return rc;
+  k_dnn_range<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(ncells, d->o.n_species, T, p, Y, d->rawb,
+                                                                d->fb_flag, d->list, d->counter);
+  rc = cuda_check(cudaGetLastError(), "range kernel");
+  // 2. the FP64 integrator advances the fallback cells on a side stream (its
+  //    work count stays on the device); the network runs on the caller's stream
+  df_integ_opts o;
+  if (fopts) o = *fopts;
+  else df_integ_opts_default(&o);
+  if (!rc) rc = cuda_check(cudaEventRecord(d->ev_ranged, st), "event");
+  if (!rc) rc = cuda_check(cudaStreamWaitEvent(d->side, d->ev_ranged, 0), "event wait");
+  if (!rc)
+    rc = launch_integrate_list(m, ncells, T, p, Y, dt, o, d->fb_status, nullptr, d->list, ncells, d->side,
+                               d->counter);
+  if (!rc && status) {
+    k_copy_status<<<256, 256, 0, d->side>>>(d->list, d->counter, d->fb_status, status);
+    rc = cuda_check(cudaGetLastError(), "fallback status copy");
+  }
+  if (!rc) rc = cuda_check(cudaEventRecord(d->ev_fallback, d->side), "event");
+  // 3. the network on the other cells, chunk by chunk
   const int inv = (int)std::lround(1.0 / d->o.lambda);
   for (int64_t c0 = 0; c0 < ncells && !rc; c0 += d->chunk) {
     const int64_t nc = std::min<int64_t>(d->chunk, ncells - c0);
@@ -865,9 +961,9 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
     fa.p = p;
     fa.Y = Y;
     fa.norm = d->norm;
-    fa.margin = (float)d->o.range_margin;
     fa.X = d->iX;
-    fa.mask = d->imask;
+    fa.Yl = d->iYl;
+    fa.ldYl = d->chunk;
     k_dnn_features<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(fa);
     rc = dnn_forward_infer(d, d->iX, nc, d->iU, st);
     if (rc) break;
@@ -886,31 +982,22 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
     pa.Y = Y;
     pa.U = d->iU;
     pa.norm = d->norm;
-    pa.mask = d->imask;
+    pa.flag = d->fb_flag;
+    pa.Yl = d->iYl;
+    pa.ldYl = d->chunk;
     pa.used_fallback = used_fallback;
     pa.status = status;
-    pa.list = d->list;
-    pa.counter = d->counter;
     k_dnn_post<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(pa);
     rc = cuda_check(cudaGetLastError(), "DNN pre/post kernels");
   }
-  if (rc) return rc;
+  // 4. join the fallback, report the count
+  if (!rc) rc = cuda_check(cudaStreamWaitEvent(st, d->ev_fallback, 0), "event wait");
   unsigned long long nfb = 0;
-  rc = cuda_check(cudaMemcpyAsync(&nfb, d->counter, 8, cudaMemcpyDeviceToHost, st), "read fallback count");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(&nfb, d->counter, 8, cudaMemcpyDeviceToHost, st), "read fallback count");
   if (!rc) rc = check_err_flag(d, st);
   if (rc) return rc;
   if (n_fallback) *n_fallback = (int64_t)nfb;
-  if (nfb > 0) {
-    df_integ_opts o;
-    if (fopts) o = *fopts;
-    else df_integ_opts_default(&o);
-    rc = launch_integrate_list(m, ncells, T, p, Y, dt, o, d->fb_status, nullptr, d->list, (int64_t)nfb, st);
-    if (!rc && status) {
-      k_copy_status<<<(unsigned)((nfb + 255) / 256), 256, 0, st>>>(d->list, (int64_t)nfb, d->fb_status, status);
-      rc = cuda_check(cudaGetLastError(), "fallback status copy");
-    }
-  }
-  return rc;
+  return DF_OK;
 }
 
 int64_t df_dnn_param_count(const df_dnn* d) { return d ? d->L.total : 0; }
@@ -969,6 +1056,7 @@ int df_dnn_load(const char* path, df_dnn** out) {
     if (!rc) {
       memcpy(d->norm_host, norm, sizeof(norm));
       rc = cuda_check(cudaMemcpy(d->norm, d->norm_host, sizeof(norm), cudaMemcpyHostToDevice), "norm");
+      if (!rc) rc = update_raw_bounds(d);
     }
   }
   fclose(f);

@@ -3,6 +3,9 @@
 // driver library) and the launch.
 #include <cuda.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "common.cuh"
 #include "gemm_host.cuh"
 #include "tc_gemm.cuh"
@@ -78,11 +81,63 @@ static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cud
   return cuda_check(cudaGetLastError(), "GEMM launch");
 }
 
+constexpr int PERS_STAGES = 4;
+
+template <int BN>
+static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
+  if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
+  if (rc) return rc;
+  auto kf = k_gemm_tc_pers<BN, PERS_STAGES>;
+  const size_t sm = (size_t)PERS_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
+  static int nsm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return set_error(DF_EUNSUPPORTED, "device index out of range");
+  if (!nsm[dev]) {
+    rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                    "set GEMM shared memory");
+    if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev), "SM count");
+    if (rc) {
+      nsm[dev] = 0;
+      return rc;
+    }
+  }
+  const int64_t tiles = (int64_t)((P.M + GEMM_BM - 1) / GEMM_BM) * ((P.N + BN - 1) / BN);
+  const int grid = (int)std::min<int64_t>(tiles, nsm[dev]);
+  kf<<<grid, 192, sm, st>>>(ta, tb, P);
+  return cuda_check(cudaGetLastError(), "persistent GEMM launch");
+}
+
+// tile width for the persistent kernel: least padding of N, then the wider tile
+static int pick_bn(int N) {
+  const int cand[4] = {256, 208, 160, 128};
+  int best = 128;
+  int64_t best_pad = INT64_MAX;
+  for (int c : cand) {
+    const int64_t pad = (int64_t)((N + c - 1) / c) * c - N;
+    if (pad < best_pad) {
+      best_pad = pad;
+      best = c;
+    }
+  }
+  return best;
+}
+
 int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st, int bn) {
   if (P.M < 1 || P.N < 1 || P.K < 1 || (P.N % 8) != 0)
     return set_error(DF_EINVAL, "GEMM sizes: M, N, K >= 1 and N a multiple of 8");
-  if (bn == 0) bn = P.N <= 64 ? 64 : 128;
+  if (bn == 0) bn = P.N <= 64 ? 64 : (P.M >= 1024 ? -pick_bn(P.N) : 128);
   switch (bn) {
+    case -128:
+      return gemm_launch_pers<128>(A, B, P, st);
+    case -160:
+      return gemm_launch_pers<160>(A, B, P, st);
+    case -208:
+      return gemm_launch_pers<208>(A, B, P, st);
+    case -256:
+      return gemm_launch_pers<256>(A, B, P, st);
     case 64:
       return gemm_launch_bn<64>(A, B, P, st);
     case 128:
@@ -90,7 +145,7 @@ int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st
     case 256:
       return gemm_launch_bn<256>(A, B, P, st);
     default:
-      return set_error(DF_EINVAL, "GEMM tile width must be 64, 128 or 256");
+      return set_error(DF_EINVAL, "GEMM tile width must be 64, 128, 256 or (persistent) -128, -160, -208, -256");
   }
 }
 

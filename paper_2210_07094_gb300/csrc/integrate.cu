@@ -49,6 +49,7 @@ struct IntegArgs {
   int32_t* nsub;
   const int32_t* order;            // optional list of the cell indices to advance
   int64_t nwork;                   // number of cells to advance (entries of order)
+  const unsigned long long* nwork_dev;  // if set, the number of cells is read from here
   unsigned long long* counters;    // [0] next cell, [1] accepted, [2] rejected
   int stage_blob;                  // 1: copy the blob into shared memory
 };
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   SV Kv{ws + (5 * NS + n * n) * stride, stride};
   const RosTab& tb = c_tab[a.method];
   const int lane = tid & 31;
+  const unsigned long long nwork = a.nwork_dev ? *a.nwork_dev : (unsigned long long)a.nwork;
 
   int64_t cell = -1;
   bool exhausted = false, done = false, last_rej = false;
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
       base = __shfl_sync(FULL, base, leader);
       if (want) {
         const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-        if (idx < (unsigned long long)a.nwork) {
+        if (idx < nwork) {
           cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
           y[0] = a.T[cell];
           bool ok = isfinite(y[0]) && y[0] > 0.0;
@@ -262,12 +264,13 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
   int* piv = reinterpret_cast<int*>(ws + L.piv);
   const RosTab& tb = c_tab[a.method];
   unsigned long long tot_acc = 0, tot_rej = 0;
+  const unsigned long long nwork = a.nwork_dev ? *a.nwork_dev : (unsigned long long)a.nwork;
 
   for (;;) {
     unsigned long long idx = 0;
     if (lane == 0) idx = atomicAdd(&a.counters[0], 1ull);
     idx = __shfl_sync(WFULL, idx, 0);
-    if (idx >= (unsigned long long)a.nwork) break;
+    if (idx >= nwork) break;
     const int64_t cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
     bool okin = true;
     for (int i = lane; i < n; i += 32) {
@@ -574,12 +577,12 @@ int launch_jacobian(const df_mech* m, int64_t ncells, const double* T, const dou
 int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, double* Y,
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st) {
-  return launch_integrate_list(m, ncells, T, p, Y, dt, o, status, nsub, nullptr, ncells, st);
+  return launch_integrate_list(m, ncells, T, p, Y, dt, o, status, nsub, nullptr, ncells, st, nullptr);
 }
 
 int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
                           const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
-                          int64_t nwork, cudaStream_t st) {
+                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev) {
   int rc = ensure_tables(m->device);
   if (rc) return rc;
   IntegArgs a;
@@ -602,6 +605,7 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   a.nsub = nsub;
   a.order = order;
   a.nwork = nwork;
+  a.nwork_dev = nwork_dev;
   a.counters = m->counters;
   const bool thread_ok = has_thread_kernel(m->dims.N);
   if (o.path == 1 && !thread_ok)

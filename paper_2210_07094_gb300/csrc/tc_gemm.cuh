@@ -260,3 +260,218 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 }  // namespace df
+
+namespace df {
+
+// ---------------------------------------------------------------------------
+// Persistent variant: one CTA per SM walks the output tiles (tile t = blockIdx.x
+// + j * gridDim.x, row-block major so consecutive tiles share their A rows in
+// L2).  Six warps: warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
+// warp 1 lane 0 issues tcgen05.mma into one of TWO TMEM accumulators (tile j
+// uses buffer j & 1), warps 2..5 drain the other accumulator through the
+// epilogue, so the epilogue of tile j overlaps the MMAs of tile j + 1.
+// BN is any multiple of 16 up to 256 (the epilogue reads TMEM 16 columns at
+// a time).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN>
+__device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint32_t (&r)[16], int row, int nb) {
+  if (nb >= P.N) return;
+  const bool rok = row < P.M;
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  if (P.bias) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
+  }
+  if (P.mode == EPI_F32) {
+    if (rok) {
+      float* o = P.out0 + (size_t)row * P.ld0 + nb;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4)
+        if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+    return;
+  }
+  if (P.mode == EPI_TRAIN_FWD && rok) {
+    float* o = P.out0 + (size_t)row * P.ld0 + nb;
+#pragma unroll
+    for (int j = 0; j < 16; j += 4)
+      if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+  }
+  if (P.mode == EPI_BWD_DZ) {
+    const float* az = P.aux + (size_t)(rok ? row : 0) * P.lda + nb;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = (rok && nb + j < P.N) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
+  }
+  __nv_bfloat16 hb[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) hb[j] = __float2bfloat16_rn(v[j]);
+  if (P.out1 && rok) {
+    __nv_bfloat16* o = P.out1 + (size_t)row * P.ld1 + nb;
+#pragma unroll
+    for (int j = 0; j < 16; j += 8)
+      if (nb + j < P.N) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(hb + j);
+  }
+  if (P.out2 && rok) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (nb + j < P.N) P.out2[(size_t)(nb + j) * P.ld2 + row] = hb[j];
+  }
+}
+
+template <int BN>
+__host__ __device__ constexpr int tmem_cols_for() {
+  return (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tc_pers(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmParams P) {
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tile width");
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int A_BYTES = GEMM_BM * GEMM_BK * 2;
+  constexpr int B_BYTES = BN * GEMM_BK * 2;
+  static_assert(B_BYTES % 1024 == 0, "B tile must keep 1024-byte alignment");
+  constexpr int TCOLS = tmem_cols_for<BN>();
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);  // full[S] empty[S] accf[2] acce[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = *tslot;
+  const int nM = (P.M + GEMM_BM - 1) / GEMM_BM, nN = (P.N + BN - 1) / BN;
+  const int ntiles = nM * nN;
+  const int nk = (P.K + GEMM_BK - 1) / GEMM_BK;
+  bool timed_out = false;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int kc = 0;
+      for (int t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x) {
+        const int m0 = (t / nN) * GEMM_BM, n0 = (t % nN) * BN;
+        for (int kb = 0; kb < nk; ++kb, ++kc) {
+          const int s = kc % STAGES;
+          const uint32_t ph = (kc / STAGES) & 1;
+          if (kc >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1)) {
+            timed_out = true;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+          tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, kb * GEMM_BK, m0, full0 + 8 * s);
+          tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, kb * GEMM_BK, n0, full0 + 8 * s);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(GEMM_BM, BN);
+      int kc = 0, i = 0;
+      for (int t = blockIdx.x; t < ntiles && !timed_out; t += gridDim.x, ++i) {
+        const int b = i & 1, u = i >> 1;
+        if (u >= 1 && !mbar_wait(acce0 + 8 * b, (u - 1) & 1)) {
+          timed_out = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = taddr + (uint32_t)(b * BN);
+        for (int kb = 0; kb < nk; ++kb, ++kc) {
+          const int s = kc % STAGES;
+          const uint32_t ph = (kc / STAGES) & 1;
+          if (!mbar_wait(full0 + 8 * s, ph)) {
+            timed_out = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < GEMM_BK / 16; ++kk) {
+            const uint64_t ad = sdesc_sw128(a0 + kk * 32), bd = sdesc_sw128(b0 + kk * 32);
+            const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           empty0 + 8 * s)
+                       : "memory");
+        }
+        if (timed_out) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         accf0 + 8 * b)
+                     : "memory");
+      }
+    }
+  } else {
+    // epilogue warps 2..5 cover TMEM lane quarters (warp % 4)
+    const int q = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int b = i & 1, u = i >> 1;
+      if (!mbar_wait(accf0 + 8 * b, u & 1)) {
+        timed_out = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (t / nN) * GEMM_BM, n0 = (t % nN) * BN;
+      const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t ta = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        gemm_epilogue_16<BN>(P, r, row, n0 + c0);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce0 + 8 * b);
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS) : "memory");
+  }
+  if (timed_out && P.err) atomicExch(P.err, 1);
+}
+
+}  // namespace df

@@ -103,3 +103,101 @@ def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6):
         "frozen_mae_Y": frozen.mean(dim=1).cpu().numpy(),
         "frozen_mae_T": float((T - Ti).abs()[ok].mean()),
     }
+
+
+def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22, oor_frac=0.02,
+               train_seconds=60.0, batch=4096, reps=3, seed=synth.TRAIN_SEED, log=None):
+    """Learned-surrogate workload: train on integrator trajectories of the
+    uneven-stiffness field, then advance n_eval held-out trajectory states (with
+    a fraction moved above the training temperature range) by the network and,
+    for comparison, by the integrator.  Returns throughput and error figures."""
+    import torch
+
+    def ev_time(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            fn(e0, e1)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    m = Mechanism(mech_json)
+    t0 = time.time()
+    Ts, p, Ys = trajectories(m, mech_json, n_train_init, n_steps, seed=seed)
+    T0, P0, Y0, T1, Y1 = pairs(Ts, p, Ys)
+    del Ts, Ys
+    t_data = time.time() - t0
+    o = dnn_default_opts()
+    o.batch = batch
+    dnn = Dnn(o, seed=seed)
+    dnn.fit_norm(T0, P0, Y0, Y1)
+    t1 = time.time()
+    losses = train(dnn, T0, P0, Y0, Y1, epochs=10_000, batch=batch, time_budget=train_seconds, log=log)
+    t_train = time.time() - t1
+    n_pairs = T0.numel()
+    del T0, P0, Y0, T1, Y1
+    # held-out states: other trajectories, all their time levels
+    n_init = max(1, n_eval // n_steps)
+    Ts, p, Ys = trajectories(m, mech_json, n_init, n_steps - 1, seed=seed + 1000)
+    Te = torch.cat(Ts)[:n_eval].contiguous()
+    Pe = p.repeat(n_steps)[:n_eval].contiguous()
+    Ye = torch.cat(Ys, dim=1)[:, :n_eval].contiguous()
+    del Ts, Ys
+    n_eval = Te.numel()
+    g = torch.Generator(device=Te.device).manual_seed(seed + 7)
+    n_oor = int(round(oor_frac * n_eval))
+    oor = torch.randperm(n_eval, device=Te.device, generator=g)[:n_oor]
+    # half of them 50-300 K below the training T range, half 50-300 K above it
+    nm = dnn.norm()
+    t_lo, t_hi = float(nm["in_min"][0]), float(nm["in_max"][0])
+    off = 50.0 + 250.0 * torch.rand(n_oor, device=Te.device, generator=g, dtype=torch.float64)
+    half = n_oor // 2
+    Te[oor[:half]] = t_lo - off[:half]
+    Te[oor[half:]] = t_hi + off[half:]
+    # accuracy: network vs integrator on the same states
+    ev = evaluate(dnn, m, Te, Pe, Ye)
+    # throughput: network (incl. pre/post and fallback) and integrator, same cells
+    Tw, Yw = Te.clone(), Ye.clone()
+
+    def run_dnn(e0, e1):
+        Tw.copy_(Te)
+        Yw.copy_(Ye)
+        e0.record()
+        dnn.infer(m, Tw, Pe, Yw, 1e-6)
+        e1.record()
+
+    def run_int(e0, e1):
+        Tw.copy_(Te)
+        Yw.copy_(Ye)
+        e0.record()
+        integrate(m, Tw, Pe, Yw, 1e-6)
+        e1.record()
+
+    run_dnn(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))  # warm-up
+    ms_dnn = ev_time(run_dnn, reps)
+    ms_int = ev_time(run_int, reps)
+    acc, rej = m.last_stats()
+    r2 = ev["r2_dF"][ev["var_dF"] > 0]
+    return {
+        "workload": f"train on {n_pairs} integrator pairs ({n_train_init} trajectories x {n_steps} steps of "
+                    f"dt=1us); infer {n_eval} held-out trajectory states, {n_oor} moved outside the training "
+                    f"T range (half below, half above)",
+        "train": {"seconds": t_train, "steps": losses[-1][0] + 1 if losses else 0, "batch": batch,
+                  "loss_first": losses[0][1] if losses else None, "loss_last": losses[-1][1] if losses else None,
+                  "data_seconds": t_data},
+        "infer_cells_per_s": n_eval / (ms_dnn * 1e-3),
+        "integrator_cells_per_s": n_eval / (ms_int * 1e-3),
+        "speedup_vs_integrator": ms_int / ms_dnn,
+        "ms_infer": ms_dnn, "ms_integrator": ms_int,
+        "n_fallback": ev["n_fallback"], "n_injected_out_of_range": n_oor,
+        "error_vs_integrator": {
+            "mae_Y_per_species": [float(x) for x in ev["mae_Y"]],
+            "max_Y_per_species": [float(x) for x in ev["max_Y"]],
+            "mae_T_K": ev["mae_T"], "max_T_K": ev["max_T"],
+            "r2_dF_mean_reacting": float(np.mean(r2)) if r2.size else None,
+            "frozen_composition_mae_Y": [float(x) for x in ev["frozen_mae_Y"]],
+        },
+        "integrator_substeps_per_cell": (acc + rej) / n_eval,
+    }

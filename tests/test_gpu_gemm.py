@@ -10,6 +10,9 @@ pytestmark = pytest.mark.gpu
 SHAPES = [  # (M, N, K, bn)
     (128, 128, 64, 128), (128, 64, 64, 64), (300, 200, 160, 128), (4096, 1600, 16, 128),
     (1000, 800, 1600, 128), (16, 400, 4096, 128), (257, 16, 400, 64), (777, 512, 200, 256),
+    # persistent kernel, double-buffered accumulator: several tiles per CTA, ragged edges
+    (128, 160, 64, -160), (3000, 800, 1600, -160), (5000, 1600, 16, -160), (2049, 400, 800, -208),
+    (4096, 512, 256, -256), (999, 384, 72, -128), (40000, 800, 1600, -160),
 ]
 
 
