@@ -69,7 +69,9 @@ typedef struct df_integ_opts {
   int32_t method;       /* 0: RODAS4 (Hairer & Wanner), 1: RODAS3 (Sandu 1997) */
   int32_t block_threads;  /* 0: autotune; else threads per block               */
   int32_t blocks_per_sm;  /* 0: autotune; else resident blocks per SM          */
-  int32_t order_by_T;     /* 1: hand out hot cells first (longest-work first)  */
+  int32_t order_by_T;     /* 1 (default): hand out cells hottest first (a device
+                             counting sort; longest work first, lanes refilled
+                             together get cells of similar stiffness)          */
   int32_t path;           /* 0: auto (thread per cell if N <= 16), 1: thread per
                              cell, 2: warp per cell                            */
   int32_t reserved[2];

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
     double t = 0.0, h = fmin(a.h0, a.dt);
     int nacc = 0, nrej = 0;
     bool last_rej = false, done = !ok || !(a.dt > 0.0);
+    StepState ss{0.0, 1.0};
     while (!done) {
       bool last = false;
       if (t + h >= a.dt) {
@@ -133,11 +134,11 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       double yold[n], ynew[n], en;
 #pragma unroll
       for (int i = 0; i < n; ++i) yold[i] = y[i];
-      const double hstep = h;
-      const bool sok =
-          ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew, en);
+      const bool sok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv,
+                                       stride, ynew, en, nullptr, nacc == 0 && nrej == 0, &last);
+      const double hstep = h;  // the step actually taken (the first one may be cut)
       const int before = nacc;
-      step_control(tb, sok, en, last, a.dt, y, ynew, t, h, nacc, nrej, last_rej, done);
+      step_control(tb, sok, en, last, a.dt, y, ynew, t, h, nacc, nrej, last_rej, done, ss);
       if (nacc > before) {
         if (nacc > a.cap) {
           status = DF_CELL_MAXSTEPS;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
         double yi[n], ynew[n], en;
 #pragma unroll
         for (int i = 0; i < n; ++i) yi[i] = slot[i];
-        const double hs = slot[n];
+        double hs = slot[n];
         int piv[n];
         ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
                         en, piv);

@@ -53,7 +53,7 @@ void df_integ_opts_default(df_integ_opts* o) {
   o->method = 0;
   o->block_threads = 0;
   o->blocks_per_sm = 0;
-  o->order_by_T = 0;
+  o->order_by_T = 1;
 }
 
 const char* df_strerror(int code) {
@@ -122,6 +122,8 @@ void df_mech_free(df_mech* m) {
   if (m->blob_dev) cudaFree(m->blob_dev);
   if (m->counters) cudaFree(m->counters);
   if (m->csr_dev) cudaFree(m->csr_dev);
+  if (m->order) cudaFree(m->order);
+  if (m->bins) cudaFree(m->bins);
   delete m;
 }
 

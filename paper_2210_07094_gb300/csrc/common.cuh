@@ -86,6 +86,10 @@ struct df_mech {
   // persistent-queue and statistics scratch (device): [0] work counter,
   // [1] accepted, [2] rejected, [3] error flag
   unsigned long long* counters = nullptr;
+  // work order scratch (cells sorted hottest first) and its histogram
+  int32_t* order = nullptr;
+  int64_t order_cap = 0;
+  unsigned* bins = nullptr;
   // autotune cache: per (path) best launch shape
   int tuned_threads = 0, tuned_bps = 0;
   int64_t tuned_for_ncells = -1;

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   int status = 0, nacc = 0, nrej = 0;
   double y[n];
   double t = 0.0, h = 0.0;
+  StepState ss{0.0, 1.0};
   unsigned long long tot_acc = 0, tot_rej = 0;
 
   for (;;) {
@@ -159,8 +160,8 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
     double ys[n];
     double en;
     const bool ok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR, Jv, Kv,
-                                    stride, ys, en);
-    step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done);
+                                    stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last);
+    step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
     if (!done) {
       if (nacc + nrej >= a.max_sub) {
         status = DF_CELL_MAXSTEPS;
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
     int status = okin ? DF_CELL_OK : DF_CELL_NONFINITE;
     bool done = !okin || !(a.dt > 0.0);
     double t = 0.0, h = fmin(a.h0, a.dt);
+    double hacc = 0.0, erracc = 1.0;
     int nacc = 0, nrej = 0;
     bool last_rej = false;
     while (!done) {
@@ -293,6 +295,18 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         last = true;
       }
       warp_eval<true>(mv, csr, N, pc, ws, L, L.y);
+      if (nacc == 0 && nrej == 0) {
+        // first trial step from the fastest relative rate (see first_step_limit)
+        double r = 0.0;
+        for (int i = lane; i < n; i += 32)
+          r = fmax(r, fabs(f[i]) / (i == 0 ? fabs(y[0]) : fmax(fabs(y[i]), 1e-6)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(WFULL, r, o));
+        if (r > 0.0 && FIRST_STEP_THETA / r < h) {
+          h = FIRST_STEP_THETA / r;
+          last = false;
+        }
+      }
       const double hgi = 1.0 / (h * tb.gamma);
       for (int e = lane; e < n * n; e += 32) {
         const int i = e / n, j = e - i * n;
@@ -337,14 +351,20 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         for (int i = lane; i < n; i += 32) y[i] = ys[i];
         t = last ? a.dt : t + h;
         ++nacc;
-        double fac = 0.9 * pow(fmax(en, 1e-10), -1.0 / tb.elo);
+        // elementary + Gustafsson predictive controller (see step_control)
+        const double e = fmax(en, 1e-10);
+        double fac = 0.9 * pow(e, -1.0 / tb.elo);
+        if (nacc > 1) fac = fmin(fac, 0.9 * (h / hacc) * pow(e * e / erracc, -1.0 / tb.elo));
         fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+        hacc = h;
+        erracc = fmax(1e-2, en);
         h *= fac;
         last_rej = false;
         if (t >= a.dt) done = true;
       } else {
         ++nrej;
-        const double fac = ok ? fmax(0.2, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
+        const double fmin = nacc == 0 ? 1e-4 : 0.2;
+        const double fac = ok ? fmax(fmin, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
         h *= fac;
         last_rej = true;
       }
@@ -399,6 +419,78 @@ __global__ void __launch_bounds__(256) k_eval_warp(EvalArgs a, const int* csr, W
   if (a.qdot && lane == 0) a.qdot[c] = 0.1 * q;
   if (WITH_J)
     for (int e = lane; e < n * n; e += 32) a.J[c * n * n + e] = ws[L.J + e];
+}
+
+// ----------------------------------------------------------------------------
+// work order by temperature (hottest first): a counting sort over 1 K bins.
+// Hot cells take the most substeps, so handing them out first shortens the
+// tail of the persistent launch, and lanes that refill together get cells of
+// similar stiffness (similar substep counts).
+// ----------------------------------------------------------------------------
+constexpr int ORDER_BINS = 4096;
+constexpr double ORDER_T_TOP = 4000.0;
+
+__device__ __forceinline__ int t_bin(double T) {
+  const double b = ORDER_T_TOP - T;
+  if (!(b >= 0.0)) return 0;  // T >= top
+  return b >= ORDER_BINS - 1 ? ORDER_BINS - 1 : (int)b;
+}
+
+__global__ void k_order_hist(const double* T, int64_t n, unsigned* hist) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) atomicAdd(&hist[t_bin(T[c])], 1u);
+}
+
+__global__ void k_order_scan(unsigned* hist) {
+  // one block of 1024 threads, 4 bins each: exclusive prefix sum in place
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x;
+  unsigned v[4], s = 0;
+  for (int i = 0; i < 4; ++i) {
+    v[i] = hist[4 * t + i];
+    s += v[i];
+  }
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned add = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += add;
+    __syncthreads();
+  }
+  unsigned base = part[t] - s;
+  for (int i = 0; i < 4; ++i) {
+    hist[4 * t + i] = base;
+    base += v[i];
+  }
+}
+
+__global__ void k_order_scatter(const double* T, int64_t n, unsigned* offs, int32_t* order) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n) order[atomicAdd(&offs[t_bin(T[c])], 1u)] = (int32_t)c;
+}
+
+static int build_order(df_mech* m, const double* T, int64_t ncells, cudaStream_t st, int32_t** out) {
+  if (m->order_cap < ncells) {
+    if (m->order) cudaFree(m->order);
+    m->order = nullptr;
+    m->order_cap = 0;
+    int rc = cuda_check(cudaMalloc(&m->order, sizeof(int32_t) * ncells), "cudaMalloc order");
+    if (rc) return rc;
+    m->order_cap = ncells;
+  }
+  if (!m->bins) {
+    int rc = cuda_check(cudaMalloc(&m->bins, sizeof(unsigned) * ORDER_BINS), "cudaMalloc bins");
+    if (rc) return rc;
+  }
+  int rc = cuda_check(cudaMemsetAsync(m->bins, 0, sizeof(unsigned) * ORDER_BINS, st), "clear bins");
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((ncells + 255) / 256);
+  k_order_hist<<<blocks, 256, 0, st>>>(T, ncells, m->bins);
+  k_order_scan<<<1, 1024, 0, st>>>(m->bins);
+  k_order_scatter<<<blocks, 256, 0, st>>>(T, ncells, m->bins, m->order);
+  *out = m->order;
+  return cuda_check(cudaGetLastError(), "order kernels");
 }
 
 // ----------------------------------------------------------------------------
@@ -603,6 +695,12 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   a.method = o.method;
   a.status = status;
   a.nsub = nsub;
+  if (!order && o.order_by_T && nwork == ncells && ncells > 1) {
+    int32_t* ord = nullptr;
+    rc = build_order(m, T, ncells, st, &ord);
+    if (rc) return rc;
+    order = ord;
+  }
   a.order = order;
   a.nwork = nwork;
   a.nwork_dev = nwork_dev;

@@ -89,14 +89,37 @@ static RosTab make_rodas3() {
 // One Rosenbrock attempt from y over h: K stages in Kv (strided, s x n), the
 // factorised W = I/(h gamma) - J(y) left in Jv, the candidate state in ynew and
 // the weighted RMS norm of the embedded error estimate in en.
+// First trial step of a cell: theta over the fastest relative rate
+// max_i |f_i| / max(|y_i|, floor_i) at the initial state (floor 1e-6 for mass
+// fractions: species that start near zero do not set the scale).  It replaces
+// the cuts the error control would otherwise make from h = dt on stiff cells,
+// and is taken from f(y0), which the first attempt computes anyway.
+constexpr double FIRST_STEP_THETA = 0.5;
+
+template <int n>
+__device__ __forceinline__ double first_step_limit(const double (&y)[n], const double (&f)[n]) {
+  double r = fabs(f[0]) / fabs(y[0]);
+#pragma unroll
+  for (int i = 1; i < n; ++i) r = fmax(r, fabs(f[i]) / fmax(fabs(y[i]), 1e-6));
+  return r > 0.0 ? FIRST_STEP_THETA / r : INFINITY;
+}
+
 template <int NS>
 __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb, double pc, const double (&y)[NS + 1],
-                                            double h, double rtol, double atolY, double atolT, SV C, SV wdot,
+                                            double& h, double rtol, double atolY, double atolT, SV C, SV wdot,
                                             SV gRT, SV hRT, SV cpR, SV Jv, SV Kv, int stride,
-                                            double (&ynew)[NS + 1], double& en, int* piv_out = nullptr) {
+                                            double (&ynew)[NS + 1], double& en, int* piv_out = nullptr,
+                                            bool first = false, bool* last = nullptr) {
   constexpr int n = NS + 1;
   double fs[n];
   eval_thread<NS, true>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  if (first) {
+    const double hl = first_step_limit<n>(y, fs);
+    if (hl < h) {
+      h = hl;
+      if (last) *last = false;
+    }
+  }
   const double hgi = 1.0 / (h * tb.gamma);
 #pragma unroll
   for (int i = 0; i < n; ++i) {
@@ -145,25 +168,42 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
   return ok && isfinite(en);
 }
 
-// accept / reject and the next step size (elementary controller with safety
-// factor 0.9, growth limits [0.2, 6], no growth right after a rejection)
+// accept / reject and the next step size.  Elementary controller (safety 0.9,
+// growth limits [0.2, 6], down to 1e-4 before the first accepted step, no
+// growth right after a rejection) combined with Gustafsson's predictive
+// controller as in RODAS (Hairer & Wanner, Solving ODEs II, Sec. IV.8): after
+// an accepted step the growth factor is the smaller of
+//   0.9 err^(-1/p)  and  0.9 (h / h_acc) (err_acc / err^2)^(1/p),
+// h_acc, err_acc being the previous accepted step and its error (>= 1e-2).
+struct StepState {
+  double hacc, erracc;
+};
+
 template <int n>
 __device__ __forceinline__ void step_control(const RosTab& tb, bool ok, double en, bool last, double dt,
                                              double (&y)[n], const double (&ynew)[n], double& t, double& h,
-                                             int& nacc, int& nrej, bool& last_rej, bool& done) {
+                                             int& nacc, int& nrej, bool& last_rej, bool& done, StepState& ss) {
+  const double ie = -1.0 / tb.elo;
   if (ok && en <= 1.0) {
 #pragma unroll
     for (int i = 0; i < n; ++i) y[i] = ynew[i];
     t = last ? dt : t + h;
     ++nacc;
-    double fac = 0.9 * pow(fmax(en, 1e-10), -1.0 / tb.elo);
+    const double e = fmax(en, 1e-10);
+    double fac = 0.9 * pow(e, ie);
+    if (nacc > 1) fac = fmin(fac, 0.9 * (h / ss.hacc) * pow(e * e / ss.erracc, ie));
     fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+    ss.hacc = h;
+    ss.erracc = fmax(1e-2, en);
     h *= fac;
     last_rej = false;
     if (t >= dt) done = true;
   } else {
     ++nrej;
-    const double fac = ok ? fmax(0.2, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
+    // before the first accepted step the trial step (= dt) may be orders of
+    // magnitude too long for a stiff cell: let the error estimate cut it deeply
+    const double fmin = nacc == 0 ? 1e-4 : 0.2;
+    const double fac = ok ? fmax(fmin, 0.9 * pow(en, ie)) : 0.25;
     h *= fac;
     last_rej = true;
   }
