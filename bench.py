@@ -120,6 +120,95 @@ def cpu_baseline(sample_cells: int, threads: int):
                       f"OpenMP over cells; {dt:.2f} s", "failed_cells": int(np.sum(st != 0))}
 
 
+def _median_ms(fn, reps):
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn(e0, e1)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def adjoint_case(reps: int = 5):
+    """Forward and discrete adjoint on 65536 cells of the 9-species field
+    (T ~ U[900,1500] K, 1 atm): L = sum_c T_c(dt) + sum_c qdot_c(dt), the
+    adjoint call re-running the forward with checkpoints and then the reverse
+    sweep.  Returns times and their ratio."""
+    import torch
+    import paper_2210_07094_gb300 as df
+    from paper_2210_07094_gb300 import synth
+    mech = synth.h2_air_mechanism()
+    m = df.Mechanism(mech)
+    f = synth.field(3, mech)
+    T0 = torch.tensor(f["T"], device="cuda")
+    p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(f["Y"], device="cuda")
+    n = T0.numel()
+    ones = torch.ones(n, dtype=torch.float64, device="cuda")
+    T, Y = T0.clone(), Y0.clone()
+
+    def fwd(e0, e1):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0.record()
+        df.integrate(m, T, p, Y, f["dt"])
+        e1.record()
+
+    def adj(e0, e1):
+        e0.record()
+        out = df.adjoint(m, T0, p, Y0, f["dt"], gT1=ones, gQ1=ones)
+        e1.record()
+        adj.status = out["status"]
+
+    fwd(*[torch.cuda.Event(enable_timing=True) for _ in range(2)])
+    adj(*[torch.cuda.Event(enable_timing=True) for _ in range(2)])
+    ms_f = _median_ms(fwd, reps)
+    ms_a = _median_ms(adj, reps)
+    acc, rej = m.last_stats()
+    return {"workload": f"{n} cells, 9-species mechanism, T ~ U[900,1500] K, 1 atm, dt = 1 us; "
+                        "L = sum T(dt) + sum qdot(dt)",
+            "cells": n, "forward_ms": ms_f, "adjoint_ms": ms_a, "ratio_adjoint_to_forward": ms_a / ms_f,
+            "adjoint_cells_per_s": n / (ms_a * 1e-3), "substeps_per_cell": (acc + rej) / n,
+            "failed_cells": int((adj.status != 0).sum())}
+
+
+def chon_case():
+    """The 50-species / 300-reaction mechanism on 262144 cells (T ~ U[800,2200]
+    K, 1 atm): one warp per cell, launch shape from the autotuner on an
+    8192-cell sample, one timed launch."""
+    import torch
+    import paper_2210_07094_gb300 as df
+    from paper_2210_07094_gb300 import synth
+    mech = synth.hydrocarbon_mechanism()
+    m = df.Mechanism(mech)
+    f = synth.field(2, mech)
+    T0 = torch.tensor(f["T"], device="cuda")
+    p = torch.tensor(f["p"], device="cuda")
+    Y0 = torch.tensor(f["Y"], device="cuda")
+    n = T0.numel()
+    best, _ = m.autotune(T0, p, Y0, f["dt"], sample=8192)
+    T, Y = T0.clone(), Y0.clone()
+    st = {}
+
+    def run(e0, e1):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        e0.record()
+        st["s"], _ = df.integrate(m, T, p, Y, f["dt"], best)
+        e1.record()
+
+    ms = _median_ms(run, 1)
+    acc, rej = m.last_stats()
+    return {"workload": f"{n} cells, 50 species / 300 reactions (20 third-body, 10 Troe), "
+                        "T ~ U[800,2200] K, 1 atm, dt = 1 us; one warp per cell",
+            "cells": n, "ms": ms, "cell_steps_per_s": n / (ms * 1e-3),
+            "substeps_per_cell": {"accepted": acc / n, "rejected": rej / n},
+            "launch_shape": {"block_threads": best.block_threads, "order_by_T": best.order_by_T},
+            "failed_cells": int((st["s"] != 0).sum())}
+
+
 def run_reference(args):
     rank, world, _ = _rank_info()
     if rank != 0:
@@ -153,26 +242,41 @@ def run_reference(args):
 def profile_case(args):
     """gemm-l2: one launch of the MLP's largest layer (262144 x 800 x 1600, the
     second hidden layer of an inference chunk) after one warm-up launch.
-    dnn-infer: two inference passes of an (untrained) network over 2^22 cells of
-    the uneven-stiffness field with 2% of them above the training T range."""
+    chon: one warp-per-cell integrator launch on 8192 cells of the 50-species
+    field.
+    dnn-infer: two inference passes of an (untrained) network over the held-out
+    states of the learned-surrogate workload (2^22 trajectory states, 2% of them
+    moved 50-300 K outside the training T range, half below, half above)."""
     import ctypes as C
     import torch
     from paper_2210_07094_gb300 import _lib
+    if args.profile_case == "chon":
+        import paper_2210_07094_gb300 as df
+        from paper_2210_07094_gb300 import synth
+        mech = synth.hydrocarbon_mechanism()
+        m = df.Mechanism(mech)
+        f = synth.field(2, mech, 8192)
+        T, p, Y = (torch.tensor(f[k], device="cuda") for k in ("T", "p", "Y"))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, _ = df.integrate(m, T, p, Y, f["dt"])
+        e1.record()
+        torch.cuda.synchronize()
+        acc, rej = m.last_stats()
+        print(json.dumps({"case": "chon", "cells": 8192, "ms": e0.elapsed_time(e1), "accepted": acc,
+                          "rejected": rej, "failed": int((st != 0).sum())}))
+        return 0
     if args.profile_case == "dnn-infer":
         import paper_2210_07094_gb300 as df
         from paper_2210_07094_gb300 import surrogate, synth
         mech = synth.h2_air_mechanism()
         m = df.Mechanism(mech)
-        Ts, p, Ys = surrogate.trajectories(m, mech, 4096, 4)
+        Ts, p, Ys = surrogate.trajectories(m, mech, 1 << 14, 32)
         dnn = df.Dnn(df.dnn_default_opts(), seed=1)
         T0, P0, Y0, T1, Y1 = surrogate.pairs(Ts, p, Ys)
         dnn.fit_norm(T0, P0, Y0, Y1)
-        f = synth.field(1, mech, 1 << 22, seed=5)
-        T = torch.tensor(f["T"], device="cuda").clamp(float(T0.min()), float(T0.max()))
-        n_oor = (1 << 22) // 50
-        T[:n_oor] = float(T0.max()) + 100.0
-        p = torch.tensor(f["p"], device="cuda")
-        Y = torch.tensor(f["Y"], device="cuda")
+        del Ts, Ys, T0, P0, Y0, T1, Y1
+        T, p, Y, n_oor = surrogate.heldout(m, mech, dnn, 1 << 22, 32, 0.02)
         Tw, Yw = T.clone(), Y.clone()
         for rep in range(2):
             Tw.copy_(T)
@@ -220,8 +324,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dnn", action="store_true", help="skip the learned-surrogate workload")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the adjoint and 50-species measurements")
     ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
-    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer"],
+    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon"],
                     help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")
@@ -262,13 +368,31 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
+    # launch shape chosen by the library's autotuner on this field (untimed
+    # set-up, cached in the mechanism handle); a sample much smaller than the
+    # workload has a different tail and picks a different shape
+    tuned, tuned_ms = m.autotune(T0, p, Y0, f["dt"], sample=ncells)
+    opts = df.default_opts()
+    opts.order_by_T = tuned.order_by_T
+    kernels_per_step = 4 if opts.order_by_T else 1  # [T histogram, scan, scatter,] integrator
+
     def step():
         T.copy_(T0)
         Y.copy_(Y0)
-        df.integrate(m, T, p, Y, f["dt"], status=status, nsub=nsub)
+        df.integrate(m, T, p, Y, f["dt"], opts, status=status, nsub=nsub)
 
-    for _ in range(args.warmup):
+    # the whole step (state reset + integrator launch) is captured once and
+    # replayed from a CUDA graph
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
         step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
@@ -282,7 +406,7 @@ def main():
     for i in range(args.steps):
         flush.fill_(i & 0xFF)  # evict L2 between timed steps (not timed)
         ev[i][0].record(stream)
-        step()
+        graph.replay()
         ev[i][1].record(stream)
         a, r = m.last_stats()  # synchronises; outside the events
         acc_tot += a
@@ -317,7 +441,7 @@ def main():
         Td.copy_(Th, non_blocking=True)
         pd.copy_(ph, non_blocking=True)
         Yd.copy_(Yh, non_blocking=True)
-        df.integrate(m, Td, pd, Yd, f["dt"], status=status, nsub=nsub)
+        df.integrate(m, Td, pd, Yd, f["dt"], opts, status=status, nsub=nsub)
         To_h.copy_(Td, non_blocking=True)
         Yo_h.copy_(Yd, non_blocking=True)
         st_h.copy_(status, non_blocking=True)
@@ -351,7 +475,10 @@ def main():
                    "cells_per_gpu": ncells, "mechanism": "9 species / 25 reactions "
                    "(4 third-body, 2 Troe)", "method": "RODAS4 (default tolerances rtol 1e-6, atol_Y 1e-10, atol_T 1e-6 K)",
                    "l2": "256 MB buffer written between timed steps (not timed)",
-                   "step": "D2D reset of T, Y to the initial state + one integrate launch",
+                   "step": "D2D reset of T, Y to the initial state + one persistent integrator launch, "
+                           "replayed from a captured CUDA graph",
+                   "launch_shape": {"block_threads": tuned.block_threads, "blocks_per_sm": tuned.blocks_per_sm,
+                                    "order_by_T": tuned.order_by_T, "autotune_sample_ms": tuned_ms},
                    "parallelism": f"replicas x{world} (independent cells)"},
         "substeps": {"accepted_per_step": acc_tot / args.steps, "rejected_per_step": rej_tot / args.steps,
                      "nsub_mean": float(ns.mean()), "nsub_max": int(ns.max()), "nsub_min": int(ns.min()),
@@ -359,10 +486,13 @@ def main():
         "roofline": roof,
         "fp64_peak_gflops_measured": fp64_peak,
         "clocks": clk,
-        "gpu_launches": args.steps,
+        "gpu_launches": kernels_per_step * args.steps,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
+    if rank == 0 and not args.no_extra and ncells == NCELLS:
+        line["adjoint"] = adjoint_case()
+        line["chon_50_species"] = chon_case()
     if rank == 0 and not args.no_dnn and ncells == NCELLS:
         # learned surrogate (BF16 tensor-core MLP) on the same GPU and cell distribution
         from paper_2210_07094_gb300 import surrogate

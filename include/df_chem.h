@@ -67,8 +67,11 @@ typedef struct df_integ_opts {
   double h_min;         /* smallest allowed substep [s]                        */
   int32_t max_substeps; /* accepted + rejected substeps allowed per cell       */
   int32_t method;       /* 0: RODAS4 (Hairer & Wanner), 1: RODAS3 (Sandu 1997) */
-  int32_t block_threads;  /* 0: autotune; else threads per block               */
-  int32_t blocks_per_sm;  /* 0: autotune; else resident blocks per SM          */
+  int32_t block_threads;  /* 0 (with blocks_per_sm 0): the shape df_chem_autotune
+                             chose for this mechanism and path, else 64; >0:
+                             threads per block (a multiple of 32)             */
+  int32_t blocks_per_sm;  /* 0: as many resident blocks as fit (or the tuned
+                             value, see block_threads); >0: at most this many */
   int32_t order_by_T;     /* 1 (default): hand out cells hottest first (a device
                              counting sort; longest work first, lanes refilled
                              together get cells of similar stiffness)          */
@@ -194,6 +197,26 @@ int df_chem_adjoint_static(const df_mech* mech, int64_t ncells, const double* T0
                            const double* Y0, double dt, const df_integ_opts* opts, int32_t max_steps,
                            const double* gT1, const double* gY1, const double* gQ1, double* gT0, double* gY0,
                            double* g_lnA, int32_t* status, int32_t* nsub, df_stream_t stream);
+
+/* Choose the integrator's launch shape for this mechanism by timing (the GPU
+ * form of the paper's dynamic load balancing, Sec. 3.2: the shape that keeps
+ * the lanes of a persistent launch busiest on a given mix of cell stiffness).
+ * The first `sample` cells (0: min(ncells, 65536)) of T, p, Y (device, layout
+ * of df_chem_integrate, ncells the array stride) are copied to library scratch
+ * (the inputs are not modified) and advanced over dt with every candidate:
+ * thread per cell 32/64/96/128 threads per block x at most 0 (all that fit)/1/2
+ * blocks per SM; warp per cell 64/128/256 threads per block; each with and
+ * without hottest-first ordering; two timed runs each, fastest kept.  The
+ * winner is cached in the handle: later df_chem_integrate calls whose options
+ * leave block_threads and blocks_per_sm at 0 use it (order_by_T stays as the
+ * caller passes it).  *best (may be NULL) receives `base` with the winning
+ * block_threads, blocks_per_sm, order_by_T and path; *best_ms (may be NULL)
+ * its time on the sample.  Synchronous (waits for `stream`); allocates and
+ * frees device scratch, so do not call it during a stream capture.  Errors:
+ * DF_EINVAL, DF_ECUDA, DF_ENOMEM, DF_EUNSUPPORTED (no candidate fits). */
+int df_chem_autotune(df_mech* mech, int64_t ncells, const double* T, const double* p, const double* Y,
+                     double dt, const df_integ_opts* base, int64_t sample, df_integ_opts* best,
+                     float* best_ms, df_stream_t stream);
 
 /* Work counters of the last df_chem_integrate on this handle (host values; the
  * call synchronises `stream`): accepted and rejected substeps summed over all

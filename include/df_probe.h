@@ -22,6 +22,13 @@ int df_probe_fp64_peak(int iters, double* gflops, double* ms);
  * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */
 int df_probe_exp(const double* x, double* y, long long n, void* stream);
 
+/* y[i] = GELU(x[i]) (derivative = 0) or GELU'(x[i]) (derivative = 1) as the GEMM
+ * epilogues compute them in FP32 (the network's activation, Sec. 2.3: GELU(z) =
+ * z Phi(z) with Phi the normal CDF, through the library's own erfc), so that their
+ * accuracy can be checked against the exact function.  x, y: device memory;
+ * asynchronous on `stream`.  DF_EINVAL for n < 0 or null arrays with n > 0. */
+int df_probe_gelu(const float* x, float* y, long long n, int derivative, void* stream);
+
 /* C = A . B^T with the library's tcgen05 BF16 GEMM (the kernel under the DNN
  * integrator's layers), FP32 result without bias or activation, so that it can be
  * checked against a reference matmul.  A [M][K], B [N][K] bf16 (device, 16-byte

@@ -86,6 +86,19 @@ class Mechanism:
                    "df_chem_last_stats")
         return a.value, r.value
 
+    def autotune(self, T, p, Y, dt: float, opts: IntegOpts | None = None, sample: int = 0, stream=None):
+        """Time the integrator's launch shapes on (a copy of) the first `sample`
+        cells and cache the fastest in the handle (df_chem_autotune).
+        Returns (best IntegOpts, its time in ms)."""
+        n, pT, pp, pY = _cells(self, T, p, Y)
+        best = IntegOpts()
+        ms = C.c_float()
+        _lib.check(_lib.load().df_chem_autotune(self._h, n, pT, pp, pY, float(dt),
+                                                C.byref(opts) if opts is not None else None, int(sample),
+                                                C.byref(best), C.byref(ms), _stream_ptr(stream)),
+                   "df_chem_autotune")
+        return best, ms.value
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().df_mech_free(self._h)
@@ -350,6 +363,19 @@ class Dnn:
         a = np.ascontiguousarray(a, np.float32)
         assert a.size == self.n_params
         _lib.check(_lib.load().df_dnn_set_params(self._h, a.ctypes.data_as(C.c_void_p)), "df_dnn_set_params")
+
+    def autotune(self, T, p, Y, dt: float, opts: IntegOpts | None = None, sample: int = 0, stream=None):
+        """Time the integrator's launch shapes on (a copy of) the first `sample`
+        cells and cache the fastest in the handle (df_chem_autotune).
+        Returns (best IntegOpts, its time in ms)."""
+        n, pT, pp, pY = _cells(self, T, p, Y)
+        best = IntegOpts()
+        ms = C.c_float()
+        _lib.check(_lib.load().df_chem_autotune(self._h, n, pT, pp, pY, float(dt),
+                                                C.byref(opts) if opts is not None else None, int(sample),
+                                                C.byref(best), C.byref(ms), _stream_ptr(stream)),
+                   "df_chem_autotune")
+        return best, ms.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -52,6 +52,7 @@ SIGNATURES = [
     ("df_chem_jacobian", _i, [_p, _i64, _p, _p, _p, _p, _p]),
     ("df_chem_integrate", _i, [_p, _i64, _p, _p, _p, _d, _p, _p, _p, _p]),
     ("df_chem_last_stats", _i, [_p, _p, _p, _p]),
+    ("df_chem_autotune", _i, [_p, _i64, _p, _p, _p, _d, _p, _i64, _p, _p, _p]),
     ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),
     ("df_chem_adjoint", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
                              _p, _sz, _p]),
@@ -76,6 +77,7 @@ SIGNATURES = [
     ("df_get_last_error_detail", _i, [C.c_char_p, _sz]),
     ("df_probe_fp64_peak", _i, [_i, _p, _p]),
     ("df_probe_exp", _i, [_p, _p, C.c_longlong, _p]),
+    ("df_probe_gelu", _i, [_p, _p, C.c_longlong, _i, _p]),
     ("df_probe_gemm_bf16", _i, [_p, _p, _p, _i, _i, _i, _i, _p, _p]),
 ]
 

@@ -193,6 +193,25 @@ int df_chem_integrate(const df_mech* mc, int64_t ncells, double* T, const double
   return launch_integrate(m, ncells, T, p, Y, dt, o, status, nsub, (cudaStream_t)stream);
 }
 
+int df_chem_autotune(df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y, double dt,
+                     const df_integ_opts* base, int64_t sample, df_integ_opts* best, float* best_ms,
+                     df_stream_t stream) {
+  int rc = check_cells("df_chem_autotune", m, ncells);
+  if (rc) return rc;
+  if (ncells == 0 || sample < 0) return set_error(DF_EINVAL, "df_chem_autotune: no cells to tune on");
+  if (!(dt >= 0.0) || !std::isfinite(dt)) return set_error(DF_EINVAL, "df_chem_autotune: dt must be finite and >= 0");
+  if ((rc = check_dev("df_chem_autotune", "T", T)) || (rc = check_dev("df_chem_autotune", "p", p)) ||
+      (rc = check_dev("df_chem_autotune", "Y", Y)))
+    return rc;
+  df_integ_opts o;
+  if (base) o = *base;
+  else df_integ_opts_default(&o);
+  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
+      o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.path < 0 || o.path > 2)
+    return set_error(DF_EINVAL, "df_chem_autotune: invalid options");
+  return autotune_integrate(m, ncells, T, p, Y, dt, o, sample, best, best_ms, (cudaStream_t)stream);
+}
+
 int df_chem_adjoint_workspace_size(const df_mech* m, int64_t ncells, int32_t max_steps, size_t* bytes) {
   int rc = check_cells("df_chem_adjoint_workspace_size", m, ncells);
   if (rc) return rc;

@@ -90,8 +90,9 @@ struct df_mech {
   int32_t* order = nullptr;
   int64_t order_cap = 0;
   unsigned* bins = nullptr;
-  // autotune cache: per (path) best launch shape
-  int tuned_threads = 0, tuned_bps = 0;
+  // autotune cache: the launch shape df_chem_autotune chose, and for which path
+  // (1 thread per cell, 2 warp per cell) and sample size
+  int tuned_threads = 0, tuned_bps = 0, tuned_path = 0;
   int64_t tuned_for_ncells = -1;
   int num_sms = 0;
   size_t max_smem_optin = 0;
@@ -114,6 +115,9 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st);
 int launch_set_lnA(df_mech* m, const double* lnA, cudaStream_t st);
+int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y, double dt,
+                       const df_integ_opts& base, int64_t sample, df_integ_opts* best, float* best_ms,
+                       cudaStream_t st);
 // advance the cells order[0 .. nwork) (nwork read from nwork_dev on the device
 // when given; nwork is then an upper bound used to size the launch)
 int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,

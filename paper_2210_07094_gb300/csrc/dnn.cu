@@ -75,7 +75,7 @@ struct df_dnn {
   __nv_bfloat16 *iX = nullptr, *iH[3] = {nullptr, nullptr, nullptr};
   float* iU = nullptr;
   int32_t* imask = nullptr;
-  double* iYl = nullptr;  // [16][chunk] Y^lambda of the chunk (features -> post)
+  float* iYl = nullptr;   // [16][chunk] Y^lambda of the chunk, FP32 (features -> post)
   double* rawb = nullptr;  // raw-variable range bounds: lo[16], hi[16] (T, p, Y_k)
   // fallback list, per-cell flags and status scratch (grown on demand)
   int64_t list_cap = 0;
@@ -155,8 +155,6 @@ struct FeatArgs {
   int64_t ldT;
   float* tgt;         // [n][16] or null (normalised change of F(Y))
   int32_t* mask;      // [n] in-range flag or null
-  double* Yl;         // [N][ldYl] Y^lambda (FP64) or null
-  int64_t ldYl;
 };
 
 __global__ void k_dnn_features(FeatArgs a) {
@@ -181,7 +179,6 @@ __global__ void k_dnn_features(FeatArgs a) {
   for (int k = 0; k < a.N; ++k) {
     yl[k] = ylam(a.Y[(int64_t)k * a.ncells + c], a.lam, tab);
     f[2 + k] = (float)((yl[k] - 1.0) / a.lam);
-    if (a.Yl) a.Yl[(int64_t)k * a.ldYl + i] = yl[k];
   }
   bool in_range = true;
   __nv_bfloat16 xb[DNN_IN];
@@ -217,6 +214,83 @@ __global__ void k_dnn_features(FeatArgs a) {
 // Training-range test on the raw variables: the Box-Cox transform is monotonic,
 // so [min, max] of F(Y_k) maps to bounds on Y_k; cells outside any bound are
 // flagged and appended to the fallback list (one atomic per cell outside).
+__device__ __forceinline__ double ipow(double a, int e) {
+  double r = 1.0;
+  while (e > 0) {
+    if (e & 1) r *= a;
+    a *= a;
+    e >>= 1;
+  }
+  return r;
+}
+
+// Y^lambda in FP64 without a logarithm, for lambda = 1/m with m an integer.
+// Y = f 2^(m q) exactly (frexp, then the exponent remainder moved into f, so
+// f lies in [1/2, 2^(m-1))), hence Y^lambda = f^(1/m) 2^q.  f^(1/m) is seeded
+// in FP32 (relative error ~2e-7) and refined by one Newton step on x^m = f,
+// x <- x - x (1 - f / x^m) / m, which squares the relative error (to about
+// (m-1)/2 * 4e-14); the reciprocal of x^m is an FP32 seed plus one Newton
+// step.  About ten FP64 operations against a logarithm and an exponential.
+__device__ __forceinline__ double ylam_newton(double Y, int m, float lamf, double inv_m) {
+  if (!(Y > 0.0)) return 0.0;
+  int e;
+  double f = frexp(Y, &e);
+  int q = e / m, r = e - q * m;
+  if (r < 0) {
+    r += m;
+    --q;
+  }
+  f = ldexp(f, r);
+  const double x0 = (double)powf((float)f, lamf);
+  const double xm = ipow(x0, m);
+  const double r0 = (double)__frcp_rn((float)xm);
+  const double r1 = r0 * fma(-xm, r0, 2.0);
+  const double d = fma(-f, r1, 1.0);
+  return ldexp(fma(-x0 * inv_m, d, x0), q);
+}
+
+// Inference features (stage 1): the encoding of k_dnn_features (F(Y) in FP64,
+// rounded to FP32, z-scored in FP32, rounded to BF16) with Y^lambda from
+// ylam_newton.  Y^lambda is kept, in FP32, for the post stage, which uses it
+// only in ratios or next to a change of its own size (see k_dnn_post).
+struct FeatInferArgs {
+  int64_t ncells, c0, n;
+  int N;
+  int inv_lam;  // 1 / lambda (integer)
+  float lam;
+  const double *T, *p, *Y;
+  const float* norm;
+  __nv_bfloat16* X;  // [n][16]
+  float* Yl;         // [N][ldYl]
+  int64_t ldYl;
+};
+
+__global__ void k_dnn_features_infer(FeatInferArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int64_t c = a.c0 + i;
+  const float* mean_in = a.norm;
+  const float* std_in = a.norm + DNN_IN;
+  __nv_bfloat16 xb[DNN_IN];
+#pragma unroll
+  for (int k = 0; k < DNN_IN; ++k) xb[k] = __float2bfloat16_rn(0.0f);
+  xb[0] = __float2bfloat16_rn(((float)a.T[c] - mean_in[0]) / std_in[0]);
+  xb[1] = __float2bfloat16_rn(((float)a.p[c] - mean_in[1]) / std_in[1]);
+  const double lam = 1.0 / a.inv_lam, inv_m = lam;
+#pragma unroll
+  for (int k = 0; k < DNN_IN - 2; ++k) {
+    if (k < a.N) {
+      const double yl = ylam_newton(a.Y[(int64_t)k * a.ncells + c], a.inv_lam, a.lam, inv_m);
+      a.Yl[(int64_t)k * a.ldYl + i] = (float)yl;
+      const float fk = (float)((yl - 1.0) / lam);
+      xb[2 + k] = __float2bfloat16_rn((fk - mean_in[2 + k]) / std_in[2 + k]);
+    }
+  }
+  uint4* xo = reinterpret_cast<uint4*>(a.X + i * DNN_IN);
+  xo[0] = *reinterpret_cast<const uint4*>(xb);
+  xo[1] = *reinterpret_cast<const uint4*>(xb + 8);
+}
+
 __global__ void k_dnn_range(int64_t ncells, int N, const double* T, const double* p, const double* Y,
                             const double* rawb, uint8_t* flag, int32_t* list, unsigned long long* counter) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -322,7 +396,7 @@ struct PostArgs {
   const float* U;  // [n][16] normalised network output
   const float* norm;
   const uint8_t* flag;  // [ncells] 1: advanced by the fallback
-  const double* Yl;     // [N][ldYl] Y^lambda of the chunk
+  const float* Yl;      // [N][ldYl] Y^lambda of the chunk (FP32)
   int64_t ldYl;
   int32_t* used_fallback;
   int32_t* status;
@@ -330,21 +404,27 @@ struct PostArgs {
   unsigned long long* counter;
 };
 
-__device__ __forceinline__ double ipow(double a, int e) {
-  double r = 1.0;
-  while (e > 0) {
-    if (e & 1) r *= a;
-    a *= a;
-    e >>= 1;
-  }
-  return r;
-}
-
-// stage 3 of the inference: Y' = F^{-1}(F(Y) + u), renormalised; T' from
-// h(T', Y') = h(T, Y) at fixed p by Newton on the NASA-7 enthalpy (FP64)
+// Stage 3 of the inference: Y' = F^{-1}(F(Y) + u), renormalised, and T' from
+// h(T', Y') = h(T, Y) at fixed p by Newton (FP64).
+//
+// Y' is formed as Y + dY.  With z = Y^lambda and r = lambda u / z, Y' = Y (1 + r)^m
+// (m = 1/lambda) exactly, so for |r| <= 1/2 dY = Y expm1(m log1p(r)) carries the
+// relative precision of r however small the change; z enters only through the
+// ratio, so its FP32 value suffices.  For larger changes (and Y = 0), Y' = (z +
+// lambda u)^m directly.
+//
+// The enthalpy per unit mass over R is a polynomial in T once the species are
+// mixed: h = sum_k Y_k/W_k (a6 + a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5),
+// cp its derivative, so each Newton iteration costs two Horner evaluations.
 __global__ void k_dnn_post(PostArgs a) {
-  __shared__ double2 tab[64];
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
+  __shared__ double hc[DNN_OUT][6];
+  const double* sp = a.blob + a.d.off_sp;
+  for (int t = threadIdx.x; t < a.N * 6; t += blockDim.x) {
+    const int k = t / 6, j = t % 6;
+    const double iw = sp[SP_REC * k + 1];
+    const double* c7 = sp + SP_REC * k + 2;
+    hc[k][j] = iw * (j == 0 ? c7[5] : c7[j - 1] / (double)j);
+  }
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -355,45 +435,54 @@ __global__ void k_dnn_post(PostArgs a) {
   }
   const float* mean_out = a.norm + 4 * DNN_IN;
   const float* std_out = a.norm + 4 * DNN_IN + DNN_OUT;
-  const double* sp = a.blob + a.d.off_sp;
-  double Yn[16];
+  const float lamf = (float)a.lam;
+  const float m = (float)a.inv_lam;
+  double Yn[DNN_OUT];
+  double h0c[6] = {0, 0, 0, 0, 0, 0};
   double s = 0.0;
-  for (int k = 0; k < a.N; ++k) {
-    const double y = a.Y[(int64_t)k * a.ncells + c];
-    const double u = (double)a.U[i * DNN_OUT + k] * std_out[k] + mean_out[k];
-    const double z = a.Yl[(int64_t)k * a.ldYl + i] + a.lam * u;  // lambda F(Y') + 1
-    (void)y;
-    const double yn = z > 0.0 ? ipow(z, a.inv_lam) : 0.0;
-    Yn[k] = yn;
-    s += yn;
+#pragma unroll
+  for (int k = 0; k < DNN_OUT; ++k) {
+    if (k < a.N) {
+      const double y = a.Y[(int64_t)k * a.ncells + c];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) h0c[j] = fma(y, hc[k][j], h0c[j]);
+      const float lu = lamf * fmaf(a.U[i * DNN_OUT + k], std_out[k], mean_out[k]);
+      const float z = a.Yl[(int64_t)k * a.ldYl + i];
+      double yn;
+      if (z > 0.0f && fabsf(lu) <= 0.5f * z) {
+        yn = y + y * (double)expm1f(m * log1pf(lu / z));
+      } else {
+        const double zz = (double)z + (double)lu;
+        yn = zz > 0.0 ? ipow(zz, a.inv_lam) : 0.0;
+      }
+      Yn[k] = yn;
+      s += yn;
+    }
   }
   const double is = s > 0.0 ? 1.0 / s : 0.0;
-  // enthalpy per unit mass / R at (T, Y) and Newton for T'
-  const double T0 = a.T[c];
-  double h0 = 0.0;
-  for (int k = 0; k < a.N; ++k) {
-    const double* c7 = sp + SP_REC * k + 2;
-    const double T = T0;
-    const double hRT = c7[0] + T * (c7[1] * 0.5 + T * (c7[2] / 3.0 + T * (c7[3] * 0.25 + T * c7[4] * 0.2))) + c7[5] / T;
-    h0 += a.Y[(int64_t)k * a.ncells + c] * sp[SP_REC * k + 1] * hRT * T;
+  double hm[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < DNN_OUT; ++k) {
+    if (k < a.N) {
+      Yn[k] *= is;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) hm[j] = fma(Yn[k], hc[k][j], hm[j]);
+    }
   }
+  const double T0 = a.T[c];
+  const double h0 = h0c[0] + T0 * (h0c[1] + T0 * (h0c[2] + T0 * (h0c[3] + T0 * (h0c[4] + T0 * h0c[5]))));
   double T = T0;
   for (int it = 0; it < 20; ++it) {
-    double h = 0.0, cp = 0.0;
-    for (int k = 0; k < a.N; ++k) {
-      const double* c7 = sp + SP_REC * k + 2;
-      const double y = Yn[k] * is * sp[SP_REC * k + 1];
-      const double hRT =
-          c7[0] + T * (c7[1] * 0.5 + T * (c7[2] / 3.0 + T * (c7[3] * 0.25 + T * c7[4] * 0.2))) + c7[5] / T;
-      h += y * hRT * T;
-      cp += y * (c7[0] + T * (c7[1] + T * (c7[2] + T * (c7[3] + T * c7[4]))));
-    }
+    const double h = hm[0] + T * (hm[1] + T * (hm[2] + T * (hm[3] + T * (hm[4] + T * hm[5]))));
+    const double cp = hm[1] + T * (2.0 * hm[2] + T * (3.0 * hm[3] + T * (4.0 * hm[4] + T * 5.0 * hm[5])));
     const double dT = (h - h0) / cp;
     T -= dT;
     if (fabs(dT) <= 1e-12 * T) break;
   }
   a.T[c] = T;
-  for (int k = 0; k < a.N; ++k) a.Y[(int64_t)k * a.ncells + c] = Yn[k] * is;
+#pragma unroll
+  for (int k = 0; k < DNN_OUT; ++k)
+    if (k < a.N) a.Y[(int64_t)k * a.ncells + c] = Yn[k];
   if (a.used_fallback) a.used_fallback[c] = 0;
   if (a.status) a.status[c] = DF_CELL_OK;
 }
@@ -557,7 +646,7 @@ static int dnn_infer_buffers(df_dnn* d) {
   int rc = dev_alloc((void**)&d->iX, C * DNN_IN * 2);
   for (int l = 0; l < 3 && !rc; ++l) rc = dev_alloc((void**)&d->iH[l], C * d->L.w[l] * 2);
   rc = rc ? rc : dev_alloc((void**)&d->iU, C * DNN_OUT * 4);
-  rc = rc ? rc : dev_alloc((void**)&d->iYl, C * DNN_OUT * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->iYl, C * DNN_OUT * 4);
   if (!rc && !d->side)
     rc = cuda_check(cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking), "fallback stream");
   if (!rc && !d->ev_ranged) rc = cuda_check(cudaEventCreateWithFlags(&d->ev_ranged, cudaEventDisableTiming), "event");
@@ -950,13 +1039,13 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
   const int inv = (int)std::lround(1.0 / d->o.lambda);
   for (int64_t c0 = 0; c0 < ncells && !rc; c0 += d->chunk) {
     const int64_t nc = std::min<int64_t>(d->chunk, ncells - c0);
-    FeatArgs fa;
-    memset(&fa, 0, sizeof(fa));
+    FeatInferArgs fa;
     fa.ncells = ncells;
     fa.c0 = c0;
     fa.n = nc;
     fa.N = d->o.n_species;
-    fa.lam = d->o.lambda;
+    fa.lam = (float)d->o.lambda;
+    fa.inv_lam = inv;
     fa.T = T;
     fa.p = p;
     fa.Y = Y;
@@ -964,7 +1053,7 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
     fa.X = d->iX;
     fa.Yl = d->iYl;
     fa.ldYl = d->chunk;
-    k_dnn_features<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(fa);
+    k_dnn_features_infer<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(fa);
     rc = dnn_forward_infer(d, d->iX, nc, d->iU, st);
     if (rc) break;
     PostArgs pa;

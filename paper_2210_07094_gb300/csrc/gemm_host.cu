@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
+#include <string>
 
 #include "common.cuh"
 #include "gemm_host.cuh"
@@ -83,14 +85,38 @@ static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cud
 
 constexpr int PERS_STAGES = 4;
 
-template <int BN>
-static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, cudaStream_t st) {
-  CUtensorMap ta, tb;
-  int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
-  if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
-  if (rc) return rc;
-  auto kf = k_gemm_tc_pers<BN, PERS_STAGES>;
-  const size_t sm = (size_t)PERS_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
+// 2D bf16 output tensor [rows][cols] (row pitch ld) for TMA stores of 32-row x
+// 16-column blocks, no swizzle
+static int make_tmap_store(CUtensorMap* m, const void* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(DF_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  if (ld == 0) ld = cols;
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || (cols % 8) != 0 || (ld % 8) != 0 || ld < cols || rows < 1)
+    return set_error(DF_EINVAL, "GEMM output must be 16-byte aligned with N and its row pitch multiples of 8");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {16, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(DF_ECUDA, "cuTensorMapEncodeTiled (store) failed: " + std::to_string((int)r));
+  return DF_OK;
+}
+
+template <int BN, int MODE>
+static int gemm_launch_pers_mode(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& P, cudaStream_t st) {
+  int rc = DF_OK;
+  CUtensorMap tc;
+  memset(&tc, 0, sizeof(tc));
+  if (MODE == EPI_GELU_BF16) {
+    if (!P.out1) return set_error(DF_EINVAL, "GEMM: bf16 output missing");
+    rc = make_tmap_store(&tc, P.out1, P.M, P.N, P.ld1);
+    if (rc) return rc;
+  }
+  auto kf = k_gemm_tc_pers<BN, PERS_STAGES, MODE>;
+  const size_t sm = (size_t)PERS_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
+                    (MODE == EPI_GELU_BF16 ? PERS_STAGE_C_BYTES : 0) + 1024 + 256;
   static int nsm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -106,8 +132,28 @@ static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, c
   }
   const int64_t tiles = (int64_t)((P.M + GEMM_BM - 1) / GEMM_BM) * ((P.N + BN - 1) / BN);
   const int grid = (int)std::min<int64_t>(tiles, nsm[dev]);
-  kf<<<grid, 192, sm, st>>>(ta, tb, P);
+  kf<<<grid, PERS_THREADS, sm, st>>>(ta, tb, tc, P);
   return cuda_check(cudaGetLastError(), "persistent GEMM launch");
+}
+
+template <int BN>
+static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
+  if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
+  if (rc) return rc;
+  switch (P.mode) {
+    case EPI_F32:
+      return gemm_launch_pers_mode<BN, EPI_F32>(ta, tb, P, st);
+    case EPI_GELU_BF16:
+      return gemm_launch_pers_mode<BN, EPI_GELU_BF16>(ta, tb, P, st);
+    case EPI_TRAIN_FWD:
+      return gemm_launch_pers_mode<BN, EPI_TRAIN_FWD>(ta, tb, P, st);
+    case EPI_BWD_DZ:
+      return gemm_launch_pers_mode<BN, EPI_BWD_DZ>(ta, tb, P, st);
+    default:
+      return set_error(DF_EINVAL, "GEMM epilogue mode");
+  }
 }
 
 // tile width for the persistent kernel: least padding of N, then the wider tile
@@ -151,7 +197,21 @@ int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st
 
 }  // namespace df
 
+namespace df {
+__global__ void k_gelu_probe(const float* x, float* y, long long n, int derivative) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = derivative ? gelu_grad_f(x[i]) : gelu_f(x[i]);
+}
+}  // namespace df
+
 using namespace df;
+
+extern "C" int df_probe_gelu(const float* x, float* y, long long n, int derivative, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_gelu: bad arguments");
+  if (n == 0) return DF_OK;
+  k_gelu_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, derivative);
+  return cuda_check(cudaGetLastError(), "GELU probe kernel");
+}
 
 extern "C" int df_probe_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int bn,
                                   int* err_flag, void* stream) {

@@ -708,9 +708,15 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   const bool thread_ok = has_thread_kernel(m->dims.N);
   if (o.path == 1 && !thread_ok)
     return set_error(DF_EUNSUPPORTED, "no thread-per-cell kernel built for this species count");
-  if (o.path == 2 || !thread_ok) return integrate_warp_dispatch(m, a, st, o.block_threads);
-  const int threads = o.block_threads > 0 ? o.block_threads : 64;
-  const int bps = o.blocks_per_sm;
+  const bool warp_path = o.path == 2 || !thread_ok;
+  // zero shape fields: the shape df_chem_autotune chose for this path, if any
+  int bt = o.block_threads, bps = o.blocks_per_sm;
+  if (bt == 0 && bps == 0 && m->tuned_threads > 0 && m->tuned_path == (warp_path ? 2 : 1)) {
+    bt = m->tuned_threads;
+    bps = m->tuned_bps;
+  }
+  if (warp_path) return integrate_warp_dispatch(m, a, st, bt);
+  const int threads = bt > 0 ? bt : 64;
   switch (m->dims.N) {
 #define X(NS) \
   case NS:    \
@@ -739,6 +745,103 @@ int launch_set_lnA(df_mech* m, const double* lnA, cudaStream_t st) {
   }
   k_set_lnA<<<(M + 127) / 128, 128, 0, st>>>(m->blob_dev, m->dims.off_rx, M, lnA);
   return cuda_check(cudaGetLastError(), "set lnA kernel");
+}
+
+}  // namespace df
+
+namespace df {
+
+// Time candidate launch shapes of the integrator on a copy of the first
+// `sample` cells and keep the fastest (the GPU form of the paper's load
+// balancing, Sec. 3.2: the shape that keeps the lanes busiest on this cell mix).
+int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y, double dt,
+                       const df_integ_opts& base, int64_t sample, df_integ_opts* best, float* best_ms,
+                       cudaStream_t st) {
+  const int N = m->dims.N;
+  const int64_t n = std::min<int64_t>(ncells, sample > 0 ? sample : 65536);
+  const bool warp_path = base.path == 2 || !has_thread_kernel(N);
+  double *T0 = nullptr, *p0 = nullptr, *Y0 = nullptr, *Tw = nullptr, *Yw = nullptr;
+  int32_t* stt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_check(cudaMalloc(&T0, sizeof(double) * n * (3 + 2 * (int64_t)N)), "autotune scratch");
+  if (!rc) {
+    p0 = T0 + n;
+    Tw = p0 + n;
+    Y0 = Tw + n;
+    Yw = Y0 + n * N;
+    rc = cuda_check(cudaMalloc(&stt, sizeof(int32_t) * n), "autotune scratch");
+  }
+  if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(T0, T, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy T");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(p0, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy p");
+  if (!rc)
+    rc = cuda_check(cudaMemcpy2DAsync(Y0, sizeof(double) * n, Y, sizeof(double) * ncells, sizeof(double) * n, N,
+                                      cudaMemcpyDeviceToDevice, st),
+                    "copy Y");
+  std::vector<df_integ_opts> cand;
+  for (int order = 0; order <= 1; ++order) {
+    if (warp_path) {
+      for (int bt : {64, 128, 256}) {
+        df_integ_opts o = base;
+        o.block_threads = bt;
+        o.blocks_per_sm = 0;
+        o.order_by_T = order;
+        o.path = 2;
+        cand.push_back(o);
+      }
+    } else {
+      for (int bt : {32, 64, 96, 128})
+        for (int bps : {0, 1, 2}) {
+          df_integ_opts o = base;
+          o.block_threads = bt;
+          o.blocks_per_sm = bps;
+          o.order_by_T = order;
+          o.path = 1;
+          cand.push_back(o);
+        }
+    }
+  }
+  float tbest = INFINITY;
+  df_integ_opts obest = base;
+  for (size_t c = 0; c < cand.size() && !rc; ++c) {
+    float tmin = INFINITY;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok && !rc; ++rep) {
+      rc = cuda_check(cudaMemcpyAsync(Tw, T0, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "reset T");
+      if (!rc)
+        rc = cuda_check(cudaMemcpyAsync(Yw, Y0, sizeof(double) * n * N, cudaMemcpyDeviceToDevice, st), "reset Y");
+      if (!rc) rc = cuda_check(cudaEventRecord(e0, st), "event");
+      if (rc) break;
+      if (launch_integrate(m, n, Tw, p0, Yw, dt, cand[c], stt, nullptr, st) != DF_OK) {
+        ok = false;  // a shape that does not fit this device: skip it
+        break;
+      }
+      rc = cuda_check(cudaEventRecord(e1, st), "event");
+      if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "synchronise");
+      float ms = 0.0f;
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed time");
+      if (!rc) tmin = std::min(tmin, ms);
+    }
+    if (!rc && ok && tmin < tbest) {
+      tbest = tmin;
+      obest = cand[c];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (T0) cudaFree(T0);
+  if (stt) cudaFree(stt);
+  if (rc) return rc;
+  if (!(tbest < INFINITY)) return set_error(DF_EUNSUPPORTED, "df_chem_autotune: no launch shape fits this device");
+  m->tuned_threads = obest.block_threads;
+  m->tuned_bps = obest.blocks_per_sm;
+  m->tuned_path = obest.path;
+  m->tuned_for_ncells = n;
+  if (best) *best = obest;
+  if (best_ms) *best_ms = tbest;
+  set_error(DF_OK, "");
+  return DF_OK;
 }
 
 }  // namespace df

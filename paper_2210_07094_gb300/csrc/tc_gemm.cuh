@@ -97,9 +97,47 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Phi(-|z|) = erfc(|z| / sqrt 2) / 2 by the Chebyshev-fitted form of Press,
+// Teukolsky, Vetterling and Flannery (Numerical Recipes, Sec. 6.2):
+// erfc(a) = t exp(-a^2 + P(t)), t = 1 / (1 + a/2), fractional error below
+// 1.2e-7 for every a >= 0, so the deep tails of the GELU keep their relative
+// accuracy.  Folded for the hardware exp2: with b = a sqrt(log2 e),
+// erfc(a) / 2 = t 2^(-b^2 + log2(e) P(t) - 1); the coefficients below are
+// log2(e) times the published ones (the constant term also carries the -1).
+// One reciprocal, eleven FMA/MUL and one exp2 (hardware approximations,
+// relative error ~2^-22).
+__device__ __forceinline__ float half_erfc_scaled(float az) {
+  constexpr double L2E = 1.4426950408889634;
+  constexpr float kb = (float)(0.70710678118654752 * 1.2011224087864498);  // 1/sqrt2 * sqrt(log2 e)
+  constexpr float kt = (float)(0.5 / 1.2011224087864498);
+  const float b = az * kb;
+  float t;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(kt, b, 1.0f)));
+  float p = (float)(0.17087277 * L2E);
+  p = fmaf(p, t, (float)(-0.82215223 * L2E));
+  p = fmaf(p, t, (float)(1.48851587 * L2E));
+  p = fmaf(p, t, (float)(-1.13520398 * L2E));
+  p = fmaf(p, t, (float)(0.27886807 * L2E));
+  p = fmaf(p, t, (float)(-0.18628806 * L2E));
+  p = fmaf(p, t, (float)(0.09678418 * L2E));
+  p = fmaf(p, t, (float)(0.37409196 * L2E));
+  p = fmaf(p, t, (float)(1.00002368 * L2E));
+  p = fmaf(p, t, (float)(-1.26551223 * L2E - 1.0));
+  float e;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(-b, b, p)));
+  return t * e;
+}
+
+// GELU(z) = z Phi(z), Phi the standard normal CDF
+__device__ __forceinline__ float gelu_f(float z) {
+  const float h = half_erfc_scaled(fabsf(z));
+  return z * (z >= 0.0f ? 1.0f - h : h);
+}
+// GELU'(z) = Phi(z) + z phi(z)
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  const float h = half_erfc_scaled(fabsf(z));
+  const float Phi = z >= 0.0f ? 1.0f - h : h;
+  return Phi + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 template <int BN, int STAGES>
@@ -266,10 +304,13 @@ namespace df {
 // ---------------------------------------------------------------------------
 // Persistent variant: one CTA per SM walks the output tiles (tile t = blockIdx.x
 // + j * gridDim.x, row-block major so consecutive tiles share their A rows in
-// L2).  Six warps: warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
+// L2).  Ten warps: warp 0 lane 0 issues TMA loads into a STAGES-deep ring,
 // warp 1 lane 0 issues tcgen05.mma into one of TWO TMEM accumulators (tile j
-// uses buffer j & 1), warps 2..5 drain the other accumulator through the
-// epilogue, so the epilogue of tile j overlaps the MMAs of tile j + 1.
+// uses buffer j & 1), warps 2..9 drain the other accumulator through the
+// epilogue, so the epilogue of tile j overlaps the MMAs of tile j + 1.  A warp
+// may only read the TMEM lane quarter (warp % 4), so two epilogue warps share
+// each quarter and take alternate 16-column chunks: two warps per SM
+// sub-partition hide the latency of the epilogue's loads and transcendentals.
 // BN is any multiple of 16 up to 256 (the epilogue reads TMEM 16 columns at
 // a time).
 // ---------------------------------------------------------------------------
@@ -277,53 +318,119 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int BN>
-__device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint32_t (&r)[16], int row, int nb) {
-  if (nb >= P.N) return;
-  const bool rok = row < P.M;
+// bf16 output staging of the persistent kernel's EPI_GELU_BF16 epilogue: per
+// epilogue warp two blocks of 32 rows x 16 columns (1 KB each), stored to
+// global memory by TMA (box 16 x 32, no swizzle)
+constexpr int PERS_STAGE_C_WARP = 32 * 16 * 2;
+constexpr int PERS_STAGE_C_BYTES = 8 * 2 * PERS_STAGE_C_WARP;
+
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta));
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// TMA store of a shared-memory block to the 2D tensor at (x = column, y = row);
+// elements outside the tensor are not written
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+
+// bias + GELU of one 16-column chunk, packed to bf16 pairs (EPI_GELU_BF16)
+__device__ __forceinline__ void gemm_gelu_chunk(const GemmParams& P, const uint32_t (&r)[16], int nb,
+                                                uint32_t (&hb)[8]) {
   float v[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
   if (P.bias) {
+    if (nb + 16 <= P.N && (reinterpret_cast<uintptr_t>(P.bias + nb) & 15) == 0) {
+      const float4* b4 = reinterpret_cast<const float4*>(P.bias + nb);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
+      for (int q = 0; q < 4; ++q) {
+        const float4 b = __ldg(b4 + q);
+        v[4 * q] += b.x;
+        v[4 * q + 1] += b.y;
+        v[4 * q + 2] += b.z;
+        v[4 * q + 3] += b.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
+    }
   }
-  if (P.mode == EPI_F32) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu_f(v[2 * j]), gelu_f(v[2 * j + 1]));
+    hb[j] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// Epilogue of one 16-column chunk of one accumulator row, the mode fixed at
+// compile time.  Bias loads are four 16-byte loads (the same address across the
+// warp); the per-column bounds tests run only on the ragged last chunk.
+template <int MODE>
+__device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint32_t (&r)[16], int row, int nb) {
+  if (nb >= P.N) return;
+  const bool rok = row < P.M;
+  const bool full = nb + 16 <= P.N;
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  if (P.bias) {
+    if (full && (reinterpret_cast<uintptr_t>(P.bias + nb) & 15) == 0) {
+      const float4* b4 = reinterpret_cast<const float4*>(P.bias + nb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 b = __ldg(b4 + q);
+        v[4 * q] += b.x;
+        v[4 * q + 1] += b.y;
+        v[4 * q + 2] += b.z;
+        v[4 * q + 3] += b.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
+    }
+  }
+  if (MODE == EPI_F32 || MODE == EPI_TRAIN_FWD) {
     if (rok) {
       float* o = P.out0 + (size_t)row * P.ld0 + nb;
 #pragma unroll
       for (int j = 0; j < 16; j += 4)
-        if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        if (full || nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
     }
-    return;
+    if (MODE == EPI_F32) return;
   }
-  if (P.mode == EPI_TRAIN_FWD && rok) {
-    float* o = P.out0 + (size_t)row * P.ld0 + nb;
-#pragma unroll
-    for (int j = 0; j < 16; j += 4)
-      if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-  }
-  if (P.mode == EPI_BWD_DZ) {
+  if (MODE == EPI_BWD_DZ) {
     const float* az = P.aux + (size_t)(rok ? row : 0) * P.lda + nb;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = (rok && nb + j < P.N) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
+    for (int j = 0; j < 16; ++j) v[j] = (rok && (full || nb + j < P.N)) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
   } else {
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
   }
-  __nv_bfloat16 hb[16];
+  __nv_bfloat162 hb[8];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) hb[j] = __float2bfloat16_rn(v[j]);
+  for (int j = 0; j < 8; ++j) hb[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
   if (P.out1 && rok) {
     __nv_bfloat16* o = P.out1 + (size_t)row * P.ld1 + nb;
-#pragma unroll
-    for (int j = 0; j < 16; j += 8)
-      if (nb + j < P.N) *reinterpret_cast<uint4*>(o + j) = *reinterpret_cast<const uint4*>(hb + j);
+    if (full || nb + 8 <= P.N) *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(hb);
+    if (full) *reinterpret_cast<uint4*>(o + 8) = *reinterpret_cast<const uint4*>(hb + 4);
   }
-  if (P.out2 && rok) {
+  if (MODE != EPI_GELU_BF16 && P.out2 && rok) {
+    const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(hb);
 #pragma unroll
     for (int j = 0; j < 16; ++j)
-      if (nb + j < P.N) P.out2[(size_t)(nb + j) * P.ld2 + row] = hb[j];
+      if (full || nb + j < P.N) P.out2[(size_t)(nb + j) * P.ld2 + row] = h[j];
   }
 }
 
@@ -332,9 +439,13 @@ __host__ __device__ constexpr int tmem_cols_for() {
   return (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
 }
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(192, 1)
-    k_gemm_tc_pers(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmParams P) {
+constexpr int PERS_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
+constexpr int PERS_EPI_THREADS = PERS_THREADS - 64;
+
+template <int BN, int STAGES, int MODE>
+__global__ void __launch_bounds__(PERS_THREADS, 1)
+    k_gemm_tc_pers(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, GemmParams P) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tile width");
   extern __shared__ uint8_t smem_raw[];
   constexpr int A_BYTES = GEMM_BM * GEMM_BK * 2;
@@ -344,7 +455,10 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);  // full[S] empty[S] accf[2] acce[2]
+  // EPI_GELU_BF16 output staging: two 32-row x 16-column bf16 blocks per epilogue warp
+  uint8_t* sC = sB + STAGES * B_BYTES;
+  constexpr int C_BYTES = (MODE == EPI_GELU_BF16) ? PERS_STAGE_C_BYTES : 0;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sC + C_BYTES);  // full[S] empty[S] accf[2] acce[2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
@@ -357,11 +471,13 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 128);
+      mbar_init(acce0 + 8 * b, PERS_EPI_THREADS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    if (MODE == EPI_GELU_BF16)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -437,8 +553,13 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 2..5 cover TMEM lane quarters (warp % 4)
+    // epilogue warps 2..9: TMEM lane quarter warp % 4, chunk parity (warp - 2) / 4.
+    // The TMEM load of the next chunk is issued before the current chunk is
+    // processed, so its latency overlaps the arithmetic.
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint32_t stg0 = smem_u32(sC) + (uint32_t)((warp - 2) * 2 * PERS_STAGE_C_WARP);
+    int sbuf = 0;
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1, u = i >> 1;
@@ -449,21 +570,47 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int m0 = (t / nN) * GEMM_BM, n0 = (t % nN) * BN;
       const int row = m0 + q * 32 + lane;
+      const uint32_t tbase = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
+      uint32_t r[16], rn[16];
+      int c0 = 16 * half;
+      tmem_ld16(tbase + (uint32_t)c0, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r[16];
-        const uint32_t ta = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        gemm_epilogue_16<BN>(P, r, row, n0 + c0);
+      for (; c0 < BN; c0 += 32) {
+        const bool more = c0 + 32 < BN;
+        if (more) tmem_ld16(tbase + (uint32_t)(c0 + 32), rn);
+        if (MODE == EPI_GELU_BF16) {
+          if (n0 + c0 < P.N) {
+            uint32_t hb[8];
+            gemm_gelu_chunk(P, r, n0 + c0, hb);
+            const uint32_t dst = stg0 + (uint32_t)(sbuf * PERS_STAGE_C_WARP);
+            // the staging block written two chunks ago must have been read out
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            __syncwarp();
+            st_shared_v4(dst + lane * 32, hb[0], hb[1], hb[2], hb[3]);
+            st_shared_v4(dst + lane * 32 + 16, hb[4], hb[5], hb[6], hb[7]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&tmC, dst, n0 + c0, m0 + q * 32);
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+            sbuf ^= 1;
+          }
+        } else {
+          gemm_epilogue_16<MODE>(P, r, row, n0 + c0);
+        }
+        if (more) {
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) r[j] = rn[j];
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(acce0 + 8 * b);
     }
+    // the staging blocks must stay valid until the last stores have read them
+    if (MODE == EPI_GELU_BF16 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

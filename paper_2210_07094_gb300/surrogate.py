@@ -105,6 +105,32 @@ def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6):
     }
 
 
+def heldout(m: Mechanism, mech_json: dict, dnn: Dnn, n_eval: int, n_steps: int, oor_frac: float,
+            seed: int = synth.TRAIN_SEED):
+    """Held-out inference states: all time levels of integrator trajectories
+    other than the training ones, with a fraction oor_frac moved outside the
+    network's training T range (half 50-300 K below it, half 50-300 K above).
+    Returns device tensors T, p, Y and the number of moved cells."""
+    import torch
+    n_init = max(1, n_eval // n_steps)
+    Ts, p, Ys = trajectories(m, mech_json, n_init, n_steps - 1, seed=seed + 1000)
+    Te = torch.cat(Ts)[:n_eval].contiguous()
+    Pe = p.repeat(n_steps)[:n_eval].contiguous()
+    Ye = torch.cat(Ys, dim=1)[:, :n_eval].contiguous()
+    del Ts, Ys
+    n_eval = Te.numel()
+    g = torch.Generator(device=Te.device).manual_seed(seed + 7)
+    n_oor = int(round(oor_frac * n_eval))
+    oor = torch.randperm(n_eval, device=Te.device, generator=g)[:n_oor]
+    nm = dnn.norm()
+    t_lo, t_hi = float(nm["in_min"][0]), float(nm["in_max"][0])
+    off = 50.0 + 250.0 * torch.rand(n_oor, device=Te.device, generator=g, dtype=torch.float64)
+    half = n_oor // 2
+    Te[oor[:half]] = t_lo - off[:half]
+    Te[oor[half:]] = t_hi + off[half:]
+    return Te, Pe, Ye, n_oor
+
+
 def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22, oor_frac=0.02,
                train_seconds=60.0, batch=4096, reps=3, seed=synth.TRAIN_SEED, log=None):
     """Learned-surrogate workload: train on integrator trajectories of the
@@ -138,24 +164,8 @@ def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22
     t_train = time.time() - t1
     n_pairs = T0.numel()
     del T0, P0, Y0, T1, Y1
-    # held-out states: other trajectories, all their time levels
-    n_init = max(1, n_eval // n_steps)
-    Ts, p, Ys = trajectories(m, mech_json, n_init, n_steps - 1, seed=seed + 1000)
-    Te = torch.cat(Ts)[:n_eval].contiguous()
-    Pe = p.repeat(n_steps)[:n_eval].contiguous()
-    Ye = torch.cat(Ys, dim=1)[:, :n_eval].contiguous()
-    del Ts, Ys
+    Te, Pe, Ye, n_oor = heldout(m, mech_json, dnn, n_eval, n_steps, oor_frac, seed)
     n_eval = Te.numel()
-    g = torch.Generator(device=Te.device).manual_seed(seed + 7)
-    n_oor = int(round(oor_frac * n_eval))
-    oor = torch.randperm(n_eval, device=Te.device, generator=g)[:n_oor]
-    # half of them 50-300 K below the training T range, half 50-300 K above it
-    nm = dnn.norm()
-    t_lo, t_hi = float(nm["in_min"][0]), float(nm["in_max"][0])
-    off = 50.0 + 250.0 * torch.rand(n_oor, device=Te.device, generator=g, dtype=torch.float64)
-    half = n_oor // 2
-    Te[oor[:half]] = t_lo - off[:half]
-    Te[oor[half:]] = t_hi + off[half:]
     # accuracy: network vs integrator on the same states
     ev = evaluate(dnn, m, Te, Pe, Ye)
     # throughput: network (incl. pre/post and fallback) and integrator, same cells

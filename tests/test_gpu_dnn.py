@@ -23,13 +23,18 @@ def _opts(widths, batch=1024):
     return o
 
 
-@pytest.mark.parametrize("widths", [(32, 16, 8), (1600, 800, 400)])
-def test_forward_matches_oracle(widths):
-    dnn = df.Dnn(_opts(widths), seed=5)
+# 1000 rows: one-tile-per-CTA kernels; 5000 rows (ragged last row block): the
+# persistent kernels with the TMA-store epilogue
+@pytest.mark.parametrize("widths,rows", [((32, 16, 8), 1000), ((1600, 800, 400), 1000),
+                                         ((1600, 800, 400), 5000), ((200, 136, 72), 5000)])
+def test_forward_matches_oracle(widths, rows):
+    o = _opts(widths)
+    o.infer_chunk = 8192
+    dnn = df.Dnn(o, seed=5)
     P = mlp.unpack(dnn.params(), widths)
     rng = np.random.default_rng(0)
-    Xf = np.zeros((1000, 16), np.float32)
-    Xf[:, :11] = rng.standard_normal((1000, 11))
+    Xf = np.zeros((rows, 16), np.float32)
+    Xf[:, :11] = rng.standard_normal((rows, 11))
     X = torch.tensor(Xf, device=DEV).to(torch.bfloat16)
     U = dnn.forward_raw(X).cpu().numpy()
     Uo, _ = mlp.forward(P, X.float().cpu().numpy(), emulate=True)
@@ -112,6 +117,39 @@ def test_infer_pipeline_and_fallback(data):
         h0 = o.enthalpy_mass(f["T"][cc], f["Y"][:, cc])
         h1 = o.enthalpy_mass(T.cpu().numpy()[cc], Yg[:, c])
         assert abs(h1 - h0) <= 1e-9 * 1.5e3 * f["T"][cc]
+
+
+def test_post_resolves_small_changes(data):
+    """Stage 3 on changes far below FP32 resolution of Y itself: with the output
+    layer's weights zeroed the network returns its bias, so every cell gets the
+    same small u (relative changes 1e-7 .. 1e-5 of Y).  Y' and T' must agree with
+    the FP64 oracle post stage to a small fraction of the change."""
+    mech, m, (T0, P, Y0, T1, Y1) = data
+    widths = (32, 16, 8)
+    dnn = df.Dnn(_opts(widths), seed=5)
+    dnn.fit_norm(T0, P, Y0, Y1)
+    dnn.set_norm(mean_out=np.zeros(9), std_out=np.ones(9))  # u = U: no de-normalisation rounding
+    nm = dnn.norm()
+    w = mlp.unpack(dnn.params(), widths)
+    w["W4"][:] = 0.0
+    w["b4"][:] = 0.0
+    w["b4"][:9] = [1e-7 * (1 if k % 2 else -1) * (1 + 0.1 * k) for k in range(9)]
+    dnn.set_params(mlp.pack(w, widths))
+    o = Mech(mech)
+    sel = np.arange(0, T0.numel(), 7)
+    T, p, Y = T0[sel].clone(), P[sel].clone(), Y0[:, sel].clone().contiguous()
+    Th, ph, Yh = T.cpu().numpy(), p.cpu().numpy(), Y.cpu().numpy()
+    nfb, used, status = dnn.infer(m, T, p, Y, 1e-6)
+    net = np.where(used.cpu().numpy() == 0)[0]
+    assert len(net) > 0.9 * len(sel)
+    U = np.tile(w["b4"].astype(np.float32), (len(net), 1)).astype(np.float64)
+    norm = {"mean_out": np.r_[nm["mean_out"], np.zeros(7)], "std_out": np.r_[nm["std_out"], np.ones(7)]}
+    To, Yo = mlp.post(Th[net], ph[net], Yh[:, net], U, 0.1, norm, 9, o.nasa, o.W)
+    Yg, Tg = Y.cpu().numpy()[:, net], T.cpu().numpy()[net]
+    dY = np.abs(Yo - Yh[:, net])
+    assert dY.max() > 0
+    assert np.all(np.abs(Yg - Yo) <= 1e-4 * dY + 1e-22), np.max(np.abs(Yg - Yo) / (dY + 1e-30))
+    assert np.all(np.abs(Tg - To) <= 1e-3 * np.abs(To - Th[net]) + 1e-10 * Th[net])
 
 
 def test_save_load_roundtrip(tmp_path):
