@@ -62,9 +62,9 @@ struct AdjArgs {
 
 template <int NS>
 __host__ __device__ constexpr int adj_ws_doubles(int M) {
-  // Dual C, wdot, gRT, hRT, cpR (10 NS) + Dual J (2 n^2) + W (n^2) + K, Kbar (12 n)
-  // + theta (M) + u, ud (2 NS) + v (n)
-  return 12 * NS + 3 * (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
+  // Dual C, wdot, gRT, hRT, cpR, sigma, v (14 NS) + W (n^2) + K, Kbar (12 n)
+  // + theta (M) + u, ud (2 NS) + Rbar (n)
+  return 16 * NS + (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
 }
 
 template <int NS>
@@ -89,13 +89,13 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
   Dual* dbase = reinterpret_cast<Dual*>(base) + tid;
   SVT<Dual> dC{dbase, stride}, dW{dbase + NS * stride, stride}, dG{dbase + 2 * NS * stride, stride},
       dH{dbase + 3 * NS * stride, stride}, dCp{dbase + 4 * NS * stride, stride},
-      dJ{dbase + 5 * NS * stride, stride};
+      dS{dbase + 5 * NS * stride, stride}, dV{dbase + 6 * NS * stride, stride};
   // double views of the same storage
   double* vb = base + 2 * tid;
   SV C{vb, 2 * stride}, wd{vb + 2 * NS * stride, 2 * stride}, gRT{vb + 4 * NS * stride, 2 * stride},
       hRT{vb + 6 * NS * stride, 2 * stride}, cpR{vb + 8 * NS * stride, 2 * stride},
-      Jv{vb + 10 * NS * stride, 2 * stride};
-  double* rest = base + (10 * NS + 2 * n * n) * stride + tid;
+      sg{vb + 10 * NS * stride, 2 * stride}, vs{vb + 12 * NS * stride, 2 * stride};
+  double* rest = base + (14 * NS) * stride + tid;
   SV Wv{rest, stride};
   SV Kv{rest + n * n * stride, stride};
   SV Kb{rest + (n * n + 6 * n) * stride, stride};
@@ -168,18 +168,31 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       for (int k = 0; k < NS; ++k) lam[1 + k] = a.gY1 ? a.gY1[(int64_t)k * a.ncells + cell] : 0.0;
       const double gq = a.gQ1 ? a.gQ1[cell] : 0.0;
       if (gq != 0.0) {
-        for (int kk = 0; kk < n; ++kk) {
-          Dual yd[n], fd[n];
-#pragma unroll
-          for (int i = 0; i < n; ++i) yd[i] = Dual(y[i], i == kk ? 1.0 : 0.0);
-          const Dual q = eval_thread<NS, false, Dual>(mv, pc, yd, fd, dC, dW, dG, dH, dCp, dJ);
-#pragma unroll
-          for (int i = 0; i < n; ++i)
-            if (i == kk) lam[i] += gq * 0.1 * q.d;
-        }
+        // Q = -sum_k H_k wdot_k = f_T rho cp, so dQ/dy = rho cp (row 0 of J) +
+        // f_T d(rho cp)/dy: one transposed product with e_T (which also adds the
+        // ln A terms of Q through the hook) and the closed-form derivative of
+        // rho cp = (p/T) A/B, A = sum_k Y_k cp_k/(R W_k), B = sum_k Y_k/W_k
         ThetaHook hk{2, vv, gq, th, uu, ud};
-        double fq[n];
-        eval_thread<NS, false, double>(mv, pc, y, fq, C, wd, gRT, hRT, cpR, Jv, &hk);
+        double e0[n], b0[n], fq[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) e0[i] = i == 0 ? 1.0 : 0.0;
+        eval_vjp<NS, double>(mv, pc, y, e0, b0, fq, C, wd, gRT, hRT, cpR, sg, vs, &hk);
+        const double T = y[0];
+        double A = 0.0, B = 0.0, dA = 0.0;
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          const double* c7 = mv.sp + SP_REC * k + 2;
+          const double iW = mv.sp[SP_REC * k + 1];
+          A += y[1 + k] * cpR[k] * iW;
+          B += y[1 + k] * iW;
+          dA += y[1 + k] * (c7[1] + T * (2.0 * c7[2] + T * (3.0 * c7[3] + T * 4.0 * c7[4]))) * iW;
+        }
+        const double rcp = pc / T * A / B;
+        const double w = gq * 0.1;
+        lam[0] += w * (rcp * b0[0] + fq[0] * pc * (dA / (T * B) - A / (T * T * B)));
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          lam[1 + k] += w * (rcp * b0[1 + k] + fq[0] * (pc / T) * mv.sp[SP_REC * k + 1] * (cpR[k] - A / B) / B);
       }
       // ---- reverse sweep over the accepted steps -----------------------
       for (int istep = nacc - 1; istep >= 0; --istep) {
@@ -243,30 +256,23 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
           }
           {
             ThetaHook hk{1, vv, 0.0, th, uu, ud};
-            eval_thread<NS, true, double>(mv, pc, ysg, fs, C, wd, gRT, hRT, cpR, Jv, &hk);
-          }
+            double bj[n];
+            eval_vjp<NS, double>(mv, pc, ysg, r, bj, fs, C, wd, gRT, hRT, cpR, sg, vs, &hk);
 #pragma unroll
-          for (int jc = 0; jc < n; ++jc) {
-            double acc = 0.0;
-#pragma unroll
-            for (int i = 0; i < n; ++i) acc += Jv[i * n + jc] * r[i];
-            yb[jc] += acc;
-            for (int j = 0; j < s; ++j) Kb[j * n + jc] += tb.a[s][j] * acc;
+            for (int jc = 0; jc < n; ++jc) {
+              yb[jc] += bj[jc];
+              for (int j = 0; j < s; ++j) Kb[j * n + jc] += tb.a[s][j] * bj[jc];
+            }
           }
           // W depends on y through J(y): d/de [J(y + e K_s)^T Rbar] and the ln A analogue
           {
-            Dual yd[n], fd[n];
+            Dual yd[n], fd[n], bd[n];
 #pragma unroll
             for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kv[s * n + i]);
             ThetaHook hk{1, vv, 0.0, th, uu, ud};
-            eval_thread<NS, true, Dual>(mv, pc, yd, fd, dC, dW, dG, dH, dCp, dJ, &hk);
+            eval_vjp<NS, Dual>(mv, pc, yd, r, bd, fd, dC, dW, dG, dH, dCp, dS, dV, &hk);
 #pragma unroll
-            for (int jc = 0; jc < n; ++jc) {
-              double acc = 0.0;
-#pragma unroll
-              for (int i = 0; i < n; ++i) acc += dJ[i * n + jc].d * r[i];
-              yb[jc] += acc;
-            }
+            for (int jc = 0; jc < n; ++jc) yb[jc] += bd[jc].d;
           }
         }
 #pragma unroll
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
   if (a.partial) {
     for (int j = tid; j < M; j += stride) {
       double acc = 0.0;
-      for (int q = 0; q < stride; ++q) acc += base[(size_t)(10 * NS + 2 * n * n + n * n + 12 * n + j) * stride + q];
+      for (int q = 0; q < stride; ++q) acc += base[(size_t)(14 * NS + n * n + 12 * n + j) * stride + q];
       a.partial[(int64_t)blockIdx.x * M + j] = acc;
     }
   }

@@ -373,6 +373,140 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
   return -Hw;
 }
 
+// b = J(y)^T r for a fixed vector r, without forming J: the transpose of the
+// assembly in eval_thread, accumulated reaction by reaction (reverse mode).
+// With rho_k = r_{1+k} + r_0 c_k, c_k = -R T h_k/(RT) / (W_k cp) the weight of
+// species row k in the temperature row, and sigma_k = W_k rho_k:
+//   v_i = sum_k sigma_k dwdot_k/dC_i,   v_T = sum_k sigma_k dwdot_k/dT|_C
+// (each reaction adds w_j dq_j/dC_i and w_j dq_j/dT, w_j = sum over its
+// products of sigma minus sum over its reactants), D = sum_k sigma_k wdot_k -
+// sum_l v_l C_l, and then
+//   b_T     = (v_T + D / T) / rho + r_0 e_T
+//   b_{Y_i} = (v_i + D Wbar / rho) / W_i + r_0 e_i
+// with e the temperature row's own terms (e_T = -(cpf + f_T dcp/dT) / cp,
+// e_i = -f_T cp_i / cp).  Also returns f = dy/dt (f may alias nothing) and, with
+// a hook, its ln A terms.  sig and v are N-entry scratch vectors.
+template <int NS, class S = double>
+__device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, const S (&y)[NS + 1],
+                                         const double (&r)[NS + 1], S (&b)[NS + 1], S (&f)[NS + 1], SVT<S> C,
+                                         SVT<S> wdot, SVT<S> gRT, SVT<S> hRT, SVT<S> cpR, SVT<S> sig, SVT<S> v,
+                                         const ThetaHook* hook = nullptr) {
+  const S T = y[0];
+  const S lnT = log(T);
+  const S invT = 1.0 / T;
+  S sumYW(0.0), cpm(0.0);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* a = mv.sp + SP_REC * k + 2;
+    const S cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    cpR[k] = cpk;
+    const S hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
+                 a[5] * invT;
+    const S sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    hRT[k] = hk;
+    gRT[k] = hk - sk;
+    sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];
+    cpm += y[1 + k] * cpk * mv.sp[SP_REC * k + 1];
+  }
+  cpm = cpm * RU;
+  const S rho = pc * invT / (RU * sumYW);
+  const S invrho = 1.0 / rho;
+  const S invcp = 1.0 / cpm;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
+    wdot[k] = S(0.0);
+    v[k] = S(0.0);
+    const S ck = -(invcp * (RU * T) * hRT[k] * mv.sp[SP_REC * k + 1]);
+    sig[k] = mv.sp[SP_REC * k] * (r[1 + k] + r[0] * ck);
+  }
+  if (hook && hook->mode) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const S Hk = RU * T * hRT[k];
+      S uk;
+      if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * hook->v[1 + k] - hook->v[0] * Hk * invcp) * invrho;
+      else uk = -0.1 * hook->g * Hk;
+      u_store(*hook, k, uk);
+    }
+  }
+  S vT(0.0);
+  const S lnP0RT = LOG_PSTD_RU - lnT;
+  for (int j = 0; j < mv.M; ++j) {
+    RateOutT<S> ro;
+    rate_one<NS, true>(mv, mv.rx + RX_REC * j, NS, T, lnT, invT, lnP0RT, C, gRT, hRT, ro);
+    if (!ro.active) continue;
+    const RxMeta mt = ro.mt;
+    const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
+    const S q = ro.q;
+    wdot[mt.reac[0]] -= q;
+    if (nr > 1) wdot[mt.reac[1]] -= q;
+    if (nr > 2) wdot[mt.reac[2]] -= q;
+    wdot[mt.prod[0]] += q;
+    if (np > 1) wdot[mt.prod[1]] += q;
+    if (np > 2) wdot[mt.prod[2]] += q;
+    if (hook && hook->mode) {
+      S w = u_load(*hook, mt.prod[0], q) - u_load(*hook, mt.reac[0], q);
+      if (np > 1) w += u_load(*hook, mt.prod[1], q);
+      if (np > 2) w += u_load(*hook, mt.prod[2], q);
+      if (nr > 1) w -= u_load(*hook, mt.reac[1], q);
+      if (nr > 2) w -= u_load(*hook, mt.reac[2], q);
+      th_add(*hook, j, q * w);
+    }
+    S w = sig[mt.prod[0]] - sig[mt.reac[0]];
+    if (np > 1) w += sig[mt.prod[1]];
+    if (np > 2) w += sig[mt.prod[2]];
+    if (nr > 1) w -= sig[mt.reac[1]];
+    if (nr > 2) w -= sig[mt.reac[2]];
+    vT += w * ro.dqdT;
+    const S wf = w * ro.fk, wr = w * ro.rk;
+    v[mt.reac[0]] += wf * (ro.cr[1] * ro.cr[2]);
+    if (nr > 1) v[mt.reac[1]] += wf * (ro.cr[0] * ro.cr[2]);
+    if (nr > 2) v[mt.reac[2]] += wf * (ro.cr[0] * ro.cr[1]);
+    v[mt.prod[0]] -= wr * (ro.cp[1] * ro.cp[2]);
+    if (np > 1) v[mt.prod[1]] -= wr * (ro.cp[0] * ro.cp[2]);
+    if (np > 2) v[mt.prod[2]] -= wr * (ro.cp[0] * ro.cp[1]);
+    const int type = mt.flags & 3;
+    if (type != 0) {
+      const double* ef = mv.eff + NS * ro.sl.eff;
+      const S wM = w * ro.dqdM;
+#pragma unroll
+      for (int l = 0; l < NS; ++l) v[l] += wM * ef[l];
+    }
+  }
+  S Hw(0.0), sw(0.0), svc(0.0);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    Hw += hRT[k] * wdot[k];
+    sw += sig[k] * wdot[k];
+    svc += v[k] * C[k];
+  }
+  Hw = Hw * (RU * T);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;
+  f[0] = -(Hw * invrho * invcp);
+  S dcp(0.0), cpf(0.0);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* a = mv.sp + SP_REC * k + 2;
+    const double iW = mv.sp[SP_REC * k + 1];
+    dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
+    cpf += cpR[k] * iW * f[1 + k];
+  }
+  dcp = dcp * RU;
+  cpf = cpf * RU;
+  const S D = sw - svc;
+  const S Wbar = 1.0 / sumYW;
+  b[0] = invrho * (vT + invT * D) - r[0] * (invcp * (cpf + f[0] * dcp));
+  const S DW = Wbar * invrho * D;
+  const S fcp = r[0] * f[0] * invcp * RU;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const double iWi = mv.sp[SP_REC * i + 1];
+    b[1 + i] = (v[i] + DW) * iWi - fcp * cpR[i] * iWi;
+  }
+}
+
 // LU with partial pivoting of the n x n matrix in the strided view A; whole rows
 // are swapped, the reciprocal of each pivot replaces the diagonal.  The matrix
 // stays in shared memory, so the pivot loop is not unrolled (register budget).
