@@ -33,10 +33,12 @@ METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
 UNIT = "cell-steps/s"
 # FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
 # 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
-# DP thread-instruction counters (2*DFMA + DADD + DMUL = 3.42e9) of one launch on
-# 65536 cells of this field divided by the 152525 attempts that launch counted
-# (profiles/integrator_thread9_h2air_bimodal.md).
-FLOP_PER_SUBSTEP = 22416
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.9698e10) of one timed
+# launch on the 2^20-cell field divided by the 2199716 attempts that launch
+# counted (profiles/integrator_thread9_h2air_bimodal.md).
+FLOP_PER_SUBSTEP = 22593
+# dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
+TRAFFIC_PER_LAUNCH = 181392128 + 215080192
 
 
 def _rank_info():
@@ -464,7 +466,11 @@ def main():
     if FLOP_PER_SUBSTEP:
         achieved = FLOP_PER_SUBSTEP * subs / (t_local / args.steps) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
-                "frac": achieved / (fp64_peak / 1e3), "traffic": None,
+                "frac": achieved / (fp64_peak / 1e3),
+                "traffic": TRAFFIC_PER_LAUNCH if ncells == NCELLS else None,
+                "traffic_note": "ncu DRAM bytes of one 2^20-cell launch; 2.2x the 180 MB of cell state read "
+                                "and written, from 8-byte accesses in hottest-first cell order (32-byte sectors); "
+                                "0.07% of HBM bandwidth over the launch",
                 "peak_source": "measured FP64 DFMA throughput (df_probe_fp64_peak), this GPU, this run",
                 "flop_per_substep": FLOP_PER_SUBSTEP}
     line = {

@@ -225,28 +225,44 @@ __device__ __forceinline__ double ipow(double a, int e) {
 }
 
 // Y^lambda in FP64 without a logarithm, for lambda = 1/m with m an integer.
-// Y = f 2^(m q) exactly (frexp, then the exponent remainder moved into f, so
-// f lies in [1/2, 2^(m-1))), hence Y^lambda = f^(1/m) 2^q.  f^(1/m) is seeded
-// in FP32 (relative error ~2e-7) and refined by one Newton step on x^m = f,
-// x <- x - x (1 - f / x^m) / m, which squares the relative error (to about
-// (m-1)/2 * 4e-14); the reciprocal of x^m is an FP32 seed plus one Newton
-// step.  About ten FP64 operations against a logarithm and an exponential.
+// Y = f 2^(m q) exactly (integer operations on the exponent field: f keeps
+// Y's mantissa with exponent r = e mod m, so f lies in [1, 2^m)), hence
+// Y^lambda = f^(1/m) 2^q.  f^(1/m) is seeded in FP32 (relative error ~2e-7)
+// and refined by one Newton step on x^m = f, x <- x - x (1 - f / x^m) / m,
+// which squares the relative error (to about (m-1)/2 * 4e-14); 1 / x^m is an
+// FP32 reciprocal refined by one Newton step.  Nine FP64 operations where a
+// logarithm and an exponential take several times that on the narrow FP64
+// pipe.  f^(1/m) lies in [1, 2), so 2^q goes straight into the exponent
+// field (the result is never subnormal for lambda <= 1).
 __device__ __forceinline__ double ylam_newton(double Y, int m, float lamf, double inv_m) {
   if (!(Y > 0.0)) return 0.0;
-  int e;
-  double f = frexp(Y, &e);
+  int eadj = 0;
+  if (Y < 2.2250738585072014e-308) {  // subnormal: scale by 2^54 first
+    Y *= 18014398509481984.0;
+    eadj = -54;
+  }
+  const long long bits = __double_as_longlong(Y);
+  const int e = (int)((bits >> 52) & 0x7FF) - 1023 + eadj;
   int q = e / m, r = e - q * m;
   if (r < 0) {
     r += m;
     --q;
   }
-  f = ldexp(f, r);
-  const double x0 = (double)powf((float)f, lamf);
-  const double xm = ipow(x0, m);
+  const double f = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | ((long long)(r + 1023) << 52));
+  const float x0f = powf((float)f, lamf);
+  const double x0 = (double)x0f;
+  double xm;
+  if (m == 10) {
+    const double x2 = x0 * x0, x4 = x2 * x2;
+    xm = x4 * x4 * x2;
+  } else {
+    xm = ipow(x0, m);
+  }
   const double r0 = (double)__frcp_rn((float)xm);
   const double r1 = r0 * fma(-xm, r0, 2.0);
   const double d = fma(-f, r1, 1.0);
-  return ldexp(fma(-x0 * inv_m, d, x0), q);
+  const double x1 = fma(x0, -inv_m * d, x0);
+  return __longlong_as_double(__double_as_longlong(x1) + ((long long)q << 52));
 }
 
 // Inference features (stage 1): the encoding of k_dnn_features (F(Y) in FP64,
@@ -276,13 +292,13 @@ __global__ void k_dnn_features_infer(FeatInferArgs a) {
   for (int k = 0; k < DNN_IN; ++k) xb[k] = __float2bfloat16_rn(0.0f);
   xb[0] = __float2bfloat16_rn(((float)a.T[c] - mean_in[0]) / std_in[0]);
   xb[1] = __float2bfloat16_rn(((float)a.p[c] - mean_in[1]) / std_in[1]);
-  const double lam = 1.0 / a.inv_lam, inv_m = lam;
+  const double inv_m = 1.0 / a.inv_lam, mm = (double)a.inv_lam;
 #pragma unroll
   for (int k = 0; k < DNN_IN - 2; ++k) {
     if (k < a.N) {
       const double yl = ylam_newton(a.Y[(int64_t)k * a.ncells + c], a.inv_lam, a.lam, inv_m);
       a.Yl[(int64_t)k * a.ldYl + i] = (float)yl;
-      const float fk = (float)((yl - 1.0) / lam);
+      const float fk = (float)fma(yl, mm, -mm);  // (Y^lambda - 1) / lambda
       xb[2 + k] = __float2bfloat16_rn((fk - mean_in[2 + k]) / std_in[2 + k]);
     }
   }
@@ -405,7 +421,7 @@ struct PostArgs {
 };
 
 // Stage 3 of the inference: Y' = F^{-1}(F(Y) + u), renormalised, and T' from
-// h(T', Y') = h(T, Y) at fixed p by Newton (FP64).
+// h(T', Y') = h(T, Y) at fixed p.
 //
 // Y' is formed as Y + dY.  With z = Y^lambda and r = lambda u / z, Y' = Y (1 + r)^m
 // (m = 1/lambda) exactly, so for |r| <= 1/2 dY = Y expm1(m log1p(r)) carries the
@@ -413,17 +429,22 @@ struct PostArgs {
 // ratio, so its FP32 value suffices.  For larger changes (and Y = 0), Y' = (z +
 // lambda u)^m directly.
 //
-// The enthalpy per unit mass over R is a polynomial in T once the species are
-// mixed: h = sum_k Y_k/W_k (a6 + a1 T + a2 T^2/2 + a3 T^3/3 + a4 T^4/4 + a5 T^5/5),
-// cp its derivative, so each Newton iteration costs two Horner evaluations.
+// T' = T + tau with the enthalpy balance written in differences, so it needs no
+// FP64: with h_k(T) = sum_j c_kj T^j the NASA-7 enthalpy over R per unit mass,
+//   sum_k Y'_k [h_k(T + tau) - h_k(T)] = sum_k (Y_k - Y'_k) h_k(T) = R,
+// and the left side is tau (t1 + tau (t2 + ... tau t5)), t_i the Taylor
+// coefficients at T of the mixture polynomial sum_k Y'_k h_k (t1 = cp/R).  Every
+// term keeps its relative precision in FP32 (no large h is ever subtracted), and
+// Newton on tau converges in a few steps; only Y' - Y, the renormalisation and
+// T + tau are FP64.
 __global__ void k_dnn_post(PostArgs a) {
-  __shared__ double hc[DNN_OUT][6];
+  __shared__ float hc[DNN_OUT][6];
   const double* sp = a.blob + a.d.off_sp;
   for (int t = threadIdx.x; t < a.N * 6; t += blockDim.x) {
     const int k = t / 6, j = t % 6;
     const double iw = sp[SP_REC * k + 1];
     const double* c7 = sp + SP_REC * k + 2;
-    hc[k][j] = iw * (j == 0 ? c7[5] : c7[j - 1] / (double)j);
+    hc[k][j] = (float)(iw * (j == 0 ? c7[5] : c7[j - 1] / (double)j));
   }
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -437,20 +458,18 @@ __global__ void k_dnn_post(PostArgs a) {
   const float* std_out = a.norm + 4 * DNN_IN + DNN_OUT;
   const float lamf = (float)a.lam;
   const float m = (float)a.inv_lam;
-  double Yn[DNN_OUT];
-  double h0c[6] = {0, 0, 0, 0, 0, 0};
+  double Yo[DNN_OUT], Yn[DNN_OUT];
   double s = 0.0;
 #pragma unroll
   for (int k = 0; k < DNN_OUT; ++k) {
     if (k < a.N) {
       const double y = a.Y[(int64_t)k * a.ncells + c];
-#pragma unroll
-      for (int j = 0; j < 6; ++j) h0c[j] = fma(y, hc[k][j], h0c[j]);
+      Yo[k] = y;
       const float lu = lamf * fmaf(a.U[i * DNN_OUT + k], std_out[k], mean_out[k]);
       const float z = a.Yl[(int64_t)k * a.ldYl + i];
       double yn;
       if (z > 0.0f && fabsf(lu) <= 0.5f * z) {
-        yn = y + y * (double)expm1f(m * log1pf(lu / z));
+        yn = fma(y, (double)expm1f(m * log1pf(lu / z)), y);
       } else {
         const double zz = (double)z + (double)lu;
         yn = zz > 0.0 ? ipow(zz, a.inv_lam) : 0.0;
@@ -459,27 +478,47 @@ __global__ void k_dnn_post(PostArgs a) {
       s += yn;
     }
   }
-  const double is = s > 0.0 ? 1.0 / s : 0.0;
-  double hm[6] = {0, 0, 0, 0, 0, 0};
+  // 1 / s: FP32 reciprocal and one Newton step (s is within rounding of 1)
+  double is = 0.0;
+  if (s > 0.0) {
+    const double r0 = (double)__frcp_rn((float)s);
+    is = r0 * fma(-s, r0, 2.0);
+  }
+  const double T0 = a.T[c];
+  const float Tf = (float)T0;
+  float D[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float R = 0.0f;
 #pragma unroll
   for (int k = 0; k < DNN_OUT; ++k) {
     if (k < a.N) {
       Yn[k] *= is;
+      const float yf = (float)Yn[k];
+      const float dy = (float)(Yo[k] - Yn[k]);
+      float hk = hc[k][5];
 #pragma unroll
-      for (int j = 0; j < 6; ++j) hm[j] = fma(Yn[k], hc[k][j], hm[j]);
+      for (int j = 4; j >= 0; --j) hk = fmaf(hk, Tf, hc[k][j]);
+      R = fmaf(dy, hk, R);
+#pragma unroll
+      for (int j = 0; j < 6; ++j) D[j] = fmaf(yf, hc[k][j], D[j]);
     }
   }
-  const double T0 = a.T[c];
-  const double h0 = h0c[0] + T0 * (h0c[1] + T0 * (h0c[2] + T0 * (h0c[3] + T0 * (h0c[4] + T0 * h0c[5]))));
-  double T = T0;
-  for (int it = 0; it < 20; ++it) {
-    const double h = hm[0] + T * (hm[1] + T * (hm[2] + T * (hm[3] + T * (hm[4] + T * hm[5]))));
-    const double cp = hm[1] + T * (2.0 * hm[2] + T * (3.0 * hm[3] + T * (4.0 * hm[4] + T * 5.0 * hm[5])));
-    const double dT = (h - h0) / cp;
-    T -= dT;
-    if (fabs(dT) <= 1e-12 * T) break;
+  // Taylor coefficients at T of sum_j D_j x^j: t_i = sum_{j >= i} C(j, i) D_j T^(j-i)
+  const float T1 = Tf, T2 = T1 * T1, T3 = T2 * T1, T4 = T3 * T1;
+  const float t1 = D[1] + 2.f * D[2] * T1 + 3.f * D[3] * T2 + 4.f * D[4] * T3 + 5.f * D[5] * T4;
+  const float t2 = D[2] + 3.f * D[3] * T1 + 6.f * D[4] * T2 + 10.f * D[5] * T3;
+  const float t3 = D[3] + 4.f * D[4] * T1 + 10.f * D[5] * T2;
+  const float t4 = D[4] + 5.f * D[5] * T1;
+  const float t5 = D[5];
+  float tau = R / t1;
+#pragma unroll 1
+  for (int it = 0; it < 8; ++it) {
+    const float g = tau * (t1 + tau * (t2 + tau * (t3 + tau * (t4 + tau * t5)))) - R;
+    const float dg = t1 + tau * (2.f * t2 + tau * (3.f * t3 + tau * (4.f * t4 + tau * 5.f * t5)));
+    const float step = g / dg;
+    tau -= step;
+    if (fabsf(step) <= 1e-7f * fabsf(tau)) break;
   }
-  a.T[c] = T;
+  a.T[c] = T0 + (double)tau;
 #pragma unroll
   for (int k = 0; k < DNN_OUT; ++k)
     if (k < a.N) a.Y[(int64_t)k * a.ncells + c] = Yn[k];
