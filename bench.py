@@ -98,6 +98,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def field_seed(rank: int) -> int:
+    """Seed of a rank's own cells: every replica advances a different field of
+    the same distribution (independent cells, no data-path exchange)."""
+    from paper_2210_07094_gb300 import synth
+    return synth.FIELD_SEED + 1 + 7919 * rank
+
+
+def whole_job_rate(t_local_s: float, units_local: int, dist=None, device="cpu"):
+    """Whole-job throughput over all ranks: the units every rank processed
+    divided by the slowest rank's time (max over ranks).  Returns (rate,
+    t_max, units_total)."""
+    import torch
+    t = torch.tensor([float(t_local_s)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    t_max, units = float(t.item()), float(u.item())
+    return units / t_max, t_max, units
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -359,7 +380,7 @@ def main():
     mech = synth.h2_air_mechanism()
     m = df.Mechanism(mech)
     # each rank advances its own 2^20 cells (independent cells: weak scaling)
-    f = synth.field(1, mech, ncells, seed=synth.FIELD_SEED + 1 + 7919 * rank)
+    f = synth.field(1, mech, ncells, seed=field_seed(rank))
     dev = torch.device("cuda", local)
     T0 = torch.tensor(f["T"], device=dev)
     p = torch.tensor(f["p"], device=dev)
@@ -417,11 +438,7 @@ def main():
     clk = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * ncells * args.steps / t_max
+    value, t_max, _ = whole_job_rate(t_local, ncells * args.steps, dist, dev)
     st = status.cpu().numpy()
     ns = nsub.cpu().numpy()
 
@@ -449,10 +466,7 @@ def main():
         st_h.copy_(status, non_blocking=True)
         torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
-    te = torch.tensor([e2e_t], device=dev)
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * ncells * e2e_steps / float(te.item())
+    e2e_value, _, _ = whole_job_rate(e2e_t, ncells * e2e_steps, dist, dev)
 
     peaks = _peaks()
     subs = (acc_tot + rej_tot) / args.steps
