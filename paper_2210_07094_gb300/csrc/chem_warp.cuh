@@ -5,7 +5,8 @@
 //   wdot, J     - lanes over species rows, summing their reactions from a
 //                 species -> (reaction, nu) list (fixed order: deterministic,
 //                 no atomics),
-//   LU          - pivot search by warp reduction, trailing update over columns,
+//   LU          - pivot search by warp reduction, trailing update dealt
+//                 element by element over the lanes,
 //   solves      - column-oriented substitution, one __syncwarp per step.
 // All per-cell vectors and the dense (N+1)^2 matrix live in shared memory.
 #pragma once
@@ -111,19 +112,36 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     }
   }
   __syncwarp();
-  // species production rates, cp, heat release
+  // species production rates, cp, heat release.  Each lane sums the reaction
+  // lists of its (at most two) species in one loop over their concatenation,
+  // so the warp waits for the longest pair, not for the longest list of each
+  // of two rounds; each list is still summed in its own fixed order.
+  const int* asg = csr + N + 1 + 2 * csr[N] + 2 * lane;
+  const int ka = asg[0], kb = asg[1];
+  const int ba = ka >= 0 ? csr[ka] : 0, la = ka >= 0 ? csr[ka + 1] - ba : 0;
+  const int bb = kb >= 0 ? csr[kb] : 0, lb = kb >= 0 ? csr[kb + 1] - bb : 0;
   double cpp = 0.0, hwp = 0.0;
-  for (int k = lane; k < N; k += 32) {
-    double w = 0.0;
-    for (int e = csr[k]; e < csr[k + 1]; ++e) {
-      const int j = csr[N + 1 + 2 * e];
-      const int nu = csr[N + 2 + 2 * e];
-      w += nu * ws[L.q + j];
+  {
+    double wa = 0.0, wb = 0.0;
+    for (int t = 0; t < la + lb; ++t) {
+      const bool first = t < la;
+      const int e = first ? ba + t : bb + (t - la);
+      const double c = csr[N + 2 + 2 * e] * ws[L.q + csr[N + 1 + 2 * e]];
+      if (first) wa += c;
+      else wb += c;
     }
-    wdot[k] = w;
-    cpp += y[1 + k] * cpR[k] * mv.sp[SP_REC * k + 1];
-    hwp += hRT[k] * w;
+    if (ka >= 0) {
+      wdot[ka] = wa;
+      cpp += y[1 + ka] * cpR[ka] * mv.sp[SP_REC * ka + 1];
+      hwp += hRT[ka] * wa;
+    }
+    if (kb >= 0) {
+      wdot[kb] = wb;
+      cpp += y[1 + kb] * cpR[kb] * mv.sp[SP_REC * kb + 1];
+      hwp += hRT[kb] * wb;
+    }
   }
+  __syncwarp();
   const double cpm = RU * warp_sum(cpp);
   const double Hw = RU * T * warp_sum(hwp);
   const double invrho = 1.0 / rho;
@@ -134,11 +152,17 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   if (WITH_J) {
     double* J = ws + L.J;
     const double Wbar = 1.0 / sumYW;
-    for (int k = lane; k < N; k += 32) {
-      double* row = J + (1 + k) * n;
-      for (int c = 0; c < n; ++c) row[c] = 0.0;
-      // concentration-space row: sum over this species' reactions
-      for (int e = csr[k]; e < csr[k + 1]; ++e) {
+    // concentration-space rows of this lane's species: one loop over the
+    // concatenation of their reaction lists (as for the production rates)
+    if (ka >= 0)
+      for (int c = 0; c < n; ++c) J[(1 + ka) * n + c] = 0.0;
+    if (kb >= 0)
+      for (int c = 0; c < n; ++c) J[(1 + kb) * n + c] = 0.0;
+    for (int t = 0; t < la + lb; ++t) {
+      const bool first = t < la;
+      const int e = first ? ba + t : bb + (t - la);
+      double* row = J + (1 + (first ? ka : kb)) * n;
+      {
         const int j = csr[N + 1 + 2 * e];
         const double nu = (double)csr[N + 2 + 2 * e];
         const double* r = mv.rx + RX_REC * j;
@@ -160,7 +184,12 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
           for (int l = 0; l < N; ++l) row[1 + l] += cM * ef[l];
         }
       }
-      // -> (T, Y) space
+    }
+    // -> (T, Y) space, row by row
+    for (int tk = 0; tk < 2; ++tk) {
+      const int k = tk == 0 ? ka : kb;
+      if (k < 0) continue;
+      double* row = J + (1 + k) * n;
       double s = 0.0;
       for (int l = 0; l < N; ++l) s += row[1 + l] * C[l];
       const double Wk = mv.sp[SP_REC * k];
@@ -226,9 +255,24 @@ __device__ bool warp_lu(double* A, int* piv, int n) {
     for (int i = k + 1 + lane; i < n; i += 32) A[i * n + k] *= inv;
     if (lane == 0) A[k * n + k] = inv;
     __syncwarp();
-    for (int j = k + 1 + lane; j < n; j += 32) {
-      const double ukj = A[k * n + j];
-      for (int i = k + 1; i < n; ++i) A[i * n + j] -= A[i * n + k] * ukj;
+    // trailing update of the m x m block: its elements are dealt to the lanes
+    // row by row (element e = i m + j to lane e mod 32), so all 32 lanes stay
+    // busy down to a block of 32 elements
+    const int m = n - 1 - k;
+    if (m > 0) {
+      const int di = 32 / m, dj = 32 - di * m;
+      int i = lane / m, j = lane - (lane / m) * m;
+      const double* urow = A + k * n + k + 1;
+      while (i < m) {
+        double* row = A + (k + 1 + i) * n;
+        row[k + 1 + j] -= row[k] * urow[j];
+        i += di;
+        j += dj;
+        if (j >= m) {
+          j -= m;
+          ++i;
+        }
+      }
     }
     __syncwarp();
   }

@@ -7,6 +7,7 @@
 // nu'_{aj} (reactants) and nu''_{aj} (products); K_f by the Arrhenius law,
 // optional third-body efficiencies and Troe falloff, and NASA-7 thermo from
 // which the equilibrium constant K_c = K_f / K_r follows.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <fstream>
@@ -293,6 +294,36 @@ int parse_mechanism(const char* path, df_mech* m) {
       m->csr_host.push_back(e.first);
       m->csr_host.push_back(e.second);
     }
+  // Lane assignment of the warp path's species loops (production rates and
+  // Jacobian rows): at most two species per lane, balanced by the cost of
+  // their reaction lists (longest first, each to the least-loaded lane that
+  // still has a free slot).  A third-body entry adds a full row of
+  // efficiencies to the Jacobian row.  Table: 32 x (k0, k1), -1 = none.
+  std::vector<std::pair<long, int>> cost(N);
+  for (int k = 0; k < N; ++k) {
+    long c = 0;
+    for (auto& e : lists[k]) {
+      RxMeta meta;
+      memcpy(&meta, &rec[RX_REC * e.first + 3], 8);
+      c += 13 + (((meta.flags & 3) != 0) ? N : 0);
+    }
+    cost[k] = {c, k};
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<long, int>& a, const std::pair<long, int>& b) { return a.first > b.first; });
+  std::vector<int> asg(64, -1);
+  std::vector<long> load(32, 0);
+  std::vector<int> used(32, 0);
+  for (auto& ck : cost) {
+    int best = -1;
+    for (int l = 0; l < 32; ++l)
+      if (used[l] < 2 && (best < 0 || load[l] < load[best])) best = l;
+    if (best < 0) return set_error(DF_EMECH, "more than 64 species");  // excluded by the parser's limit
+    asg[2 * best + used[best]] = ck.second;
+    ++used[best];
+    load[best] += ck.first;
+  }
+  m->csr_host.insert(m->csr_host.end(), asg.begin(), asg.end());
   return DF_OK;
 }
 
