@@ -198,6 +198,23 @@ int df_chem_adjoint_static(const df_mech* mech, int64_t ncells, const double* T0
                            const double* gT1, const double* gY1, const double* gQ1, double* gT0, double* gY0,
                            double* g_lnA, int32_t* status, int32_t* nsub, df_stream_t stream);
 
+/* Advance every cell by nsteps consecutive steps of dt (the repeated CFD step
+ * of the 0D ignition runs, Sec. 3.1) in one persistent launch, and report each
+ * cell's ignition delay as the paper defines it (Sec. 3.1: from [dT/dt]_max).
+ * Same arguments and per-cell status as df_chem_integrate, plus:
+ *   nsteps >= 1: the substep sequence stops at every multiple of dt (the
+ *     step-size controller carries h across the boundaries); max_substeps in
+ *     opts bounds the total over all steps;
+ *   nsub [ncells] (may be NULL): accepted substeps over all steps;
+ *   t_ign [ncells] (device, may be NULL): the time in [0, nsteps*dt) of the
+ *     largest dT/dt among the states at which accepted substeps start (the
+ *     integrator evaluates f there anyway); NaN for a failed cell.
+ * With nsteps = 1 the result equals df_chem_integrate's.  Errors: DF_EINVAL
+ * (also nsteps < 1), DF_ECUDA.  Asynchronous on `stream`. */
+int df_chem_integrate_steps(const df_mech* mech, int64_t ncells, double* T, const double* p, double* Y,
+                            double dt, int32_t nsteps, const df_integ_opts* opts, int32_t* status,
+                            int32_t* nsub, double* t_ign, df_stream_t stream);
+
 /* Choose the integrator's launch shape for this mechanism by timing (the GPU
  * form of the paper's dynamic load balancing, Sec. 3.2: the shape that keeps
  * the lanes of a persistent launch busiest on a given mix of cell stiffness).

@@ -158,6 +158,29 @@ class Mech:
         _load().or_rhs(self.ref, float(p), _ptr(y), _ptr(f), C.addressof(q))
         return f, q.value
 
+    def ignition(self, T, p, Y, dt, nsteps, grid=4, rtol=1e-10):
+        """nsteps consecutive steps of dt (the repeated CFD step of the 0D
+        ignition runs, Sec. 3.1) from (T, p, Y); the ignition delay is the time
+        of [dT/dt]_max (Sec. 3.1), here over a grid of dt/grid.  Returns the
+        final T, Y, the grid time of the largest dT/dt per cell and that rate."""
+        T = np.array(T, dtype=np.float64)
+        Y = np.array(Y, dtype=np.float64)
+        p = np.asarray(p, dtype=np.float64)
+        n = T.shape[0]
+        best = np.full(n, -np.inf)
+        tbest = np.zeros(n)
+        h = dt / grid
+        for k in range(nsteps * grid):
+            for c in range(n):
+                fT = self.rhs(p[c], np.r_[T[c], Y[:, c]])[0][0]
+                if fT > best[c]:
+                    best[c] = fT
+                    tbest[c] = k * h
+            T, Y, st, _ = self.integrate(T, p, Y, h, rtol=rtol)
+            if np.any(st != 0):
+                raise RuntimeError("oracle integration failed")
+        return T, Y, tbest, best
+
     def jac(self, p, y):
         y = np.ascontiguousarray(y, dtype=np.float64)
         n = self.N + 1

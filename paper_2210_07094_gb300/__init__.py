@@ -158,6 +158,28 @@ def integrate(mech: Mechanism, T, p, Y, dt: float, opts: IntegOpts | None = None
     return status, nsub
 
 
+def integrate_steps(mech: Mechanism, T, p, Y, dt: float, nsteps: int, opts: IntegOpts | None = None,
+                    status=None, nsub=None, t_ign=None, stream=None):
+    """Advance every cell by nsteps consecutive steps of dt in place and return
+    (status, nsub, t_ign): t_ign is the time of the largest dT/dt (the
+    ignition delay of Sec. 3.1) per cell."""
+    torch = _torch()
+    n, pT, pp, pY = _cells(mech, T, p, Y)
+    if status is None:
+        status = torch.empty(n, dtype=torch.int32, device=T.device)
+    if nsub is None:
+        nsub = torch.empty(n, dtype=torch.int32, device=T.device)
+    if t_ign is None:
+        t_ign = torch.empty(n, dtype=torch.float64, device=T.device)
+    o = C.byref(opts) if opts is not None else None
+    _lib.check(_lib.load().df_chem_integrate_steps(mech.handle, n, pT, pp, pY, float(dt), int(nsteps), o,
+                                                   _dptr(status, "status", torch.int32, n),
+                                                   _dptr(nsub, "nsub", torch.int32, n),
+                                                   _dptr(t_ign, "t_ign", torch.float64, n), _stream_ptr(stream)),
+               "df_chem_integrate_steps")
+    return status, nsub, t_ign
+
+
 def adjoint(mech: Mechanism, T0, p, Y0, dt: float, gT1=None, gY1=None, gQ1=None,
             opts: IntegOpts | None = None, max_steps: int = 64, stream=None):
     """Discrete adjoint of integrate() (RODAS4, accepted steps frozen).

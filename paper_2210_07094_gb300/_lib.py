@@ -53,6 +53,7 @@ SIGNATURES = [
     ("df_chem_integrate", _i, [_p, _i64, _p, _p, _p, _d, _p, _p, _p, _p]),
     ("df_chem_last_stats", _i, [_p, _p, _p, _p]),
     ("df_chem_autotune", _i, [_p, _i64, _p, _p, _p, _d, _p, _i64, _p, _p, _p]),
+    ("df_chem_integrate_steps", _i, [_p, _i64, _p, _p, _p, _d, C.c_int32, _p, _p, _p, _p, _p]),
     ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),
     ("df_chem_adjoint", _i, [_p, _i64, _p, _p, _p, _d, _p, C.c_int32, _p, _p, _p, _p, _p, _p, _p, _p,
                              _p, _sz, _p]),

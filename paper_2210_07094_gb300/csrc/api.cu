@@ -193,6 +193,30 @@ int df_chem_integrate(const df_mech* mc, int64_t ncells, double* T, const double
   return launch_integrate(m, ncells, T, p, Y, dt, o, status, nsub, (cudaStream_t)stream);
 }
 
+int df_chem_integrate_steps(const df_mech* mc, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                            int32_t nsteps, const df_integ_opts* opts, int32_t* status, int32_t* nsub,
+                            double* t_ign, df_stream_t stream) {
+  df_mech* m = const_cast<df_mech*>(mc);
+  const char* fn = "df_chem_integrate_steps";
+  int rc = check_cells(fn, m, ncells);
+  if (rc || ncells == 0) return rc;
+  if (!(dt >= 0.0) || !std::isfinite(dt) || nsteps < 1)
+    return set_error(DF_EINVAL, "df_chem_integrate_steps: dt must be finite and >= 0, nsteps >= 1");
+  if ((rc = check_dev(fn, "T", T)) || (rc = check_dev(fn, "p", p)) || (rc = check_dev(fn, "Y", Y)) ||
+      (rc = check_dev(fn, "status", status)))
+    return rc;
+  if (nsub && (rc = check_dev(fn, "nsub", nsub))) return rc;
+  if (t_ign && (rc = check_dev(fn, "t_ign", t_ign))) return rc;
+  df_integ_opts o;
+  if (opts) o = *opts;
+  else df_integ_opts_default(&o);
+  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
+      o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.block_threads < 0 || o.block_threads > 1024 ||
+      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0 || o.path < 0 || o.path > 2)
+    return set_error(DF_EINVAL, "df_chem_integrate_steps: invalid options");
+  return launch_integrate_steps(m, ncells, T, p, Y, dt, nsteps, o, status, nsub, t_ign, (cudaStream_t)stream);
+}
+
 int df_chem_autotune(df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y, double dt,
                      const df_integ_opts* base, int64_t sample, df_integ_opts* best, float* best_ms,
                      df_stream_t stream) {

@@ -115,6 +115,9 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
                      double dt, const df_integ_opts& o, int32_t* status, int32_t* nsub,
                      cudaStream_t st);
 int launch_set_lnA(df_mech* m, const double* lnA, cudaStream_t st);
+int launch_integrate_steps(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                           int nsteps, const df_integ_opts& o, int32_t* status, int32_t* nsub, double* t_ign,
+                           cudaStream_t st);
 int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y, double dt,
                        const df_integ_opts& base, int64_t sample, df_integ_opts* best, float* best_ms,
                        cudaStream_t st);
@@ -122,7 +125,8 @@ int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double
 // when given; nwork is then an upper bound used to size the launch)
 int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
                           const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
-                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev = nullptr);
+                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev = nullptr,
+                          int nsteps = 1, double* t_ign = nullptr);
 
 // adjoint (adjoint.cu)
 size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap);

@@ -52,6 +52,8 @@ struct IntegArgs {
   const unsigned long long* nwork_dev;  // if set, the number of cells is read from here
   unsigned long long* counters;    // [0] next cell, [1] accepted, [2] rejected
   int stage_blob;                  // 1: copy the blob into shared memory
+  int nsteps;                      // consecutive steps of dt per cell (>= 1)
+  double* t_ign;                   // optional: time of the largest dT/dt per cell
 };
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -95,9 +97,9 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
 
   int64_t cell = -1;
   bool exhausted = false, done = false, last_rej = false;
-  int status = 0, nacc = 0, nrej = 0;
+  int status = 0, nacc = 0, nrej = 0, istep = 0;
   double y[n];
-  double t = 0.0, h = 0.0;
+  double t = 0.0, h = 0.0, fbest = -INFINITY, tbest = 0.0;
   StepState ss{0.0, 1.0};
   unsigned long long tot_acc = 0, tot_rej = 0;
 
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) a.Y[(int64_t)k * a.ncells + cell] = y[1 + k];
       }
+      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? tbest : NAN;
       a.status[cell] = status;
       if (a.nsub) a.nsub[cell] = nacc;
       tot_acc += nacc;
@@ -138,7 +141,9 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
           ok = ok && isfinite(pc) && pc > 0.0;
           t = 0.0;
           h = fmin(a.h0, a.dt);
-          nacc = nrej = 0;
+          nacc = nrej = istep = 0;
+          fbest = -INFINITY;
+          tbest = 0.0;
           last_rej = false;
           status = ok ? DF_CELL_OK : DF_CELL_NONFINITE;
           done = !ok || !(a.dt > 0.0);
@@ -159,9 +164,20 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
     }
     double ys[n];
     double en;
+    double fT;
+    const double t0 = t;
     const bool ok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR, Jv, Kv,
-                                    stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last);
+                                    stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last, &fT);
+    const int nacc0 = nacc;
     step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
+    if (nacc > nacc0 && fT > fbest) {  // dT/dt at the start of an accepted substep
+      fbest = fT;
+      tbest = istep * a.dt + t0;
+    }
+    if (done && ++istep < a.nsteps) {  // next consecutive step of dt
+      done = false;
+      t = 0.0;
+    }
     if (!done) {
       if (nacc + nrej >= a.max_sub) {
         status = DF_CELL_MAXSTEPS;
@@ -286,7 +302,8 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
     bool done = !okin || !(a.dt > 0.0);
     double t = 0.0, h = fmin(a.h0, a.dt);
     double hacc = 0.0, erracc = 1.0;
-    int nacc = 0, nrej = 0;
+    int nacc = 0, nrej = 0, istep = 0;
+    double fbest = -INFINITY, tbest = 0.0;
     bool last_rej = false;
     while (!done) {
       bool last = false;
@@ -295,6 +312,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         last = true;
       }
       warp_eval<true>(mv, csr, N, pc, ws, L, L.y);
+      const double fT = f[0], t0 = t;
       if (nacc == 0 && nrej == 0) {
         // first trial step from the fastest relative rate (see first_step_limit)
         double r = 0.0;
@@ -360,7 +378,14 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         erracc = fmax(1e-2, en);
         h *= fac;
         last_rej = false;
-        if (t >= a.dt) done = true;
+        if (fT > fbest) {  // dT/dt at the start of an accepted substep
+          fbest = fT;
+          tbest = istep * a.dt + t0;
+        }
+        if (t >= a.dt) {
+          if (++istep < a.nsteps) t = 0.0;  // next consecutive step of dt
+          else done = true;
+        }
       } else {
         ++nrej;
         const double fmin = nacc == 0 ? 1e-4 : 0.2;
@@ -386,6 +411,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
       }
     }
     if (lane == 0) {
+      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? tbest : NAN;
       a.status[cell] = status;
       if (a.nsub) a.nsub[cell] = nacc;
       tot_acc += nacc;
@@ -672,9 +698,17 @@ int launch_integrate(df_mech* m, int64_t ncells, double* T, const double* p, dou
   return launch_integrate_list(m, ncells, T, p, Y, dt, o, status, nsub, nullptr, ncells, st, nullptr);
 }
 
+int launch_integrate_steps(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                           int nsteps, const df_integ_opts& o, int32_t* status, int32_t* nsub, double* t_ign,
+                           cudaStream_t st) {
+  return launch_integrate_list(m, ncells, T, p, Y, dt, o, status, nsub, nullptr, ncells, st, nullptr, nsteps,
+                               t_ign);
+}
+
 int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
                           const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
-                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev) {
+                          int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev, int nsteps,
+                          double* t_ign) {
   int rc = ensure_tables(m->device);
   if (rc) return rc;
   IntegArgs a;
@@ -695,6 +729,8 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   a.method = o.method;
   a.status = status;
   a.nsub = nsub;
+  a.nsteps = nsteps;
+  a.t_ign = t_ign;
   if (!order && o.order_by_T && nwork == ncells && ncells > 1) {
     int32_t* ord = nullptr;
     rc = build_order(m, T, ncells, st, &ord);

@@ -109,10 +109,11 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
                                             double& h, double rtol, double atolY, double atolT, SV C, SV wdot,
                                             SV gRT, SV hRT, SV cpR, SV Jv, SV Kv, int stride,
                                             double (&ynew)[NS + 1], double& en, int* piv_out = nullptr,
-                                            bool first = false, bool* last = nullptr) {
+                                            bool first = false, bool* last = nullptr, double* fT = nullptr) {
   constexpr int n = NS + 1;
   double fs[n];
   eval_thread<NS, true>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  if (fT) *fT = fs[0];
   if (first) {
     const double hl = first_step_limit<n>(y, fs);
     if (hl < h) {

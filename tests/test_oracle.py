@@ -373,3 +373,21 @@ def test_replay_directional_derivative_vs_fd(h2):
             d.append((L(1) - L(-1)) / (2 * eps))
         d_fd = (4 * d[1] - d[0]) / 3  # Richardson
         assert abs(d_cs - d_fd) <= 1e-6 * abs(d_fd), (d_cs, d_fd)
+
+
+def test_ignition_helper_zero_rate_and_additivity():
+    """The oracle's multi-step helper: with every rate zero nothing moves and
+    the largest dT/dt (0) is found at t = 0; otherwise its final state is the
+    single integration over the whole window (time additivity)."""
+    mech = synth.h2_air_mechanism()
+    f = synth.field(0, mech, 6, seed=3)
+    z = Mech(synth.zero_rate(mech))
+    T, Y, tb, best = z.ignition(f["T"], f["p"], f["Y"], 1e-6, 3, grid=2)
+    assert np.array_equal(T, f["T"]) and np.array_equal(Y, f["Y"])
+    assert np.all(tb == 0.0) and np.all(best == 0.0)
+    o = Mech(mech)
+    T1, Y1, tb1, best1 = o.ignition(f["T"], f["p"], f["Y"], 2e-6, 3, grid=2)
+    T2, Y2, _, _ = o.integrate(f["T"], f["p"], f["Y"], 6e-6)
+    assert np.max(np.abs(T1 - T2)) <= 1e-7
+    assert np.max(np.abs(Y1 - Y2)) <= 1e-11
+    assert np.all((tb1 >= 0.0) & (tb1 < 6e-6)) and np.all(np.isfinite(best1))
