@@ -82,16 +82,19 @@ static void thermo(const OMech& m, const S& T, S* cp_R, S* h_RT, S* s_R) {
 // ---------------------------------------------------------------------------
 // reaction rates: net molar production wdot [mol/cm^3/s], per-reaction data
 // ---------------------------------------------------------------------------
+// Reaction rates at (T, Y).  Constant-pressure reactor: rho from the pressure
+// p_pa [Pa] and the ideal-gas law.  Constant-volume reactor (rho_fixed > 0):
+// rho = rho_fixed [g/cm^3] (Sec. 2.2: df0DFoam's constant-volume case).
 template <class S>
 static void rates(const OMech& m, const S& T, double p_pa, const S* Y, S* wdot, S* rho_out,
-                  S* qnet, S* kf_out, S* kr_out, const S* dlnA) {
+                  S* qnet, S* kf_out, S* kr_out, const S* dlnA, double rho_fixed = 0.0) {
   const int N = m.N;
   std::vector<S> cp(N), h(N), s(N), C(N);
   thermo(m, T, cp.data(), h.data(), s.data());
   S sumYW = 0.0;
   for (int k = 0; k < N; ++k) sumYW += Y[k] / m.W[k];
   const double p = 10.0 * p_pa;
-  S rho = p / (RU * T * sumYW);
+  S rho = rho_fixed > 0.0 ? S(rho_fixed) : p / (RU * T * sumYW);
   for (int k = 0; k < N; ++k) C[k] = rho * Y[k] / m.W[k];
   for (int k = 0; k < N; ++k) wdot[k] = 0.0;
   S lnT = std::log(T);
@@ -154,26 +157,31 @@ static void rates(const OMech& m, const S& T, double p_pa, const S* Y, S* wdot, 
   if (rho_out) *rho_out = rho;
 }
 
-// y = (T, Y_1..Y_N); f = dy/dt.  qdot = -sum H_k wdot_k [erg/cm^3/s]
+// y = (T, Y_1..Y_N); f = dy/dt.  Constant pressure: dT/dt = -sum H_k wdot_k /
+// (rho cp), qdot = -sum H_k wdot_k [erg/cm^3/s].  Constant volume (rho_fixed >
+// 0): the internal energy is conserved, dT/dt = -sum U_k wdot_k / (rho cv) with
+// U_k = H_k - R T and cv = cp - R / W (per unit mass), qdot = -sum U_k wdot_k.
 template <class S>
-static void rhs(const OMech& m, double p_pa, const S* y, S* f, S* qdot, const S* dlnA) {
+static void rhs(const OMech& m, double p_pa, const S* y, S* f, S* qdot, const S* dlnA,
+                double rho_fixed = 0.0) {
   const int N = m.N;
   std::vector<S> wdot(N), cp(N), h(N), s(N);
   S rho;
-  rates(m, y[0], p_pa, y + 1, wdot.data(), &rho, (S*)nullptr, (S*)nullptr, (S*)nullptr, dlnA);
+  rates(m, y[0], p_pa, y + 1, wdot.data(), &rho, (S*)nullptr, (S*)nullptr, (S*)nullptr, dlnA, rho_fixed);
   thermo(m, y[0], cp.data(), h.data(), s.data());
-  S cpm = 0.0, Hw = 0.0;
+  const double shift = rho_fixed > 0.0 ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
+  S cm = 0.0, Hw = 0.0;
   for (int k = 0; k < N; ++k) {
-    cpm += y[1 + k] * RU * cp[k] / m.W[k];
-    Hw += RU * y[0] * h[k] * wdot[k];
+    cm += y[1 + k] * RU * (cp[k] - shift) / m.W[k];
+    Hw += RU * y[0] * (h[k] - shift) * wdot[k];
   }
   for (int k = 0; k < N; ++k) f[1 + k] = m.W[k] * wdot[k] / rho;
-  f[0] = -Hw / (rho * cpm);
+  f[0] = -Hw / (rho * cm);
   if (qdot) *qdot = -Hw;
 }
 
 template <class S>
-static void jac_cs(const OMech& m, double p_pa, const double* y, double* J) {
+static void jac_cs(const OMech& m, double p_pa, const double* y, double* J, double rho_fixed = 0.0) {
   const int n = m.N + 1;
   const double hstep = 1e-30;
   std::vector<cplx> yc(n), fc(n);
@@ -181,7 +189,7 @@ static void jac_cs(const OMech& m, double p_pa, const double* y, double* J) {
     for (int i = 0; i < n; ++i) yc[i] = cplx(y[i], 0.0);
     double scale = std::max(std::fabs(y[jcol]), 1.0);
     yc[jcol] = cplx(y[jcol], hstep * scale);
-    rhs<cplx>(m, p_pa, yc.data(), fc.data(), (cplx*)nullptr, (const cplx*)nullptr);
+    rhs<cplx>(m, p_pa, yc.data(), fc.data(), (cplx*)nullptr, (const cplx*)nullptr, rho_fixed);
     for (int i = 0; i < n; ++i) J[i * n + jcol] = fc[i].imag() / (hstep * scale);
   }
 }
@@ -248,6 +256,7 @@ struct RadauTab {
 struct Ctx {
   const OMech* m;
   double p;
+  double rho_fixed = 0.0;  // > 0: constant-volume reactor at this density
   int n;
   double rtol, atolY, atolT;
   long nrhs = 0, njac = 0;
@@ -279,7 +288,7 @@ static bool radau_step(Ctx& c, const RadauTab& tab, const double* y0, const doub
   for (int it = 0; it < 25; ++it) {
     for (int s = 0; s < 3; ++s) {
       for (int i = 0; i < n; ++i) yi[i] = y0[i] + Z[s * n + i];
-      rhs<double>(*c.m, c.p, yi.data(), F.data() + s * n, (double*)nullptr, (const double*)nullptr);
+      rhs<double>(*c.m, c.p, yi.data(), F.data() + s * n, (double*)nullptr, (const double*)nullptr, c.rho_fixed);
       c.nrhs++;
     }
     for (int s = 0; s < 3; ++s)
@@ -336,12 +345,12 @@ static int radau_cell(Ctx& c, double* y, double dt, int max_steps, int* nsteps_o
     nstep++;
     bool last = false;
     if (t + h >= dt) { h = dt - t; last = true; }
-    jac_cs<double>(*c.m, c.p, y, J.data());
+    jac_cs<double>(*c.m, c.p, y, J.data(), c.rho_fixed);
     c.njac++;
     bool ok = radau_step(c, tab, y, J.data(), h, yb.data());
     if (ok) ok = radau_step(c, tab, y, J.data(), 0.5 * h, ym.data());
     if (ok) {
-      jac_cs<double>(*c.m, c.p, ym.data(), Jm.data());
+      jac_cs<double>(*c.m, c.p, ym.data(), Jm.data(), c.rho_fixed);
       c.njac++;
       ok = radau_step(c, tab, ym.data(), Jm.data(), 0.5 * h, ys.data());
     }
@@ -515,6 +524,55 @@ int or_integrate(const OMech* m, int64_t ncells, double* T, const double* p, dou
     ctx.atolT = atolT;
     int ns = 0;
     int st = radau_cell(ctx, y.data(), dt, max_steps, &ns);
+    status[c] = st;
+    if (nsteps) nsteps[c] = ns;
+    if (st == 0) {
+      T[c] = y[0];
+      for (int k = 0; k < N; ++k) Y[(int64_t)k * ncells + c] = y[1 + k];
+    }
+  }
+  return 0;
+}
+
+// Constant-volume reactor (Sec. 2.2, df0DFoam): right-hand side and Jacobian at
+// density rho [g/cm^3]; qdot = -sum U_k wdot_k [W/m^3].
+int or_rhs_v(const OMech* m, double rho, const double* y, double* f, double* qdot) {
+  double q;
+  rhs<double>(*m, 0.0, y, f, &q, (const double*)nullptr, rho);
+  if (qdot) *qdot = 0.1 * q;
+  return 0;
+}
+
+int or_jac_v(const OMech* m, double rho, const double* y, double* J) {
+  jac_cs<double>(*m, 0.0, y, J, rho);
+  return 0;
+}
+
+// Constant-volume integration: each cell's density is fixed from its initial
+// state (p[c] [Pa], T, Y) by the ideal-gas law; T and Y are overwritten.
+int or_integrate_v(const OMech* m, int64_t ncells, double* T, const double* p, double* Y, double dt,
+                   double rtol, double atolY, double atolT, int max_steps, int* status, int* nsteps,
+                   int nthreads) {
+  const int N = m->N, n = N + 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+  for (int64_t c = 0; c < ncells; ++c) {
+    std::vector<double> y(n);
+    y[0] = T[c];
+    double sumYW = 0.0;
+    for (int k = 0; k < N; ++k) {
+      y[1 + k] = Y[(int64_t)k * ncells + c];
+      sumYW += y[1 + k] / m->W[k];
+    }
+    Ctx ctx;
+    ctx.m = m;
+    ctx.p = p[c];
+    ctx.rho_fixed = 10.0 * p[c] / (RU * y[0] * sumYW);
+    ctx.n = n;
+    ctx.rtol = rtol;
+    ctx.atolY = atolY;
+    ctx.atolT = atolT;
+    int ns = 0;
+    int st = (ctx.rho_fixed > 0.0 && std::isfinite(ctx.rho_fixed)) ? radau_cell(ctx, y.data(), dt, max_steps, &ns) : 2;
     status[c] = st;
     if (nsteps) nsteps[c] = ns;
     if (st == 0) {

@@ -64,6 +64,9 @@ def _load():
         _lib.or_integrate.argtypes = [p, C.c_int64, p, p, p, d, d, d, d, i, p, p, i]
         _lib.or_rates.argtypes = [p, d, d, p, p, p, p, p, p]
         _lib.or_rhs.argtypes = [p, d, p, p, p]
+        _lib.or_rhs_v.argtypes = [p, d, p, p, p]
+        _lib.or_jac_v.argtypes = [p, d, p, p]
+        _lib.or_integrate_v.argtypes = [p, C.c_int64, p, p, p, d, d, d, d, i, p, p, i]
         _lib.or_jac.argtypes = [p, d, p, p]
         _lib.or_thermo.argtypes = [p, d, p, p, p]
         _lib.or_ros_replay.argtypes = [p, d, p, i, p]
@@ -190,9 +193,12 @@ class Mech:
 
     # -- integration --------------------------------------------------------
     def integrate(self, T, p, Y, dt, rtol=1e-10, atolY=1e-20, atolT=1e-10, max_steps=100000,
-                  threads=None):
+                  threads=None, constant_volume=False):
         """Integrate cells over dt.  Y is species-major [N, ncells].  Returns
-        (T, Y, status, nsteps) as new arrays."""
+        (T, Y, status, nsteps) as new arrays.  constant_volume: each cell's
+        density is fixed from its initial (p, T, Y) and its internal energy is
+        conserved (Sec. 2.2's constant-volume reactor); otherwise p is fixed and
+        the enthalpy conserved."""
         T = np.array(T, dtype=np.float64, copy=True)
         p = np.ascontiguousarray(p, dtype=np.float64)
         Y = np.array(Y, dtype=np.float64, copy=True, order="C")
@@ -201,9 +207,35 @@ class Mech:
         nst = np.zeros(n, np.int32)
         if threads is None:
             threads = os.cpu_count() or 1
-        _load().or_integrate(self.ref, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), rtol, atolY,
-                             atolT, int(max_steps), _ptr(status), _ptr(nst), int(threads))
+        fn = _load().or_integrate_v if constant_volume else _load().or_integrate
+        fn(self.ref, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), rtol, atolY, atolT, int(max_steps),
+           _ptr(status), _ptr(nst), int(threads))
         return T, Y, status, nst
+
+    def rhs_v(self, rho, y):
+        """Constant-volume right-hand side at density rho [g/cm^3]: (f, qdot)."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        f = np.zeros(self.N + 1)
+        q = C.c_double()
+        _load().or_rhs_v(self.ref, float(rho), _ptr(y), _ptr(f), C.addressof(q))
+        return f, q.value
+
+    def jac_v(self, rho, y):
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        n = self.N + 1
+        J = np.zeros((n, n))
+        _load().or_jac_v(self.ref, float(rho), _ptr(y), _ptr(J))
+        return J
+
+    def density(self, T, p, Y):
+        """Ideal-gas density [g/cm^3] from T [K], p [Pa], Y (species-major)."""
+        Y = np.asarray(Y, dtype=np.float64)
+        sumYW = (Y / self.W[:, None]).sum(axis=0) if Y.ndim == 2 else float(np.sum(Y / self.W))
+        return 10.0 * np.asarray(p) / (8.314462618e7 * np.asarray(T) * sumYW)
+
+    def internal_energy_mass(self, T, Y):
+        """Mixture specific internal energy [J/kg]: u = h - R T sum_k Y_k / W_k."""
+        return self.enthalpy_mass(T, Y) - 8.314462618 * T * float(np.sum(np.asarray(Y) / (self.W * 1e-3)))
 
     def ros_step(self, p, y, h):
         y = np.ascontiguousarray(y, dtype=np.float64)

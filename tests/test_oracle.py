@@ -391,3 +391,71 @@ def test_ignition_helper_zero_rate_and_additivity():
     assert np.max(np.abs(T1 - T2)) <= 1e-7
     assert np.max(np.abs(Y1 - Y2)) <= 1e-11
     assert np.all((tb1 >= 0.0) & (tb1 < 6e-6)) and np.all(np.isfinite(best1))
+
+
+# ---------------------------------------------------------------------------
+# constant-volume reactor (Sec. 2.2: df0DFoam's constant-volume case)
+# ---------------------------------------------------------------------------
+
+def test_constant_volume_isomerisation_closed_form():
+    """Equal-enthalpy isomers release no heat, so at constant volume as at
+    constant pressure T stays fixed and Y_A relaxes with rate k_f + k_r."""
+    A, b, Ea, T, a7b = 1.0e6, 0.7, 50.0, 1500.0, 10.7
+    mech = synth.isomer_mechanism(A=A, b=b, Ea=Ea, a7_b=a7b)
+    kf = A * T ** b * np.exp(-Ea * 1e3 / (R * T))
+    Kc = np.exp(a7b - 10.0)
+    lam = kf * (1.0 + 1.0 / Kc)
+    m = Mech(mech)
+    Y0 = [0.7, 0.1, 0.2]
+    for frac in (0.3, 1.0, 3.0):
+        dt = frac / lam
+        T1, Y1, st, _ = m.integrate(np.array([T]), np.array([P_ATM]), np.array(Y0, float).reshape(3, 1), dt,
+                                    rtol=1e-12, atolY=1e-22, atolT=1e-12, constant_volume=True)
+        assert st[0] == 0
+        assert T1[0] == pytest.approx(T, abs=1e-9)
+        assert abs(Y1[0, 0] - _iso_expected(Y0, lam, Kc, dt)) <= 1e-11
+
+
+def test_constant_volume_conserves_internal_energy_and_heats_more(h2):
+    """u(T, Y) is conserved at constant volume; the same composition change
+    releases the same heat into cv instead of cp, so T rises more, by about
+    cp/cv for a small change."""
+    f = synth.field(1, h2.json, 24, seed=41)
+    Tv, Yv, sv, _ = h2.integrate(f["T"], f["p"], f["Y"], f["dt"], constant_volume=True)
+    Tp, Yp, sp, _ = h2.integrate(f["T"], f["p"], f["Y"], f["dt"])
+    assert np.all(sv == 0) and np.all(sp == 0)
+    for c in range(24):
+        u0 = h2.internal_energy_mass(f["T"][c], f["Y"][:, c])
+        u1 = h2.internal_energy_mass(Tv[c], Yv[:, c])
+        assert abs(u1 - u0) <= 1e-9 * 1.5e3 * f["T"][c]
+    dTp, dTv = Tp - f["T"], Tv - f["T"]
+    big = np.abs(dTp) > 1e-3
+    assert big.sum() >= 4
+    ratio = dTv[big] / dTp[big]
+    assert np.all((ratio > 1.1) & (ratio < 1.6)), ratio  # cp/cv of air-like mixtures ~1.3-1.4
+
+
+def test_constant_volume_jacobian_vs_finite_differences(h2):
+    f = synth.field(1, h2.json, 4, seed=5)
+    for c in range(4):
+        y = np.concatenate([[f["T"][c]], f["Y"][:, c]])
+        rho = h2.density(f["T"][c], f["p"][c], f["Y"][:, c])
+        J = h2.jac_v(rho, y)
+        n = y.shape[0]
+        Jf = np.zeros((n, n))
+        for j in range(n):
+            hs = 0.5 if j == 0 else 1e-4 * max(abs(y[j]), 1e-2)
+            cols = []
+            for hh in (hs, hs / 2):
+                yp, ym = y.copy(), y.copy()
+                yp[j] += hh
+                ym[j] -= hh
+                cols.append((h2.rhs_v(rho, yp)[0] - h2.rhs_v(rho, ym)[0]) / (2 * hh))
+            Jf[:, j] = (4 * cols[1] - cols[0]) / 3
+        scale = np.abs(Jf).max(axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(J - Jf) / scale) <= 1e-7
+        # the constant-volume right-hand side differs from the constant-pressure one
+        # only through rho (same here) and cv, U in the temperature row
+        fv = h2.rhs_v(rho, y)[0]
+        fp = h2.rhs(f["p"][c], y)[0]
+        assert np.allclose(fv[1:], fp[1:], rtol=1e-12, atol=0)
