@@ -77,7 +77,14 @@ typedef struct df_integ_opts {
                              together get cells of similar stiffness)          */
   int32_t path;           /* 0: auto (thread per cell if N <= 16), 1: thread per
                              cell, 2: warp per cell                            */
-  int32_t reserved[2];
+  int32_t reactor;        /* 0 (default): constant pressure, p[c] fixed and h
+                             conserved; 1: constant volume (Sec. 2.2), the
+                             density fixed from the initial p[c], T, Y and the
+                             internal energy conserved (df_chem_integrate,
+                             df_chem_integrate_steps, df_chem_autotune; the
+                             adjoint and the DNN integrator are constant
+                             pressure and reject 1 with DF_EUNSUPPORTED)       */
+  int32_t reserved;
 } df_integ_opts;
 
 void df_integ_opts_default(df_integ_opts* opts);

@@ -22,7 +22,8 @@ class IntegOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol_Y", C.c_double), ("atol_T", C.c_double),
                 ("h0", C.c_double), ("h_min", C.c_double), ("max_substeps", C.c_int32),
                 ("method", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("order_by_T", C.c_int32), ("path", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("order_by_T", C.c_int32), ("path", C.c_int32), ("reactor", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class DnnOpts(C.Structure):

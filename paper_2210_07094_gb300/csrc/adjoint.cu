@@ -461,6 +461,7 @@ extern "C" int df_chem_adjoint_static(const df_mech* m, int64_t ncells, const do
   df_integ_opts o;
   if (opts) o = *opts;
   else df_integ_opts_default(&o);
+  if (o.reactor != 0) return set_error(DF_EUNSUPPORTED, "df_chem_adjoint_static: constant-pressure reactor only");
   if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
       o.max_substeps < 1)
     return set_error(DF_EINVAL, "df_chem_adjoint_static: invalid options");

@@ -188,7 +188,8 @@ int df_chem_integrate(const df_mech* mc, int64_t ncells, double* T, const double
   else df_integ_opts_default(&o);
   if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
       o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.block_threads < 0 || o.block_threads > 1024 ||
-      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0 || o.path < 0 || o.path > 2)
+      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0 || o.path < 0 || o.path > 2 ||
+      o.reactor < 0 || o.reactor > 1)
     return set_error(DF_EINVAL, "df_chem_integrate: invalid options");
   return launch_integrate(m, ncells, T, p, Y, dt, o, status, nsub, (cudaStream_t)stream);
 }
@@ -212,7 +213,8 @@ int df_chem_integrate_steps(const df_mech* mc, int64_t ncells, double* T, const 
   else df_integ_opts_default(&o);
   if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
       o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.block_threads < 0 || o.block_threads > 1024 ||
-      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0 || o.path < 0 || o.path > 2)
+      (o.block_threads % 32) != 0 || o.blocks_per_sm < 0 || o.path < 0 || o.path > 2 ||
+      o.reactor < 0 || o.reactor > 1)
     return set_error(DF_EINVAL, "df_chem_integrate_steps: invalid options");
   return launch_integrate_steps(m, ncells, T, p, Y, dt, nsteps, o, status, nsub, t_ign, (cudaStream_t)stream);
 }
@@ -231,7 +233,8 @@ int df_chem_autotune(df_mech* m, int64_t ncells, const double* T, const double* 
   if (base) o = *base;
   else df_integ_opts_default(&o);
   if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
-      o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.path < 0 || o.path > 2)
+      o.max_substeps < 1 || o.method < 0 || o.method > 1 || o.path < 0 || o.path > 2 ||
+      o.reactor < 0 || o.reactor > 1)
     return set_error(DF_EINVAL, "df_chem_autotune: invalid options");
   return autotune_integrate(m, ncells, T, p, Y, dt, o, sample, best, best_ms, (cudaStream_t)stream);
 }
@@ -264,6 +267,7 @@ int df_chem_adjoint(const df_mech* m, int64_t ncells, const double* T0, const do
   df_integ_opts o;
   if (opts) o = *opts;
   else df_integ_opts_default(&o);
+  if (o.reactor != 0) return set_error(DF_EUNSUPPORTED, "df_chem_adjoint: constant-pressure reactor only");
   if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
       o.max_substeps < 1)
     return set_error(DF_EINVAL, "df_chem_adjoint: invalid options");

@@ -215,12 +215,19 @@ __device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) {
 
 // Evaluate f = dy/dt for y = (T, Y) and, when WITH_J, the analytic Jacobian
 // J = df/dy (row-major in the strided view Jv, n x n with n = NS + 1).
-// Returns qdot = -sum_k H_k wdot_k in erg/(cm^3 s).
-template <int NS, bool WITH_J, class S = double>
+// Constant-pressure reactor (CONSTV false): pc is the pressure [dyn/cm^2], rho
+// follows from the ideal-gas law, and the energy balance conserves h.
+// Constant-volume reactor (Sec. 2.2, CONSTV true): pc is the fixed density
+// [g/cm^3]; U_k = H_k - R T and cv = cp - R/W replace H_k and cp in the
+// temperature equation, and C_k = rho Y_k / W_k no longer depends on T or on
+// the mean molar mass.  Returns qdot = -sum_k H_k wdot_k (U_k at constant
+// volume) in erg/(cm^3 s).
+template <int NS, bool WITH_J, class S = double, bool CONSTV = false>
 __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, const S (&y)[NS + 1], S (&f)[NS + 1],
                                          SVT<S> C, SVT<S> wdot, SVT<S> gRT, SVT<S> hRT, SVT<S> cpR, SVT<S> Jv,
                                          const ThetaHook* hook = nullptr) {
   constexpr int n = NS + 1;
+  constexpr double EV = CONSTV ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
   const S T = y[0];
   const S lnT = log(T);
   const S invT = 1.0 / T;
@@ -236,10 +243,10 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
     hRT[k] = hk;
     gRT[k] = hk - sk;
     sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];
-    cpm += y[1 + k] * cpk * mv.sp[SP_REC * k + 1];
+    cpm += y[1 + k] * (cpk - EV) * mv.sp[SP_REC * k + 1];
   }
-  cpm = cpm * RU;
-  const S rho = pc * invT / (RU * sumYW);
+  cpm = cpm * RU;  // cp, or cv at constant volume
+  const S rho = CONSTV ? S(pc) : pc * invT / (RU * sumYW);
   const S invrho = 1.0 / rho;
   const S invcp = 1.0 / cpm;
 #pragma unroll
@@ -250,7 +257,7 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
   if (hook && hook->mode) {
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
-      const S Hk = RU * T * hRT[k];
+      const S Hk = RU * T * (hRT[k] - EV);
       S uk;
       if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * hook->v[1 + k] - hook->v[0] * Hk * invcp) * invrho;
       else uk = -0.1 * hook->g * Hk;
@@ -319,39 +326,48 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
   // heat release
   S Hw(0.0);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) Hw += hRT[k] * wdot[k];
+  for (int k = 0; k < NS; ++k) Hw += (hRT[k] - EV) * wdot[k];
   Hw = Hw * (RU * T);
 #pragma unroll
   for (int k = 0; k < NS; ++k) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;
   f[0] = -(Hw * invrho * invcp);
   if (WITH_J) {
     // species rows: concentration-space Jc[k][l] = d wdot_k / d C_l (stored in
-    // Jv[1+k][1+l]) and dwdot_k/dT at fixed C (Jv[1+k][0]) -> (T, Y) space
+    // Jv[1+k][1+l]) and dwdot_k/dT at fixed C (Jv[1+k][0]) -> (T, Y) space.
+    // At constant pressure C also moves with T and with the mean molar mass;
+    // at constant volume it does not.
     const S Wbar = 1.0 / sumYW;
 #pragma unroll 1
     for (int k = 0; k < NS; ++k) {
       const int row = (1 + k) * n;
-      S s(0.0);
-#pragma unroll
-      for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * C[l];
       const double Wk = mv.sp[SP_REC * k];
-      const S wk = wdot[k];
-      const S a = Wk * Wbar * invrho * (wk - s);
+      if (CONSTV) {
 #pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const double iWi = mv.sp[SP_REC * i + 1];
-        Jv[row + 1 + i] = (Wk * Jv[row + 1 + i] + a) * iWi;
+        for (int i = 0; i < NS; ++i) Jv[row + 1 + i] = Wk * Jv[row + 1 + i] * mv.sp[SP_REC * i + 1];
+        Jv[row] = Wk * invrho * Jv[row];
+      } else {
+        S s(0.0);
+#pragma unroll
+        for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * C[l];
+        const S wk = wdot[k];
+        const S a = Wk * Wbar * invrho * (wk - s);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+          const double iWi = mv.sp[SP_REC * i + 1];
+          Jv[row + 1 + i] = (Wk * Jv[row + 1 + i] + a) * iWi;
+        }
+        Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);
       }
-      Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);
     }
-    // temperature row: f_T = -sum_k h_k f_Yk / cp (h_k specific enthalpy)
+    // temperature row: f_T = -sum_k e_k f_Yk / c with e_k the specific enthalpy
+    // (internal energy) and c = cp (cv)
     S dcp(0.0), cpf(0.0);
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
       const double* a = mv.sp + SP_REC * k + 2;
       const double iW = mv.sp[SP_REC * k + 1];
       dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
-      cpf += cpR[k] * iW * f[1 + k];
+      cpf += (cpR[k] - EV) * iW * f[1 + k];
     }
     dcp = dcp * RU;
     cpf = cpf * RU;
@@ -359,13 +375,13 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
     for (int jc = 0; jc < n; ++jc) {
       S acc(0.0);
 #pragma unroll
-      for (int k = 0; k < NS; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];
+      for (int k = 0; k < NS; ++k) acc += (hRT[k] - EV) * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];
       acc = acc * (RU * T);
       if (jc == 0) {
         Jv[0] = -(invcp * (acc + cpf)) - f[0] * dcp * invcp;
       } else {
         const double iWj = mv.sp[SP_REC * (jc - 1) + 1];
-        const S cpj = RU * cpR[jc - 1] * iWj;
+        const S cpj = RU * (cpR[jc - 1] - EV) * iWj;
         Jv[jc] = -(invcp * acc) - f[0] * cpj * invcp;
       }
     }

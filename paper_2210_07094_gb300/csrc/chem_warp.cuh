@@ -59,9 +59,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Evaluate f(y) (and J when WITH_J) for the state at ws + yoff.
 // csr: [N+1] row pointers, then (reaction, nu) pairs.  Returns qdot in erg/(cm^3 s).
-template <bool WITH_J>
+// pc: pressure [dyn/cm^2], or the fixed density [g/cm^3] of a constant-volume
+// reactor (CONSTV; the same closure as eval_thread).
+template <bool WITH_J, bool CONSTV = false>
 __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc, double* ws, const WarpWS& L,
                             int yoff) {
+  constexpr double EV = CONSTV ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
   const int lane = threadIdx.x & 31;
   const int n = N + 1;
   const double* y = ws + yoff;
@@ -85,7 +88,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     sYW += y[1 + k] * mv.sp[SP_REC * k + 1];
   }
   const double sumYW = warp_sum(sYW);
-  const double rho = pc * invT / (RU * sumYW);
+  const double rho = CONSTV ? pc : pc * invT / (RU * sumYW);
   for (int k = lane; k < N; k += 32) C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
   __syncwarp();
   const double lnP0RT = LOG_PSTD_RU - lnT;
@@ -132,13 +135,13 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     }
     if (ka >= 0) {
       wdot[ka] = wa;
-      cpp += y[1 + ka] * cpR[ka] * mv.sp[SP_REC * ka + 1];
-      hwp += hRT[ka] * wa;
+      cpp += y[1 + ka] * (cpR[ka] - EV) * mv.sp[SP_REC * ka + 1];
+      hwp += (hRT[ka] - EV) * wa;
     }
     if (kb >= 0) {
       wdot[kb] = wb;
-      cpp += y[1 + kb] * cpR[kb] * mv.sp[SP_REC * kb + 1];
-      hwp += hRT[kb] * wb;
+      cpp += y[1 + kb] * (cpR[kb] - EV) * mv.sp[SP_REC * kb + 1];
+      hwp += (hRT[kb] - EV) * wb;
     }
   }
   __syncwarp();
@@ -190,9 +193,14 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       const int k = tk == 0 ? ka : kb;
       if (k < 0) continue;
       double* row = J + (1 + k) * n;
+      const double Wk = mv.sp[SP_REC * k];
+      if (CONSTV) {  // C does not move with T or the mean molar mass
+        for (int i = 0; i < N; ++i) row[1 + i] = Wk * row[1 + i] * mv.sp[SP_REC * i + 1];
+        row[0] = Wk * invrho * row[0];
+        continue;
+      }
       double s = 0.0;
       for (int l = 0; l < N; ++l) s += row[1 + l] * C[l];
-      const double Wk = mv.sp[SP_REC * k];
       const double wk = wdot[k];
       const double a = Wk * Wbar * invrho * (wk - s);
       for (int i = 0; i < N; ++i) row[1 + i] = (Wk * row[1 + i] + a) * mv.sp[SP_REC * i + 1];
@@ -205,16 +213,16 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       const double* a = mv.sp + SP_REC * k + 2;
       const double iW = mv.sp[SP_REC * k + 1];
       dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
-      cpf += cpR[k] * iW * f[1 + k];
+      cpf += (cpR[k] - EV) * iW * f[1 + k];
     }
     dcp = RU * warp_sum(dcp);
     cpf = RU * warp_sum(cpf);
     for (int jc = lane; jc < n; jc += 32) {
       double acc = 0.0;
-      for (int k = 0; k < N; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * J[(1 + k) * n + jc];
+      for (int k = 0; k < N; ++k) acc += (hRT[k] - EV) * mv.sp[SP_REC * k + 1] * J[(1 + k) * n + jc];
       acc *= RU * T;
       if (jc == 0) J[0] = -invcp * (acc + cpf) - fT * dcp * invcp;
-      else J[jc] = -invcp * acc - fT * RU * cpR[jc - 1] * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
+      else J[jc] = -invcp * acc - fT * RU * (cpR[jc - 1] - EV) * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
     }
   }
   __syncwarp();

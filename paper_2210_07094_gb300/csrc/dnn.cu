@@ -1064,6 +1064,7 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
   df_integ_opts o;
   if (fopts) o = *fopts;
   else df_integ_opts_default(&o);
+  if (o.reactor != 0) return set_error(DF_EUNSUPPORTED, "df_dnn_infer: the network is a constant-pressure model");
   if (!rc) rc = cuda_check(cudaEventRecord(d->ev_ranged, st), "event");
   if (!rc) rc = cuda_check(cudaStreamWaitEvent(d->side, d->ev_ranged, 0), "event wait");
   if (!rc)

@@ -66,7 +66,7 @@ __host__ __device__ constexpr int thread_ws_doubles() {
 
 __host__ __device__ inline int blob_smem_doubles(const MechDims& d) { return (d.total + 1) & ~1; }
 
-template <int NS>
+template <int NS, bool CONSTV = false>
 __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   constexpr int n = NS + 1;
   extern __shared__ double smem[];
@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   int status = 0, nacc = 0, nrej = 0, istep = 0;
   double y[n];
   double t = 0.0, h = 0.0, fbest = -INFINITY, tbest = 0.0;
+  double prm = 0.0;  // pressure [dyn/cm^2], or the fixed density [g/cm^3] at constant volume
   StepState ss{0.0, 1.0};
   unsigned long long tot_acc = 0, tot_rej = 0;
 
@@ -139,6 +140,14 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
           }
           const double pc = a.p[cell];
           ok = ok && isfinite(pc) && pc > 0.0;
+          prm = 10.0 * pc;  // Pa -> dyn/cm^2
+          if (CONSTV) {  // density of the initial state, fixed from here on
+            double sYW = 0.0;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) sYW += y[1 + k] * mv.sp[SP_REC * k + 1];
+            prm = prm / (RU * y[0] * sYW);
+            ok = ok && isfinite(prm) && prm > 0.0;
+          }
           t = 0.0;
           h = fmin(a.h0, a.dt);
           nacc = nrej = istep = 0;
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
     if (cell < 0 || done) continue;
 
     // ---- one substep attempt ------------------------------------------------
-    const double pc = 10.0 * a.p[cell];  // Pa -> dyn/cm^2
+    const double pc = prm;
     bool last = false;
     if (t + h >= a.dt) {
       h = a.dt - t;
@@ -166,8 +175,8 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
     double en;
     double fT;
     const double t0 = t;
-    const bool ok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR, Jv, Kv,
-                                    stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last, &fT);
+    const bool ok = ros_attempt<NS, CONSTV>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR,
+                                            Jv, Kv, stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last, &fT);
     const int nacc0 = nacc;
     step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
     if (nacc > nacc0 && fT > fbest) {  // dT/dt at the start of an accepted substep
@@ -257,6 +266,7 @@ __global__ void __launch_bounds__(128) k_eval_thread(EvalArgs a) {
 // ----------------------------------------------------------------------------
 // one cell per warp (any N <= 64)
 // ----------------------------------------------------------------------------
+template <bool CONSTV>
 __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const int* csr, WarpWS L) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -295,9 +305,15 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
       y[i] = v;
       okin = okin && isfinite(v) && (i > 0 || v > 0.0);
     }
-    const double pc = 10.0 * a.p[cell];
+    double pc = 10.0 * a.p[cell];  // Pa -> dyn/cm^2
     okin = __all_sync(WFULL, okin) && isfinite(pc) && pc > 0.0;
     __syncwarp();
+    if (CONSTV) {  // density of the initial state, fixed from here on
+      double s = 0.0;
+      for (int k = lane; k < N; k += 32) s += y[1 + k] * mv.sp[SP_REC * k + 1];
+      pc = pc / (RU * y[0] * warp_sum(s));
+      okin = okin && isfinite(pc) && pc > 0.0;
+    }
     int status = okin ? DF_CELL_OK : DF_CELL_NONFINITE;
     bool done = !okin || !(a.dt > 0.0);
     double t = 0.0, h = fmin(a.h0, a.dt);
@@ -311,7 +327,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         h = a.dt - t;
         last = true;
       }
-      warp_eval<true>(mv, csr, N, pc, ws, L, L.y);
+      warp_eval<true, CONSTV>(mv, csr, N, pc, ws, L, L.y);
       const double fT = f[0], t0 = t;
       if (nacc == 0 && nrej == 0) {
         // first trial step from the fastest relative rate (see first_step_limit)
@@ -341,7 +357,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
             ys[i] = acc;
           }
           __syncwarp();
-          warp_eval<false>(mv, csr, N, pc, ws, L, L.ys);
+          warp_eval<false, CONSTV>(mv, csr, N, pc, ws, L, L.ys);
         }
         for (int i = lane; i < n; i += 32) {
           double acc = f[i];
@@ -553,7 +569,7 @@ int eval_dispatch(const df_mech* m, int64_t ncells, const double* T, const doubl
 }
 
 template <int NS>
-int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, int bps) {
+int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, int bps, bool constv) {
   IntegArgs a = a0;
   a.stage_blob = 1;
   size_t sm = thread_smem_bytes<NS>(m->dims, threads, true);
@@ -563,7 +579,7 @@ int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int thr
   }
   if (sm > m->max_smem_optin)
     return set_error(DF_EUNSUPPORTED, "integrator shared memory exceeds the per-block limit");
-  auto kf = k_integrate_thread<NS>;
+  auto kf = constv ? k_integrate_thread<NS, true> : k_integrate_thread<NS, false>;
   int rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                       "set integrator shared memory");
   if (rc) return rc;
@@ -638,7 +654,7 @@ int eval_warp_dispatch(const df_mech* m, int64_t ncells, const double* T, const 
   return cuda_check(cudaGetLastError(), "warp evaluation kernel");
 }
 
-int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads) {
+int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, bool constv) {
   const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M);
   int warps, stage;
   size_t sm;
@@ -647,7 +663,7 @@ int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, in
   if (rc) return rc;
   IntegArgs a = a0;
   a.stage_blob = stage;
-  auto kf = k_integrate_warp;
+  auto kf = constv ? k_integrate_warp<true> : k_integrate_warp<false>;
   rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                   "set warp integrator shared memory");
   if (rc) return rc;
@@ -751,12 +767,12 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
     bt = m->tuned_threads;
     bps = m->tuned_bps;
   }
-  if (warp_path) return integrate_warp_dispatch(m, a, st, bt);
+  if (warp_path) return integrate_warp_dispatch(m, a, st, bt, o.reactor == 1);
   const int threads = bt > 0 ? bt : 64;
   switch (m->dims.N) {
 #define X(NS) \
   case NS:    \
-    return integrate_dispatch<NS>(m, a, st, threads, bps);
+    return integrate_dispatch<NS>(m, a, st, threads, bps, o.reactor == 1);
     DF_THREAD_NS_LIST(X)
 #undef X
     default:

@@ -104,7 +104,9 @@ __device__ __forceinline__ double first_step_limit(const double (&y)[n], const d
   return r > 0.0 ? FIRST_STEP_THETA / r : INFINITY;
 }
 
-template <int NS>
+// pc: the reactor's fixed state parameter, pressure [dyn/cm^2] (CONSTV false)
+// or density [g/cm^3] (CONSTV true; see eval_thread)
+template <int NS, bool CONSTV = false>
 __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb, double pc, const double (&y)[NS + 1],
                                             double& h, double rtol, double atolY, double atolT, SV C, SV wdot,
                                             SV gRT, SV hRT, SV cpR, SV Jv, SV Kv, int stride,
@@ -112,7 +114,7 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
                                             bool first = false, bool* last = nullptr, double* fT = nullptr) {
   constexpr int n = NS + 1;
   double fs[n];
-  eval_thread<NS, true>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  eval_thread<NS, true, double, CONSTV>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
   if (fT) *fT = fs[0];
   if (first) {
     const double hl = first_step_limit<n>(y, fs);
@@ -139,7 +141,7 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
         for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
         ynew[i] = acc;
       }
-      eval_thread<NS, false>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
+      eval_thread<NS, false, double, CONSTV>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
     }
     // stage right-hand side, solved in place in the K slot of this stage
     SV Ks{&Kv[s * n], stride};
