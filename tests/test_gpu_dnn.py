@@ -79,9 +79,11 @@ def test_train_step_gradients_match_oracle(data):
         assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-12, name
 
 
-def test_infer_pipeline_and_fallback(data):
+# small widths, and the full 1600-800-400 network (its layers take the
+# shared-memory-capped GEMM shapes while fallback blocks share the SMs)
+@pytest.mark.parametrize("widths", [(32, 16, 8), (1600, 800, 400)])
+def test_infer_pipeline_and_fallback(data, widths):
     mech, m, (T0, P, Y0, T1, Y1) = data
-    widths = (32, 16, 8)
     dnn = df.Dnn(_opts(widths), seed=7)
     dnn.fit_norm(T0, P, Y0, Y1)
     o = Mech(mech)
