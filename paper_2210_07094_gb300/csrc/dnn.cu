@@ -70,6 +70,14 @@ struct df_dnn {
   __nv_bfloat16* dZ[3] = {nullptr, nullptr, nullptr};
   __nv_bfloat16* dZT[3] = {nullptr, nullptr, nullptr};
   double* loss_part = nullptr;  // per-block partial sums
+  // training step replayed from a CUDA graph: the batch is copied into these
+  // buffers and the step's scalars (lr, bias corrections) read from train_sc
+  double *bT = nullptr, *bp = nullptr, *bY = nullptr, *bYn = nullptr;
+  float* train_sc = nullptr;
+  cudaGraphExec_t train_exec = nullptr;
+  int64_t train_n = -1;
+  cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
+  bool no_graph = false;              // capture unavailable here: enqueue the kernels directly
   // inference scratch (chunk rows)
   int64_t chunk = 0;
   __nv_bfloat16 *iX = nullptr, *iH[3] = {nullptr, nullptr, nullptr};
@@ -387,10 +395,19 @@ __global__ void k_dnn_rowsum(const __nv_bfloat16* A, int64_t ld, int rows, int64
   if (threadIdx.x == 0) db[r] = (float)red[0];
 }
 
-__global__ void k_adam(float* P, float* m1, float* m2, const float* g, int64_t n, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+// sc = {lr, 1 - beta1^t, 1 - beta2^t} of this step (device memory, so a
+// captured step can be replayed with new values)
+__global__ void k_set_train_scalars(float* sc, float lr, float c1, float c2) {
+  sc[0] = lr;
+  sc[1] = c1;
+  sc[2] = c2;
+}
+
+__global__ void k_adam(float* P, float* m1, float* m2, const float* g, int64_t n, const float* sc, float b1,
+                       float b2, float eps) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const float lr = sc[0], c1 = sc[1], c2 = sc[2];
   const float gi = g[i];
   const float a = b1 * m1[i] + (1.0f - b1) * gi;
   const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
@@ -675,6 +692,11 @@ static int dnn_train_buffers(df_dnn* d) {
   rc = rc ? rc : dev_alloc((void**)&d->dU, B * DNN_OUT * 2);
   rc = rc ? rc : dev_alloc((void**)&d->dUT, B * DNN_OUT * 2);
   rc = rc ? rc : dev_alloc((void**)&d->loss_part, ((B + 255) / 256 + 1) * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->bT, B * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->bp, B * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->bY, B * d->o.n_species * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->bYn, B * d->o.n_species * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->train_sc, 4 * 4);
   return rc;
 }
 
@@ -865,7 +887,9 @@ void df_dnn_free(df_dnn* d) {
   if (!d) return;
   void* ptrs[] = {d->params, d->m1, d->m2, d->grads, d->norm, d->X, d->XT, d->U, d->tgt, d->dU, d->dUT,
                   d->loss_part, d->iX, d->iU, d->imask, d->list, d->fb_status, d->counter, d->err, d->iYl,
-                  d->rawb, d->fb_flag};
+                  d->rawb, d->fb_flag, d->bT, d->bp, d->bY, d->bYn, d->train_sc};
+  if (d->train_exec) cudaGraphExecDestroy(d->train_exec);
+  if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   if (d->side) cudaStreamDestroy(d->side);
   if (d->ev_ranged) cudaEventDestroy(d->ev_ranged);
   if (d->ev_fallback) cudaEventDestroy(d->ev_fallback);
@@ -933,17 +957,13 @@ int df_dnn_fit_norm(df_dnn* d, int64_t n, const double* T, const double* p, cons
   return rc;
 }
 
-int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, const double* Y, const double* Yn,
-                      float lr, float* loss_out, df_stream_t stream) {
-  if (!d || n < 1 || n > d->o.batch || !T || !p || !Y || !Yn)
-    return set_error(DF_EINVAL, "df_dnn_train_step: bad arguments (1 <= n <= batch)");
-  cudaStream_t st = (cudaStream_t)stream;
-  int rc = dnn_train_buffers(d);
-  if (rc) return rc;
+// The kernels of one training step on the staged batch (bT, bp, bY, bYn).
+static int dnn_train_enqueue(df_dnn* d, int64_t n, cudaStream_t st) {
   const DnnLayout& L = d->L;
   const int64_t B = d->B;
   const int64_t M = (n + 7) / 8 * 8;  // rows used by the GEMMs (K of the weight gradients)
   const int N = d->o.n_species;
+  int rc = DF_OK;
   FeatArgs fa;
   memset(&fa, 0, sizeof(fa));
   fa.ncells = n;
@@ -951,10 +971,10 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
   fa.n = n;
   fa.N = N;
   fa.lam = d->o.lambda;
-  fa.T = T;
-  fa.p = p;
-  fa.Y = Y;
-  fa.Ynext = Yn;
+  fa.T = d->bT;
+  fa.p = d->bp;
+  fa.Y = d->bY;
+  fa.Ynext = d->bYn;
   fa.norm = d->norm;
   fa.margin = 0.0f;
   fa.X = d->X;
@@ -1000,21 +1020,83 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
   }
   if (rc) return rc;
   // Adam (bias-corrected) on the master weights, then the bf16 copies
-  d->step += 1;
   const float b1 = (float)d->o.beta1, b2 = (float)d->o.beta2;
-  const float c1 = (float)(1.0 - std::pow(d->o.beta1, (double)d->step));
-  const float c2 = (float)(1.0 - std::pow(d->o.beta2, (double)d->step));
-  k_adam<<<(unsigned)((L.total + 255) / 256), 256, 0, st>>>(P, d->m1, d->m2, G, L.total, lr, b1, b2,
-                                                             (float)d->o.adam_eps, c1, c2);
+  k_adam<<<(unsigned)((L.total + 255) / 256), 256, 0, st>>>(P, d->m1, d->m2, G, L.total, d->train_sc, b1, b2,
+                                                             (float)d->o.adam_eps);
   rc = cuda_check(cudaGetLastError(), "train step kernels");
   if (!rc) rc = dnn_cast_all(d, st);
+  return rc;
+}
+
+// the mean loss of the step, when asked for (synchronises the stream)
+static int train_step_loss(df_dnn* d, int64_t n, int rc, float* loss_out, cudaStream_t st) {
   if (!rc && loss_out) {
+    const int64_t M = (n + 7) / 8 * 8;
+    const int nbl = (int)((M + 255) / 256);
     double l = 0.0;
     rc = cuda_check(cudaMemcpyAsync(&l, d->loss_part + nbl, 8, cudaMemcpyDeviceToHost, st), "read loss");
     if (!rc) rc = check_err_flag(d, st);
-    *loss_out = (float)(l / ((double)n * N));
+    *loss_out = (float)(l / ((double)n * d->o.n_species));
   }
   return rc;
+}
+
+int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, const double* Y, const double* Yn,
+                      float lr, float* loss_out, df_stream_t stream) {
+  if (!d || n < 1 || n > d->o.batch || !T || !p || !Y || !Yn)
+    return set_error(DF_EINVAL, "df_dnn_train_step: bad arguments (1 <= n <= batch)");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = dnn_train_buffers(d);
+  if (rc) return rc;
+  const int N = d->o.n_species;
+  // stage the batch and this step's scalars
+  rc = cuda_check(cudaMemcpyAsync(d->bT, T, n * 8, cudaMemcpyDeviceToDevice, st), "stage T");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bp, p, n * 8, cudaMemcpyDeviceToDevice, st), "stage p");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bY, Y, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bYn, Yn, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y_next");
+  if (rc) return rc;
+  d->step += 1;
+  const float c1 = (float)(1.0 - std::pow(d->o.beta1, (double)d->step));
+  const float c2 = (float)(1.0 - std::pow(d->o.beta2, (double)d->step));
+  k_set_train_scalars<<<1, 1, 0, st>>>(d->train_sc, lr, c1, c2);
+  rc = cuda_check(cudaGetLastError(), "train scalars");
+  if (rc) return rc;
+  // The step's ~25 launches are captured once per batch size, on a private
+  // stream (the caller's may be the legacy stream, which cannot be captured),
+  // after a first eager step has done the one-time set-up, and replayed on the
+  // caller's stream.  Inside a caller's own stream capture they are simply
+  // enqueued.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  rc = cuda_check(cudaStreamIsCapturing(st, &cs), "capture status");
+  if (rc) return rc;
+  if (cs != cudaStreamCaptureStatusNone || d->step == 1 || d->no_graph)
+    return train_step_loss(d, n, dnn_train_enqueue(d, n, st), loss_out, st);
+  if (!d->train_exec || d->train_n != n) {
+    if (d->train_exec) cudaGraphExecDestroy(d->train_exec);
+    d->train_exec = nullptr;
+    d->train_n = -1;
+    if (!d->cap_stream)
+      rc = cuda_check(cudaStreamCreateWithFlags(&d->cap_stream, cudaStreamNonBlocking), "capture stream");
+    if (rc) return rc;
+    if (cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      d->no_graph = true;  // capture unavailable: run the kernels as they are from now on
+      return train_step_loss(d, n, dnn_train_enqueue(d, n, st), loss_out, st);
+    }
+    const int erc = dnn_train_enqueue(d, n, d->cap_stream);
+    cudaGraph_t g = nullptr;
+    rc = cuda_check(cudaStreamEndCapture(d->cap_stream, &g), "end capture");
+    if (erc) {
+      if (g) cudaGraphDestroy(g);
+      return erc;
+    }
+    if (!rc) rc = cuda_check(cudaGraphInstantiate(&d->train_exec, g, 0), "instantiate training graph");
+    if (g) cudaGraphDestroy(g);
+    if (rc) return rc;
+    d->train_n = n;
+  }
+  rc = cuda_check(cudaGraphLaunch(d->train_exec, st), "launch training graph");
+  return train_step_loss(d, n, rc, loss_out, st);
 }
 
 int df_dnn_forward_raw(df_dnn* d, int64_t n, const void* X, float* U, df_stream_t stream) {

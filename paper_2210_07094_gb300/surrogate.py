@@ -50,23 +50,30 @@ def pairs(Ts, p, Ys):
 
 def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, seed=0, time_budget=None,
           log=None):
-    """Adam with a cosine learning-rate schedule over shuffled mini-batches."""
+    """Adam with a cosine learning-rate schedule over shuffled mini-batches.
+    Each epoch the pairs are permuted once into batch-major blocks, so every
+    step hands the library contiguous views (no per-step gathers)."""
     import torch
     n = T.numel()
+    batch = min(batch, n)
     steps_per_epoch = max(1, n // batch)
     total = max(1, int(epochs * steps_per_epoch))
     g = torch.Generator(device=T.device).manual_seed(seed)
     losses = []
     t0 = time.time()
-    perm = None
+    N = Y.shape[0]
+    m = steps_per_epoch * batch
     for s in range(total):
-        if s % steps_per_epoch == 0:
-            perm = torch.randperm(n, device=T.device, generator=g)
-        idx = perm[(s % steps_per_epoch) * batch:(s % steps_per_epoch + 1) * batch]
+        k = s % steps_per_epoch
+        if k == 0:
+            perm = torch.randperm(n, device=T.device, generator=g)[:m]
+            Ts = T[perm].view(steps_per_epoch, batch)
+            Ps = p[perm].view(steps_per_epoch, batch)
+            Ys = Y[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
+            Yns = Yn[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
         lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * s / total))
         want = (s % 50 == 0) or s == total - 1
-        loss = dnn.train_step(T[idx].contiguous(), p[idx].contiguous(), Y[:, idx].contiguous(),
-                              Yn[:, idx].contiguous(), lr, want_loss=want)
+        loss = dnn.train_step(Ts[k], Ps[k], Ys[k], Yns[k], lr, want_loss=want)
         if want:
             losses.append((s, loss))
             if log:
