@@ -74,6 +74,8 @@ struct df_dnn {
   // buffers and the step's scalars (lr, bias corrections) read from train_sc
   double *bT = nullptr, *bp = nullptr, *bY = nullptr, *bYn = nullptr;
   float* train_sc = nullptr;
+  float* splitk_ws = nullptr;  // split-K partial sums of the small-output GEMMs (weight gradients)
+  size_t splitk_elems = 0;
   cudaGraphExec_t train_exec = nullptr;
   int64_t train_n = -1;
   cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
@@ -697,6 +699,8 @@ static int dnn_train_buffers(df_dnn* d) {
   rc = rc ? rc : dev_alloc((void**)&d->bY, B * d->o.n_species * 8);
   rc = rc ? rc : dev_alloc((void**)&d->bYn, B * d->o.n_species * 8);
   rc = rc ? rc : dev_alloc((void**)&d->train_sc, 4 * 4);
+  d->splitk_elems = (size_t)2 << 20;
+  rc = rc ? rc : dev_alloc((void**)&d->splitk_ws, d->splitk_elems * 4);
   return rc;
 }
 
@@ -771,6 +775,10 @@ static int gemm(df_dnn* d, const void* A, int ldA, const void* B, int ldB, int M
   P.out2 = out2;
   P.ld2 = ld2;
   P.err = d->err;
+  if (mode == EPI_F32) {
+    P.ws = d->splitk_ws;
+    P.ws_elems = d->splitk_ws ? d->splitk_elems : 0;
+  }
   return gemm_bf16(A, B, P, st, 0);
 }
 
@@ -887,7 +895,7 @@ void df_dnn_free(df_dnn* d) {
   if (!d) return;
   void* ptrs[] = {d->params, d->m1, d->m2, d->grads, d->norm, d->X, d->XT, d->U, d->tgt, d->dU, d->dUT,
                   d->loss_part, d->iX, d->iU, d->imask, d->list, d->fb_status, d->counter, d->err, d->iYl,
-                  d->rawb, d->fb_flag, d->bT, d->bp, d->bY, d->bYn, d->train_sc};
+                  d->rawb, d->fb_flag, d->bT, d->bp, d->bY, d->bYn, d->train_sc, d->splitk_ws};
   if (d->train_exec) cudaGraphExecDestroy(d->train_exec);
   if (d->cap_stream) cudaStreamDestroy(d->cap_stream);
   if (d->side) cudaStreamDestroy(d->side);

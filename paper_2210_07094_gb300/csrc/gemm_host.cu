@@ -60,6 +60,17 @@ static size_t gemm_smem() {
   return (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
 }
 
+// out0[r][c] = sum_z ws[z][r][c] (+ bias[c]), z in order
+__global__ void k_splitk_reduce(const float* ws, int splits, int M, int N, const float* bias, float* out, int ld) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)M * N) return;
+  const int r = (int)(i / N), c = (int)(i - (int64_t)r * N);
+  float acc = 0.0f;
+  for (int z = 0; z < splits; ++z) acc += ws[(int64_t)z * M * N + i];
+  if (bias) acc += bias[c];
+  out[(int64_t)r * ld + c] = acc;
+}
+
 template <int BN>
 static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cudaStream_t st) {
   CUtensorMap ta, tb;
@@ -79,8 +90,29 @@ static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cud
   }
   dim3 grid((P.N + BN - 1) / BN, (P.M + GEMM_BM - 1) / GEMM_BM);
   if (grid.y > 65535) return set_error(DF_EUNSUPPORTED, "GEMM M too large for one launch");
-  kf<<<grid, 128, sm, st>>>(ta, tb, P);
-  return cuda_check(cudaGetLastError(), "GEMM launch");
+  // split-K when the output has few tiles but the reduction is long (weight
+  // gradients: K = the batch): enough CTAs for the SMs, at least two k-blocks
+  // each, within the caller's workspace
+  GemmParams Q = P;
+  Q.splits = 1;
+  if (P.mode == EPI_F32 && P.ws && P.ws_elems > 0) {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (int64_t)grid.x * grid.y;
+    const int nk = (P.K + GEMM_BK - 1) / GEMM_BK;
+    int64_t sp = std::min<int64_t>(nk / 2, (nsm + tiles - 1) / tiles);
+    sp = std::min<int64_t>(sp, (int64_t)(P.ws_elems / ((size_t)P.M * P.N)));
+    if (tiles * 2 <= nsm && sp >= 2) Q.splits = (int)sp;
+  }
+  grid.z = Q.splits;
+  kf<<<grid, 128, sm, st>>>(ta, tb, Q);
+  rc = cuda_check(cudaGetLastError(), "GEMM launch");
+  if (!rc && Q.splits > 1) {
+    const int64_t mn = (int64_t)P.M * P.N;
+    k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, st>>>(P.ws, Q.splits, P.M, P.N, P.bias, P.out0, P.ld0);
+    rc = cuda_check(cudaGetLastError(), "split-K reduction");
+  }
+  return rc;
 }
 
 constexpr int PERS_STAGES = 4;

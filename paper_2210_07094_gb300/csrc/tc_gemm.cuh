@@ -39,6 +39,12 @@ struct GemmParams {
   __nv_bfloat16* out2;
   int ld0, ld1, ld2;
   int* err;           // device error flag (0 = ok)
+  // EPI_F32 split-K (one-tile-per-CTA kernel): with splits > 1, CTA z sums
+  // its share of the k-blocks into ws[z][M][N]; a second kernel adds the
+  // slices in a fixed order into out0 (+ bias)
+  int splits;
+  float* ws;
+  size_t ws_elems;
 };
 
 constexpr int GEMM_BM = 128;
@@ -174,7 +180,11 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = *tslot;
   const int m0 = blockIdx.y * GEMM_BM, n0 = blockIdx.x * BN;
-  const int nk = (P.K + GEMM_BK - 1) / GEMM_BK;
+  const int nk_all = (P.K + GEMM_BK - 1) / GEMM_BK;
+  const int nsplit = P.splits > 1 ? P.splits : 1;
+  // k-blocks [kb0, kb0 + nk) of this split (the host keeps nsplit <= nk_all)
+  const int kb0 = (int)((int64_t)blockIdx.z * nk_all / nsplit);
+  const int nk = (int)((int64_t)(blockIdx.z + 1) * nk_all / nsplit) - kb0;
   bool timed_out = false;
 
   if (warp == 0 && lane == 0) {
@@ -187,8 +197,8 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
-      tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, kb * GEMM_BK, m0, full0 + 8 * s);
-      tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, kb * GEMM_BK, n0, full0 + 8 * s);
+      tma_load_2d(smem_u32(sA + s * A_BYTES), &tmA, (kb0 + kb) * GEMM_BK, m0, full0 + 8 * s);
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &tmB, (kb0 + kb) * GEMM_BK, n0, full0 + 8 * s);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -246,6 +256,15 @@ __global__ void __launch_bounds__(128, 1)
       float v[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+      if (nsplit > 1) {  // partial sum of this split (bias added by the reduction)
+        if (rok) {
+          float* o = P.ws + ((size_t)blockIdx.z * P.M + row) * P.N + nb;
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            if (nb + j < P.N) *reinterpret_cast<float4*>(o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        continue;
+      }
       if (P.bias) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] += (nb + j < P.N) ? P.bias[nb + j] : 0.0f;
