@@ -38,12 +38,13 @@ def test_one_step_equals_integrate(h2):
 
 
 def test_ignition_window_against_oracle(h2):
-    """Stoichiometric mixtures at 10 atm, T0 = 1300..1900 K, 150 steps of 2 ms:
-    the final state matches the oracle, and the time of the largest dT/dt
-    agrees within the sampling resolution (the rate peak is broad)."""
+    """Stoichiometric mixtures at 10 atm, T0 = 950..1200 K, 150 steps of 2 ms
+    (the synthetic mechanism's heat release peaks 20-90 ms in): the final
+    state matches the oracle, and the time of the largest dT/dt agrees within
+    the sampling resolution (the rate peak is broad)."""
     mech, m, o = h2
     n = 24
-    T0 = np.linspace(1300.0, 1900.0, n)
+    T0 = np.linspace(950.0, 1200.0, n)
     Y0 = np.asarray(synth._h2_air_Y(mech, np.ones(n)))
     p0 = np.full(n, 10 * 101325.0)
     dt, nsteps = 2e-3, 150
@@ -55,6 +56,7 @@ def test_ignition_window_against_oracle(h2):
     assert np.max(np.abs(Tg - To)) <= 1e-3
     assert np.max(np.abs(Yg - Yo) / Yo.max(axis=0)) <= 1e-7
     tig = ti.cpu().numpy()
+    assert np.all(to > 5 * dt)  # an interior maximum, not the initial state
     assert np.all(np.abs(tig - to) <= 2 * dt), np.max(np.abs(tig - to))
     # the GPU's chosen time has (nearly) the oracle's largest rate
     for c in range(0, n, 6):
