@@ -22,6 +22,12 @@ int df_probe_fp64_peak(int iters, double* gflops, double* ms);
  * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */
 int df_probe_exp(const double* x, double* y, long long n, void* stream);
 
+/* y[i] = ln(x[i]) by the library's own table-driven logarithm (the one the
+ * rate kernels use for ln T and the Troe falloff), so that its accuracy can be
+ * checked against CUDA's log.  x, y: device memory; asynchronous on `stream`.
+ * DF_EINVAL for n < 0 or null arrays with n > 0. */
+int df_probe_log(const double* x, double* y, long long n, void* stream);
+
 /* y[i] = GELU(x[i]) (derivative = 0) or GELU'(x[i]) (derivative = 1) as the GEMM
  * epilogues compute them in FP32 (the network's activation, Sec. 2.3: GELU(z) =
  * z Phi(z) with Phi the normal CDF, through the library's own erfc), so that their

@@ -19,9 +19,19 @@
 #pragma once
 #include "common.cuh"
 #include "fastexp.cuh"
+#include "fastlog.cuh"
 #include "dual.cuh"
 
 namespace df {
+
+// ln and log10 of the rate expressions by the table-driven logarithm (the
+// dual-number versions carry the derivative d/x)
+__device__ __forceinline__ double fast_log(double x) { return log_tab(x); }
+__device__ __forceinline__ Dual fast_log(const Dual& x) { return Dual(log_tab(x.v), x.d / x.v); }
+__device__ __forceinline__ double fast_log10(double x) { return log10_tab(x); }
+__device__ __forceinline__ Dual fast_log10(const Dual& x) {
+  return Dual(log10_tab(x.v), x.d / (x.v * 2.302585092994045684));
+}
 
 // strided view of a per-thread vector (any scalar type) in shared memory
 template <class S>
@@ -138,10 +148,10 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
     const S e1 = exp_tang(-T * tr[5], mv.etab);
     const S e2 = exp_tang(-tr[6] * invT, mv.etab);
     const S Fc = (1.0 - tr[3]) * e3 + tr[3] * e1 + e2;
-    const S Lc = log10(Fc);
+    const S Lc = fast_log10(Fc);
     const S cc = -0.4 - 0.67 * Lc;
     const S nn = 0.75 - 1.27 * Lc;
-    const S L = log10(Pr);
+    const S L = fast_log10(Pr);
     const S x = L + cc;
     const S den = nn - 0.14 * x;
     const S f1 = x / den;
@@ -229,7 +239,7 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
   constexpr int n = NS + 1;
   constexpr double EV = CONSTV ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
   const S T = y[0];
-  const S lnT = log(T);
+  const S lnT = fast_log(T);
   const S invT = 1.0 / T;
   S sumYW(0.0), cpm(0.0);
 #pragma unroll
@@ -408,7 +418,7 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
                                          SVT<S> wdot, SVT<S> gRT, SVT<S> hRT, SVT<S> cpR, SVT<S> sig, SVT<S> v,
                                          const ThetaHook* hook = nullptr) {
   const S T = y[0];
-  const S lnT = log(T);
+  const S lnT = fast_log(T);
   const S invT = 1.0 / T;
   S sumYW(0.0), cpm(0.0);
 #pragma unroll

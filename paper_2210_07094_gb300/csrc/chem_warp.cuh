@@ -73,7 +73,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   double* cpR = ws + L.cpR;
   double* wdot = ws + L.wdot;
   const double T = y[0];
-  const double lnT = log(T);
+  const double lnT = log_tab(T);
   const double invT = 1.0 / T;
   // thermo and sum Y/W
   double sYW = 0.0;

@@ -4,6 +4,7 @@
 #include "common.cuh"
 #include "../../include/df_probe.h"
 #include "fastexp.cuh"
+#include "fastlog.cuh"
 
 namespace df {
 
@@ -26,9 +27,21 @@ __global__ void k_exp_probe(const double* x, double* y, long long n) {
   if (i < n) y[i] = exp_tang(x[i], tab);
 }
 
+__global__ void k_log_probe(const double* x, double* y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = log_tab(x[i]);
+}
+
 }  // namespace df
 
 using namespace df;
+
+extern "C" int df_probe_log(const double* x, double* y, long long n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_log: bad arguments");
+  if (n == 0) return DF_OK;
+  k_log_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n);
+  return cuda_check(cudaGetLastError(), "log probe kernel");
+}
 
 extern "C" int df_probe_exp(const double* x, double* y, long long n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_exp: bad arguments");

@@ -30,3 +30,26 @@ def test_exp_tang_within_two_ulp():
     assert np.max(_ulp_err(y[ok], y_host[ok])) <= 2.0
     assert np.max(_ulp_err(y[ok], y_cuda[ok])) <= 2.0
     assert y[x.size - 11] == 1.0 and y[x.size - 10] == 1.0
+
+
+def test_log_tab_absolute_accuracy():
+    """The table-driven logarithm of the rate kernels: within 2 ulp of
+    max(1, |ln x|) of the exact value (ln T and the Troe log10s enter the rates
+    as addends), on random magnitudes, near 1 and at the special values that go
+    to the library log."""
+    from paper_2210_07094_gb300 import _lib
+    L = _lib.load()
+    rng = np.random.default_rng(1)
+    x = np.concatenate([10.0 ** rng.uniform(-307, 307, 1 << 20), rng.uniform(0.5, 2.0, 1 << 18),
+                        1.0 + rng.uniform(-1e-6, 1e-6, 1 << 12), rng.uniform(200.0, 5000.0, 1 << 16),
+                        [1.0, 2.0, 0.5, 300.0, 3000.0, 5e-324, 0.0, np.inf]])
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    _lib.check(L.df_probe_log(C.c_void_p(xd.data_ptr()), C.c_void_p(yd.data_ptr()), x.size,
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream)), "df_probe_log")
+    y = yd.cpu().numpy()
+    y_cuda = torch.log(xd).cpu().numpy()
+    fin = np.isfinite(y_cuda)
+    scale = np.maximum(1.0, np.abs(y_cuda[fin]))
+    assert np.max(np.abs(y[fin] - y_cuda[fin]) / scale) <= 2 * 2.0 ** -52
+    assert y[x.size - 1] == np.inf and y[x.size - 2] == -np.inf
