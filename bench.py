@@ -33,12 +33,12 @@ METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
 UNIT = "cell-steps/s"
 # FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
 # 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
-# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.9698e10) of one timed
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.8086e10) of one timed
 # launch on the 2^20-cell field divided by the 2199716 attempts that launch
 # counted (profiles/integrator_thread9_h2air_bimodal.md).
-FLOP_PER_SUBSTEP = 22593
+FLOP_PER_SUBSTEP = 21860
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 181392128 + 215080192
+TRAFFIC_PER_LAUNCH = 182001664 + 215038464
 
 
 def _rank_info():
