@@ -160,7 +160,11 @@ int df_chem_integrate(const df_mech* mech, int64_t ncells, double* T, const doub
  * cell's initial T, Y and to ln A_j of every reaction, for the map the
  * integrator computes with RODAS4 and the given options, its accepted step
  * sequence held fixed (discrete adjoint).  The call recomputes the forward
- * pass, storing one checkpoint per accepted step, then sweeps back.
+ * pass, storing one checkpoint per accepted step, then sweeps back.  When the
+ * workspace has room (df_chem_adjoint_workspace_size), the forward pass also
+ * keeps each accepted step's stage vectors and LU factors and the reverse
+ * sweep reads them back; with only the compact size (checkpoints and partials,
+ * below) it recomputes each step instead.  Both give bitwise the same result.
  *
  *  T0, p, Y0     inputs as for df_chem_integrate (device, not modified)
  *  gT1, gY1, gQ1 cotangents (device; each may be NULL = 0)
@@ -170,10 +174,13 @@ int df_chem_integrate(const df_mech* mech, int64_t ncells, double* T, const doub
  *  status, nsub [ncells] (device; nsub may be NULL): per-cell status and number
  *                of accepted steps; a cell with more than max_steps accepted
  *                steps gets DF_CELL_MAXSTEPS and a zero gradient
- *  workspace     device memory of at least df_chem_adjoint_workspace_size()
- *                bytes, owned by the caller.  On return its first
- *                ncells*max_steps*(N+2) doubles hold the checkpoints
- *                [cell][step][T, Y_1..Y_N, h] of the accepted steps.
+ *  workspace     device memory owned by the caller: at least the compact size
+ *                8 * (ncells*max_steps*(N+2) + ceil(ncells/32)*M) + 256
+ *                bytes; df_chem_adjoint_workspace_size() returns the size with
+ *                the stored stages, 8 * ncells*max_steps*(7n + n^2) bytes more
+ *                (n = N + 1).  On return its first ncells*max_steps*(N+2)
+ *                doubles hold the checkpoints [cell][step][T, Y_1..Y_N, h] of
+ *                the accepted steps.
  * Built for mechanisms of 3 and 9 species (one cell per thread); other sizes
  * return DF_EUNSUPPORTED.  Errors: DF_EINVAL, DF_EWORKSPACE, DF_EUNSUPPORTED,
  * DF_ECUDA. */

@@ -181,12 +181,16 @@ def integrate_steps(mech: Mechanism, T, p, Y, dt: float, nsteps: int, opts: Inte
 
 
 def adjoint(mech: Mechanism, T0, p, Y0, dt: float, gT1=None, gY1=None, gQ1=None,
-            opts: IntegOpts | None = None, max_steps: int = 64, stream=None):
+            opts: IntegOpts | None = None, max_steps: int = 64, stream=None, store_stages: bool = True):
     """Discrete adjoint of integrate() (RODAS4, accepted steps frozen).
 
     Returns a dict with gT0 [ncells], gY0 [N, ncells], g_lnA [M] (summed over
     cells), status, nsub and the checkpoint workspace (uint8 device tensor whose
-    leading doubles are [cell][step][T, Y..., h])."""
+    leading doubles are [cell][step][T, Y..., h]).  store_stages=False passes
+    the compact workspace (checkpoints and partials only): the reverse sweep
+    then recomputes each step instead of reading its stored stages and LU
+    factors, keeping n + 1 doubles per accepted step instead of 8n + n^2 + 1
+    (n = N + 1).  Both give bitwise the same result."""
     torch = _torch()
     lib = _lib.load()
     n, pT, pp, pY = _cells(mech, T0, p, Y0)
@@ -194,6 +198,9 @@ def adjoint(mech: Mechanism, T0, p, Y0, dt: float, gT1=None, gY1=None, gQ1=None,
     size = C.c_size_t()
     _lib.check(lib.df_chem_adjoint_workspace_size(mech.handle, n, int(max_steps), C.byref(size)),
                "df_chem_adjoint_workspace_size")
+    if not store_stages:
+        N, M = mech.n_species, mech.n_reactions
+        size = C.c_size_t(8 * (n * int(max_steps) * (N + 2) + (n + 31) // 32 * M) + 256)
     ws = torch.empty(size.value, dtype=torch.uint8, device=dev)
     out = {
         "gT0": torch.empty(n, dtype=torch.float64, device=dev),

@@ -58,6 +58,11 @@ struct AdjArgs {
   double* ckpt;     // [ncells][cap][n + 1]: y_i then h_i
   double* partial;  // [gridDim.x][M]
   int stage_blob;
+  // optional [cap][7n + n^2][ncells] (cell fastest, so a warp's accesses
+  // coalesce): the accepted step's stage vectors K_s (6n), LU factors of W
+  // (n^2) and row pivots (n), kept by the forward sweep so that the reverse
+  // sweep need not recompute the step; null: the reverse sweep recomputes it
+  double* stages;
 };
 
 template <int NS>
@@ -134,8 +139,9 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       double yold[n], ynew[n], en;
 #pragma unroll
       for (int i = 0; i < n; ++i) yold[i] = y[i];
+      int pv[n];
       const bool sok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv,
-                                       stride, ynew, en, nullptr, nacc == 0 && nrej == 0, &last);
+                                       stride, ynew, en, pv, nacc == 0 && nrej == 0, &last);
       const double hstep = h;  // the step actually taken (the first one may be cut)
       const int before = nacc;
       step_control(tb, sok, en, last, a.dt, y, ynew, t, h, nacc, nrej, last_rej, done, ss);
@@ -148,6 +154,13 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
 #pragma unroll
           for (int i = 0; i < n; ++i) slot[i] = yold[i];
           slot[n] = hstep;
+          if (a.stages) {
+            double* sp = a.stages + (int64_t)(nacc - 1) * (7 * n + n * n) * a.ncells + cell;
+            for (int i = 0; i < 6 * n; ++i) sp[i * a.ncells] = Kv[i];
+            for (int i = 0; i < n * n; ++i) sp[(6 * n + i) * a.ncells] = Wv[i];
+#pragma unroll
+            for (int i = 0; i < n; ++i) sp[(6 * n + n * n + i) * a.ncells] = (double)pv[i];
+          }
         }
       }
       if (!done) {
@@ -202,8 +215,16 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
         for (int i = 0; i < n; ++i) yi[i] = slot[i];
         double hs = slot[n];
         int piv[n];
-        ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
-                        en, piv);
+        if (a.stages) {  // the forward sweep kept this step's stages and factors
+          const double* sp = a.stages + (int64_t)istep * (7 * n + n * n) * a.ncells + cell;
+          for (int i = 0; i < 6 * n; ++i) Kv[i] = sp[i * a.ncells];
+          for (int i = 0; i < n * n; ++i) Wv[i] = sp[(6 * n + i) * a.ncells];
+#pragma unroll
+          for (int i = 0; i < n; ++i) piv[i] = (int)sp[(6 * n + n * n + i) * a.ncells];
+        } else {
+          ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
+                          en, piv);
+        }
         const double ih = 1.0 / hs;
         double yb[n];
 #pragma unroll
@@ -321,10 +342,19 @@ static int ensure_adj_table(int dev) {
 
 static constexpr int ADJ_THREADS = 32;
 
-size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap) {
+// Workspace: checkpoints [ncells][cap][n + 1], then the per-block ln A
+// partials, then (with_stages) the stored stages [cap][7n + n^2][ncells].
+static size_t adj_compact_doubles(const df_mech* m, int64_t ncells, int cap) {
   const int n = m->dims.N + 1;
   const int64_t blocks = (ncells + ADJ_THREADS - 1) / ADJ_THREADS;
-  return sizeof(double) * ((size_t)ncells * cap * (n + 1) + (size_t)blocks * m->dims.M) + 256;
+  return (size_t)ncells * cap * (n + 1) + (size_t)blocks * m->dims.M;
+}
+
+size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages) {
+  const int n = m->dims.N + 1;
+  size_t d = adj_compact_doubles(m, ncells, cap);
+  if (with_stages) d += (size_t)ncells * cap * (7 * n + n * n);
+  return sizeof(double) * d + 256;
 }
 
 template <int NS>
@@ -355,10 +385,11 @@ static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double
 int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
                    double dt, const df_integ_opts& o, int cap, const double* gT1, const double* gY1,
                    const double* gQ1, double* gT0, double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
-                   void* ws, size_t ws_bytes, cudaStream_t st) {
+                   void* ws, size_t ws_bytes, bool allow_stages, cudaStream_t st) {
   if (o.method != 0) return set_error(DF_EUNSUPPORTED, "the adjoint is built for RODAS4 (method 0)");
-  const size_t need = adjoint_workspace_bytes(m, ncells, cap);
+  const size_t need = adjoint_workspace_bytes(m, ncells, cap, false);
   if (!ws || ws_bytes < need) return set_error(DF_EWORKSPACE, "adjoint workspace too small");
+  const bool keep_stages = allow_stages && ws_bytes >= adjoint_workspace_bytes(m, ncells, cap, true);
   int rc = ensure_adj_table(m->device);
   if (rc) return rc;
   const int n = m->dims.N + 1;
@@ -387,6 +418,7 @@ int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const dou
   a.nsub = nsub;
   a.ckpt = static_cast<double*>(ws);
   a.partial = static_cast<double*>(ws) + (size_t)ncells * cap * (n + 1);
+  a.stages = keep_stages ? static_cast<double*>(ws) + adj_compact_doubles(m, ncells, cap) : nullptr;
   switch (m->dims.N) {
     case 3:
       return adjoint_dispatch<3>(m, a, st, g_lnA);
@@ -452,7 +484,7 @@ extern "C" int df_chem_adjoint_static(const df_mech* m, int64_t ncells, const do
   if (ncells == 0) return DF_OK;
   if (!T0 || !p || !Y0 || !status) return set_error(DF_EINVAL, "df_chem_adjoint_static: null input or status");
   if (!(dt >= 0.0) || !std::isfinite(dt)) return set_error(DF_EINVAL, "df_chem_adjoint_static: dt must be finite and >= 0");
-  const size_t need = adjoint_workspace_bytes(m, ncells, max_steps);
+  const size_t need = adjoint_workspace_bytes(m, ncells, max_steps, false);
   if (need > ADJ_STATIC_BYTES)
     return set_error(DF_EWORKSPACE,
                      "df_chem_adjoint_static: ncells * max_steps * (N + 2) checkpoints plus the ln A partials need " +
@@ -469,5 +501,5 @@ extern "C" int df_chem_adjoint_static(const df_mech* m, int64_t ncells, const do
   int rc = adj_static_scratch(&ws);
   if (rc) return rc;
   return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub, ws,
-                        ADJ_STATIC_BYTES, (cudaStream_t)stream);
+                        ADJ_STATIC_BYTES, false, (cudaStream_t)stream);
 }

@@ -243,7 +243,7 @@ int df_chem_adjoint_workspace_size(const df_mech* m, int64_t ncells, int32_t max
   int rc = check_cells("df_chem_adjoint_workspace_size", m, ncells);
   if (rc) return rc;
   if (max_steps < 1 || !bytes) return set_error(DF_EINVAL, "df_chem_adjoint_workspace_size: bad arguments");
-  *bytes = adjoint_workspace_bytes(m, ncells, max_steps);
+  *bytes = adjoint_workspace_bytes(m, ncells, max_steps, true);
   return DF_OK;
 }
 
@@ -272,7 +272,7 @@ int df_chem_adjoint(const df_mech* m, int64_t ncells, const double* T0, const do
       o.max_substeps < 1)
     return set_error(DF_EINVAL, "df_chem_adjoint: invalid options");
   return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub,
-                        workspace, ws_bytes, (cudaStream_t)stream);
+                        workspace, ws_bytes, true, (cudaStream_t)stream);
 }
 
 int df_chem_last_stats(const df_mech* m, int64_t* accepted, int64_t* rejected, df_stream_t stream) {

@@ -129,9 +129,12 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
                           int nsteps = 1, double* t_ign = nullptr);
 
 // adjoint (adjoint.cu)
-size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap);
+// with_stages: also room for the stored stages and LU factors of every
+// accepted step (the reverse sweep then skips recomputing the step)
+size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages);
+// allow_stages: keep the stages when ws_bytes has room for them
 int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
                    double dt, const df_integ_opts& o, int cap, const double* gT1, const double* gY1,
                    const double* gQ1, double* gT0, double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
-                   void* ws, size_t ws_bytes, cudaStream_t st);
+                   void* ws, size_t ws_bytes, bool allow_stages, cudaStream_t st);
 }  // namespace df
