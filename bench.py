@@ -38,7 +38,7 @@ UNIT = "cell-steps/s"
 # counted (profiles/integrator_thread9_h2air_bimodal.md).
 FLOP_PER_SUBSTEP = 21860
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 182001664 + 215038464
+TRAFFIC_PER_LAUNCH = 183550208 + 213393920
 
 
 def _rank_info():
@@ -312,10 +312,33 @@ def profile_case(args):
     field.
     dnn-infer: two inference passes of an (untrained) network over the held-out
     states of the learned-surrogate workload (2^22 trajectory states, 2% of them
-    moved 50-300 K outside the training T range, half below, half above)."""
+    moved 50-300 K outside the training T range, half below, half above).
+    h2: two thread-per-cell integrator launches (warm-up, measured) on 2^18
+    cells of the bimodal 9-species field, in the launch shape the autotuner
+    picks for the full field (64 threads x 2 blocks per SM, hottest first)."""
     import ctypes as C
     import torch
     from paper_2210_07094_gb300 import _lib
+    if args.profile_case == "h2":
+        import paper_2210_07094_gb300 as df
+        from paper_2210_07094_gb300 import synth
+        mech = synth.h2_air_mechanism()
+        m = df.Mechanism(mech)
+        f = synth.field(1, mech, 1 << 18)
+        T0, p, Y0 = (torch.tensor(f[k], device="cuda") for k in ("T", "p", "Y"))
+        o = df.default_opts()
+        o.block_threads, o.blocks_per_sm, o.order_by_T, o.path = 64, 2, 1, 1
+        for rep in range(2):
+            T, Y = T0.clone(), Y0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st, _ = df.integrate(m, T, p, Y, f["dt"], o)
+            e1.record()
+            torch.cuda.synchronize()
+            acc, rej = m.last_stats()
+            print(json.dumps({"case": "h2", "rep": rep, "cells": 1 << 18, "ms": e0.elapsed_time(e1),
+                              "accepted": acc, "rejected": rej, "failed": int((st != 0).sum())}))
+        return 0
     if args.profile_case == "chon":
         import paper_2210_07094_gb300 as df
         from paper_2210_07094_gb300 import synth
@@ -393,7 +416,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the adjoint and 50-species measurements")
     ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
-    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon"],
+    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon", "h2"],
                     help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")

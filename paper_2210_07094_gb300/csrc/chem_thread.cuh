@@ -33,12 +33,14 @@ __device__ __forceinline__ Dual fast_log10(const Dual& x) {
   return Dual(log10_tab(x.v), x.d / (x.v * 2.302585092994045684));
 }
 
-// strided view of a per-thread vector (any scalar type) in shared memory
-template <class S>
+// strided view of a per-thread vector (any scalar type) in shared memory; a
+// stride fixed at compile time (ST > 0, the block size) turns the address of
+// every constant index into an immediate offset
+template <class S, int ST = 0>
 struct SVT {
   S* p;
   int s;
-  __device__ __forceinline__ S& operator[](int i) const { return p[i * s]; }
+  __device__ __forceinline__ S& operator[](int i) const { return p[i * (ST > 0 ? ST : s)]; }
 };
 typedef SVT<double> SV;
 
@@ -81,6 +83,14 @@ __device__ __forceinline__ RxSlots load_slots(const double* r) {
 // derivatives); Vec is any indexable vector of S.  NS > 0 fixes the species
 // count at compile time; otherwise Nrt is used.  With WITH_J it also returns
 // the pieces of dq/dT|_C and dq/dC.
+__device__ __forceinline__ void exp_pair(double a, double b, const double2* tab, double& ea, double& eb) {
+  exp_tang2(a, b, tab, ea, eb);
+}
+__device__ __forceinline__ void exp_pair(const Dual& a, const Dual& b, const double2* tab, Dual& ea, Dual& eb) {
+  ea = exp_tang(a, tab);
+  eb = exp_tang(b, tab);
+}
+
 template <class S>
 struct RateOutT {
   bool active;
@@ -176,8 +186,8 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
       dqdM = k0 * F * g * onePr * (Pf - Pb * invKc);
     }
   } else {
-    kf = exp_tang(lnkf, mv.etab);
-    kr = rev ? exp_tang(lnkf + lnKcinv, mv.etab) : S(0.0);
+    exp_pair(lnkf, lnkf + lnKcinv, mv.etab, kf, kr);
+    if (!rev) kr = S(0.0);
     if (type == 1) {
       const double* ef = mv.eff + N * sl.eff;
       S Mc(0.0);
@@ -232,9 +242,10 @@ __device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) {
 // temperature equation, and C_k = rho Y_k / W_k no longer depends on T or on
 // the mean molar mass.  Returns qdot = -sum_k H_k wdot_k (U_k at constant
 // volume) in erg/(cm^3 s).
-template <int NS, bool WITH_J, class S = double, bool CONSTV = false>
+template <int NS, bool WITH_J, class S = double, bool CONSTV = false, int ST = 0>
 __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, const S (&y)[NS + 1], S (&f)[NS + 1],
-                                         SVT<S> C, SVT<S> wdot, SVT<S> gRT, SVT<S> hRT, SVT<S> cpR, SVT<S> Jv,
+                                         SVT<S, ST> C, SVT<S, ST> wdot, SVT<S, ST> gRT, SVT<S, ST> hRT,
+                                         SVT<S, ST> cpR, SVT<S, ST> Jv,
                                          const ThetaHook* hook = nullptr) {
   constexpr int n = NS + 1;
   constexpr double EV = CONSTV ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
@@ -536,8 +547,8 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
 // LU with partial pivoting of the n x n matrix in the strided view A; whole rows
 // are swapped, the reciprocal of each pivot replaces the diagonal.  The matrix
 // stays in shared memory, so the pivot loop is not unrolled (register budget).
-template <int n>
-__device__ __forceinline__ bool lu_factor(SV A, int* piv) {
+template <int n, int ST = 0>
+__device__ __forceinline__ bool lu_factor(SVT<double, ST> A, int* piv) {
   bool ok = true;
 #pragma unroll 1
   for (int k = 0; k < n; ++k) {
@@ -571,9 +582,9 @@ __device__ __forceinline__ bool lu_factor(SV A, int* piv) {
 
 // Solve in place on the strided vector x with the factors of lu_factor: the
 // whole row permutation first, then the unit-lower and upper solves.
-template <int n>
-__device__ __forceinline__ void lu_solve(SV A, const int* piv, SV x) {
-#pragma unroll 1
+template <int n, int ST = 0>
+__device__ __forceinline__ void lu_solve(SVT<double, ST> A, const int* piv, SVT<double, ST> x) {
+#pragma unroll
   for (int k = 0; k < n; ++k) {
     const int p = piv[k];
     if (p != k) {
@@ -582,14 +593,16 @@ __device__ __forceinline__ void lu_solve(SV A, const int* piv, SV x) {
       x[p] = t;
     }
   }
-#pragma unroll 1
+#pragma unroll
   for (int k = 0; k < n; ++k) {
     const double xk = x[k];
+#pragma unroll
     for (int i = k + 1; i < n; ++i) x[i] -= A[i * n + k] * xk;
   }
-#pragma unroll 1
+#pragma unroll
   for (int k = n - 1; k >= 0; --k) {
     double acc = x[k];
+#pragma unroll
     for (int j = k + 1; j < n; ++j) acc -= A[k * n + j] * x[j];
     x[k] = acc * A[k * n + k];
   }

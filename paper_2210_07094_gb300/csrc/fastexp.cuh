@@ -80,11 +80,8 @@ static __device__ const double2 g_exp2_tab[64] = {
     {0x1.fa7c1819e90d8p+0, 0x1.74853f3a5931ep-55},
 };
 
-__device__ __forceinline__ double exp_tang(double x, const double2* tab) {
-  // |x| >= 700, inf and NaN, tested on the high word with integer operations
-  // (0x4085E000 is the high word of 700.0; the low word of 700.0 is zero), so
-  // the narrow FP64 pipe is not spent on the guard
-  if ((__double2hiint(x) & 0x7fffffff) >= 0x4085E000) return exp(x);
+// the reduction and polynomial of exp_tang for |x| < 700 (no range guard)
+__device__ __forceinline__ double exp_tang_core(double x, const double2* tab) {
   const double SHIFT = 0x1.8p52;                 // 1.5 * 2^52: round-to-integer shifter
   const double INV_L = 0x1.71547652b82fep+6;     // 64 / ln 2
   const double L1 = 0x1.62e42fefa39efp-7;        // ln 2 / 64, leading part
@@ -104,6 +101,28 @@ __device__ __forceinline__ double exp_tang(double x, const double2* tab) {
   const double2 tj = tab[j];
   const double s = tj.x + fma(tj.x, p, tj.y);    // 2^(j/64) * exp(r)
   return __hiloint2double(__double2hiint(s) + (int)((unsigned)m << 20), __double2loint(s));
+}
+
+// exp of two arguments at once: both reductions and polynomials in one
+// straight-line block (two independent dependency chains for the scheduler),
+// the rare |x| >= 700 / inf / NaN cases fixed up afterwards
+__device__ __forceinline__ void exp_tang2(double x1, double x2, const double2* tab, double& e1, double& e2) {
+  const bool big1 = (__double2hiint(x1) & 0x7fffffff) >= 0x4085E000;
+  const bool big2 = (__double2hiint(x2) & 0x7fffffff) >= 0x4085E000;
+  e1 = exp_tang_core(big1 ? 0.0 : x1, tab);
+  e2 = exp_tang_core(big2 ? 0.0 : x2, tab);
+  if (big1 | big2) {
+    if (big1) e1 = exp(x1);
+    if (big2) e2 = exp(x2);
+  }
+}
+
+__device__ __forceinline__ double exp_tang(double x, const double2* tab) {
+  // |x| >= 700, inf and NaN, tested on the high word with integer operations
+  // (0x4085E000 is the high word of 700.0; the low word of 700.0 is zero), so
+  // the narrow FP64 pipe is not spent on the guard
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x4085E000) return exp(x);
+  return exp_tang_core(x, tab);
 }
 
 }  // namespace df

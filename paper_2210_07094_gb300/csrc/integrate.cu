@@ -66,12 +66,14 @@ __host__ __device__ constexpr int thread_ws_doubles() {
 
 __host__ __device__ inline int blob_smem_doubles(const MechDims& d) { return (d.total + 1) & ~1; }
 
-template <int NS, bool CONSTV = false>
+// BT > 0: the kernel is launched with exactly BT threads per block, the
+// stride of the per-thread shared-memory vectors is a compile-time constant
+template <int NS, bool CONSTV = false, int BT = 0>
 __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   constexpr int n = NS + 1;
   extern __shared__ double smem[];
   const int tid = threadIdx.x;
-  const int stride = blockDim.x;
+  const int stride = BT > 0 ? BT : blockDim.x;
   const double* blob = a.blob;
   double2* etab = reinterpret_cast<double2*>(smem);
   for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
@@ -84,13 +86,14 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   __syncthreads();
   const MechView mv = make_view(blob, a.d, etab);
   double* ws = smem + boff + tid;
-  SV C{ws, stride};
-  SV wdot{ws + NS * stride, stride};
-  SV gRT{ws + 2 * NS * stride, stride};
-  SV hRT{ws + 3 * NS * stride, stride};
-  SV cpR{ws + 4 * NS * stride, stride};
-  SV Jv{ws + 5 * NS * stride, stride};
-  SV Kv{ws + (5 * NS + n * n) * stride, stride};
+  typedef SVT<double, BT> V;
+  V C{ws, stride};
+  V wdot{ws + NS * stride, stride};
+  V gRT{ws + 2 * NS * stride, stride};
+  V hRT{ws + 3 * NS * stride, stride};
+  V cpR{ws + 4 * NS * stride, stride};
+  V Jv{ws + 5 * NS * stride, stride};
+  V Kv{ws + (5 * NS + n * n) * stride, stride};
   const RosTab& tb = c_tab[a.method];
   const int lane = tid & 31;
   const unsigned long long nwork = a.nwork_dev ? *a.nwork_dev : (unsigned long long)a.nwork;
@@ -175,8 +178,9 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
     double en;
     double fT;
     const double t0 = t;
-    const bool ok = ros_attempt<NS, CONSTV>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT, cpR,
-                                            Jv, Kv, stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last, &fT);
+    const bool ok = ros_attempt<NS, CONSTV, BT>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT,
+                                                cpR, Jv, Kv, stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last,
+                                                &fT);
     const int nacc0 = nacc;
     step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
     if (nacc > nacc0 && fT > fbest) {  // dT/dt at the start of an accepted substep
@@ -579,7 +583,13 @@ int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int thr
   }
   if (sm > m->max_smem_optin)
     return set_error(DF_EUNSUPPORTED, "integrator shared memory exceeds the per-block limit");
-  auto kf = constv ? k_integrate_thread<NS, true> : k_integrate_thread<NS, false>;
+  // block sizes with a compile-time stride (constant pressure); others take
+  // the run-time stride
+  auto kf = constv            ? k_integrate_thread<NS, true>
+            : threads == 32  ? k_integrate_thread<NS, false, 32>
+            : threads == 64  ? k_integrate_thread<NS, false, 64>
+            : threads == 128 ? k_integrate_thread<NS, false, 128>
+                             : k_integrate_thread<NS, false>;
   int rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                       "set integrator shared memory");
   if (rc) return rc;

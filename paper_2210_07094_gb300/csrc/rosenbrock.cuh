@@ -106,15 +106,16 @@ __device__ __forceinline__ double first_step_limit(const double (&y)[n], const d
 
 // pc: the reactor's fixed state parameter, pressure [dyn/cm^2] (CONSTV false)
 // or density [g/cm^3] (CONSTV true; see eval_thread)
-template <int NS, bool CONSTV = false>
+template <int NS, bool CONSTV = false, int ST = 0>
 __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb, double pc, const double (&y)[NS + 1],
-                                            double& h, double rtol, double atolY, double atolT, SV C, SV wdot,
-                                            SV gRT, SV hRT, SV cpR, SV Jv, SV Kv, int stride,
+                                            double& h, double rtol, double atolY, double atolT, SVT<double, ST> C,
+                                            SVT<double, ST> wdot, SVT<double, ST> gRT, SVT<double, ST> hRT,
+                                            SVT<double, ST> cpR, SVT<double, ST> Jv, SVT<double, ST> Kv, int stride,
                                             double (&ynew)[NS + 1], double& en, int* piv_out = nullptr,
                                             bool first = false, bool* last = nullptr, double* fT = nullptr) {
   constexpr int n = NS + 1;
   double fs[n];
-  eval_thread<NS, true, double, CONSTV>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  eval_thread<NS, true, double, CONSTV, ST>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
   if (fT) *fT = fs[0];
   if (first) {
     const double hl = first_step_limit<n>(y, fs);
@@ -131,7 +132,7 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
   }
   int piv_l[n];
   int* piv = piv_out ? piv_out : piv_l;
-  bool ok = lu_factor<n>(Jv, piv);
+  bool ok = lu_factor<n, ST>(Jv, piv);
   const double ih = 1.0 / h;
   for (int s = 0; s < tb.s; ++s) {
     if (s > 0 && tb.newf[s]) {
@@ -141,17 +142,17 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
         for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
         ynew[i] = acc;
       }
-      eval_thread<NS, false, double, CONSTV>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
+      eval_thread<NS, false, double, CONSTV, ST>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
     }
     // stage right-hand side, solved in place in the K slot of this stage
-    SV Ks{&Kv[s * n], stride};
+    SVT<double, ST> Ks{&Kv[s * n], stride};
 #pragma unroll
     for (int i = 0; i < n; ++i) {
       double acc = fs[i];
       for (int j = 0; j < s; ++j) acc += (tb.c[s][j] * ih) * Kv[j * n + i];
       Ks[i] = acc;
     }
-    lu_solve<n>(Jv, piv, Ks);
+    lu_solve<n, ST>(Jv, piv, Ks);
   }
   double e2 = 0.0;
 #pragma unroll
