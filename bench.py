@@ -33,12 +33,12 @@ METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
 UNIT = "cell-steps/s"
 # FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
 # 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
-# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.8086e10) of one timed
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.6911e10) of one timed
 # launch on the 2^20-cell field divided by the 2199716 attempts that launch
 # counted (profiles/integrator_thread9_h2air_bimodal.md).
-FLOP_PER_SUBSTEP = 21860
+FLOP_PER_SUBSTEP = 21326
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 183550208 + 213393920
+TRAFFIC_PER_LAUNCH = 181079808 + 212591616
 
 
 def _rank_info():
@@ -313,12 +313,37 @@ def profile_case(args):
     dnn-infer: two inference passes of an (untrained) network over the held-out
     states of the learned-surrogate workload (2^22 trajectory states, 2% of them
     moved 50-300 K outside the training T range, half below, half above).
+    fp64-chains: df_probe_fp64_chains over 1-8 warps per SM and 1-8 independent
+    DFMA chains per thread (FP64 dependent latency against throughput).
     h2: two thread-per-cell integrator launches (warm-up, measured) on 2^18
     cells of the bimodal 9-species field, in the launch shape the autotuner
     picks for the full field (64 threads x 2 blocks per SM, hottest first)."""
     import ctypes as C
     import torch
     from paper_2210_07094_gb300 import _lib
+    if args.profile_case == "fp64-chains":
+        L = _lib.load()
+        clk = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+        clk.start()
+        rows = []
+        for warps in (1, 2, 4, 8):
+            for chains in (1, 2, 4, 8):
+                ns, gf = C.c_double(), C.c_double()
+                _lib.check(L.df_probe_fp64_chains(warps, chains, 20000, C.byref(ns), C.byref(gf)),
+                           "df_probe_fp64_chains")
+                rows.append({"warps_per_sm": warps, "chains_per_thread": chains, "ns_per_step": ns.value,
+                             "gflops": gf.value})
+        c = clk.stop()
+        mhz = c.get("sm_mhz") or c.get("sm_max_mhz")
+        for r in rows:
+            r["cycles_per_step"] = r["ns_per_step"] * mhz * 1e-3 if mhz else None
+            # warp DFMA instructions per busy SM sub-partition per step (4 per SM;
+            # fewer than 4 warps occupy one sub-partition each)
+            per_smsp = r["chains_per_thread"] * max(1.0, r["warps_per_sm"] / 4.0)
+            r["cycles_per_warp_dfma_per_smsp"] = r["cycles_per_step"] / per_smsp if mhz else None
+            print(json.dumps({"case": "fp64-chains", **r}))
+        print(json.dumps({"case": "fp64-chains", "clocks": c}))
+        return 0
     if args.profile_case == "h2":
         import paper_2210_07094_gb300 as df
         from paper_2210_07094_gb300 import synth
@@ -416,7 +441,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the adjoint and 50-species measurements")
     ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
-    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon", "h2"],
+    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon", "h2", "fp64-chains"],
                     help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")

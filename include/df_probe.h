@@ -17,6 +17,16 @@ extern "C" {
  * Returns 0 or a negative DF_E* code (DF_EINVAL for iters < 1). */
 int df_probe_fp64_peak(int iters, double* gflops, double* ms);
 
+/* FP64 dependent-issue latency against throughput: one block of
+ * warps_per_sm warps on every SM, each thread running `chains` independent
+ * chains of `iters` dependent DFMAs (chains in {1, 2, 4, 8}, warps_per_sm in
+ * [1, 32], iters >= 1), timed with CUDA events on a private stream after one
+ * warm-up run; synchronous.
+ * ns_per_step: kernel time / iters, i.e. the time of one dependent step of a
+ * chain (host); gflops: 2 * FMAs / time (host, may be NULL).
+ * Returns 0 or a negative DF_E* code (DF_EINVAL for arguments out of range). */
+int df_probe_fp64_chains(int warps_per_sm, int chains, int iters, double* ns_per_step, double* gflops);
+
 /* y[i] = exp(x[i]) for i < n by the library's own table-driven exponential
  * (the one the rate kernels use), so that its accuracy can be checked against
  * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */

@@ -78,6 +78,7 @@ SIGNATURES = [
     ("df_strerror", C.c_char_p, [_i]),
     ("df_get_last_error_detail", _i, [C.c_char_p, _sz]),
     ("df_probe_fp64_peak", _i, [_i, _p, _p]),
+    ("df_probe_fp64_chains", _i, [_i, _i, _i, _p, _p]),
     ("df_probe_exp", _i, [_p, _p, C.c_longlong, _p]),
     ("df_probe_gelu", _i, [_p, _p, C.c_longlong, _i, _p]),
     ("df_probe_log", _i, [_p, _p, C.c_longlong, _p]),

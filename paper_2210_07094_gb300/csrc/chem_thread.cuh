@@ -149,14 +149,16 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
     S Mc(0.0);
 #pragma unroll
     for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
-    const S kinf = exp_tang(lnkf, mv.etab);
     const S lnk0 = lnA + tr[0] + tr[1] * lnT - tr[2] * invT;
-    const S k0 = exp_tang(lnk0, mv.etab);
-    const S Pr = k0 * Mc / kinf;
+    // Pr = k0 [M] / kinf, as exp(ln k0 - ln kinf) [M] (no division); the
+    // exponentials in pairs (see exp_pair)
+    S kinf, r0, e3, e1, e2, invKc;
+    exp_pair(lnkf, lnk0 - lnkf, mv.etab, kinf, r0);
+    const S Pr = r0 * Mc;
     if (!(val(Pr) > 0.0)) return;  // no low-pressure rate or no collider: k = 0
-    const S e3 = exp_tang(-T * tr[4], mv.etab);
-    const S e1 = exp_tang(-T * tr[5], mv.etab);
-    const S e2 = exp_tang(-tr[6] * invT, mv.etab);
+    exp_pair(-T * tr[4], -T * tr[5], mv.etab, e3, e1);
+    exp_pair(-tr[6] * invT, lnKcinv, mv.etab, e2, invKc);
+    if (!rev) invKc = S(0.0);
     const S Fc = (1.0 - tr[3]) * e3 + tr[3] * e1 + e2;
     const S Lc = fast_log10(Fc);
     const S cc = -0.4 - 0.67 * Lc;
@@ -164,15 +166,17 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
     const S L = fast_log10(Pr);
     const S x = L + cc;
     const S den = nn - 0.14 * x;
-    const S f1 = x / den;
-    const S q1 = 1.0 / (1.0 + f1 * f1);
+    // 1 / (1 + (x / den)^2) with one division
+    const S den2 = den * den;
+    const S q1 = den2 / (den2 + x * x);
     const S log10F = Lc * q1;
     const S F = exp_tang(LN10 * log10F, mv.etab);
     const S onePr = 1.0 / (1.0 + Pr);
     kf = kinf * Pr * onePr * F;
-    const S invKc = rev ? exp_tang(lnKcinv, mv.etab) : S(0.0);
     kr = kf * invKc;
     if (WITH_J) {
+      const S k0 = exp_tang(lnk0, mv.etab);
+      const S f1 = x / den;
       const S df1_dL = nn / (den * den);
       const S df1_dLc = (-0.67 * den - x * (-1.27 + 0.67 * 0.14)) / (den * den);
       const S dlogF_dL = -2.0 * Lc * f1 * df1_dL * q1 * q1;
@@ -256,11 +260,12 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
     const double* a = mv.sp + SP_REC * k + 2;
+    const double* ah = mv.sp + SP_REC * k + SP_H;  // a2/2 .. a5/5
+    const double* as = mv.sp + SP_REC * k + SP_S;  // a3/2 .. a5/4
     const S cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
     cpR[k] = cpk;
-    const S hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
-                 a[5] * invT;
-    const S sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    const S hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;
+    const S sk = a[0] * lnT + T * (a[1] + T * (as[0] + T * (as[1] + T * as[2]))) + a[6];
     hRT[k] = hk;
     gRT[k] = hk - sk;
     sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];
@@ -437,9 +442,10 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
     const double* a = mv.sp + SP_REC * k + 2;
     const S cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
     cpR[k] = cpk;
-    const S hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
-                 a[5] * invT;
-    const S sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    const double* ah = mv.sp + SP_REC * k + SP_H;  // a2/2 .. a5/5
+    const double* as = mv.sp + SP_REC * k + SP_S;  // a3/2 .. a5/4
+    const S hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;
+    const S sk = a[0] * lnT + T * (a[1] + T * (as[0] + T * (as[1] + T * as[2]))) + a[6];
     hRT[k] = hk;
     gRT[k] = hk - sk;
     sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];

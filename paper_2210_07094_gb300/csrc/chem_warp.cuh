@@ -80,9 +80,10 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   for (int k = lane; k < N; k += 32) {
     const double* a = mv.sp + SP_REC * k + 2;
     cpR[k] = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-    const double hk = a[0] + T * (a[1] * 0.5 + T * (a[2] * (1.0 / 3.0) + T * (a[3] * 0.25 + T * a[4] * 0.2))) +
-                      a[5] * invT;
-    const double sk = a[0] * lnT + T * (a[1] + T * (a[2] * 0.5 + T * (a[3] * (1.0 / 3.0) + T * a[4] * 0.25))) + a[6];
+    const double* ah = mv.sp + SP_REC * k + SP_H;  // a2/2 .. a5/5
+    const double* as = mv.sp + SP_REC * k + SP_S;  // a3/2 .. a5/4
+    const double hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;
+    const double sk = a[0] * lnT + T * (a[1] + T * (as[0] + T * (as[1] + T * as[2]))) + a[6];
     hRT[k] = hk;
     gRT[k] = hk - sk;
     sYW += y[1 + k] * mv.sp[SP_REC * k + 1];

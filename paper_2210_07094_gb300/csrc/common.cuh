@@ -29,8 +29,12 @@ constexpr int MAX_REACTIONS = 4096;
 constexpr int THREAD_PATH_MAX_N = 16;   // N <= this runs one cell per thread
 
 // --- blob layout (all in doubles) -----------------------------------------
-// species record k (SP_REC doubles):   W, 1/W, a1..a7
-constexpr int SP_REC = 9;
+// species record k (SP_REC doubles):   W, 1/W, a1..a7, then the NASA-7
+//   coefficients as the enthalpy and entropy polynomials use them:
+//   a2/2, a3/3, a4/4, a5/5 (h/RT) and a3/2, a4/3, a5/4 (s/R)
+constexpr int SP_REC = 16;
+constexpr int SP_H = 9;   // offset of a2/2 .. a5/5
+constexpr int SP_S = 13;  // offset of a3/2 .. a5/4
 // reaction record j (RX_REC doubles):  lnA, beta, Ea/R, meta0, meta1
 //   meta0 (8 bytes): reac[3], prod[3] species indices, nr | np << 4, flags
 //     flags: bit0-1 type (0 elementary, 1 third-body, 2 Troe), bit2 reversible

@@ -182,6 +182,9 @@ int parse_mechanism(const char* path, df_mech* m) {
       if (!num_of(&nasa->arr[i], &spec[SP_REC * k + 2 + i]))
         return set_error(DF_EMECH, "species " + name->str + ": nasa7 must hold numbers");
     }
+    const double* a = &spec[SP_REC * k + 2];
+    for (int i = 0; i < 4; ++i) spec[SP_REC * k + SP_H + i] = a[1 + i] / (2.0 + i);
+    for (int i = 0; i < 3; ++i) spec[SP_REC * k + SP_S + i] = a[2 + i] / (2.0 + i);
   }
   // reactions
   std::vector<double> rec(RX_REC * M);

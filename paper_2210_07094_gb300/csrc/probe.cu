@@ -19,6 +19,22 @@ __global__ void __launch_bounds__(256) k_dfma_chains(double* out, int iters, dou
   out[tid] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+template <int NC>
+__global__ void k_fma_chains(double* out, int iters, double a, double b) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  double x[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) x[c] = 1.0 + tid * 1e-9 + c * 1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) s += x[c];
+  out[tid] = s;
+}
+
 __global__ void k_exp_probe(const double* x, double* y, long long n) {
   __shared__ double2 tab[64];
   for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
@@ -81,6 +97,50 @@ extern "C" int df_probe_fp64_peak(int iters, double* gflops, double* ms) {
     const double flops = 2.0 * 8.0 * (double)iters * threads * blocks;
     *gflops = flops / (best * 1e-3) / 1e9;
     if (ms) *ms = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (out) cudaFree(out);
+  return rc;
+}
+
+extern "C" int df_probe_fp64_chains(int warps_per_sm, int chains, int iters, double* ns_per_step,
+                                    double* gflops) {
+  if (warps_per_sm < 1 || warps_per_sm > 32 || iters < 1 || !ns_per_step ||
+      !(chains == 1 || chains == 2 || chains == 4 || chains == 8))
+    return set_error(DF_EINVAL, "df_probe_fp64_chains: warps_per_sm in [1, 32], chains in {1, 2, 4, 8}, "
+                                "iters >= 1, ns_per_step required");
+  int dev = 0;
+  int rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  int sms = 0;
+  if ((rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count"))) return rc;
+  const int threads = 32 * warps_per_sm;
+  const int blocks = sms;
+  double* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rc = cuda_check(cudaMalloc(&out, sizeof(double) * threads * blocks), "cudaMalloc");
+  if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  float t = 0.f;
+  for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first run is a warm-up
+    cudaEventRecord(e0, st);
+    switch (chains) {
+      case 1: k_fma_chains<1><<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7); break;
+      case 2: k_fma_chains<2><<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7); break;
+      case 4: k_fma_chains<4><<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7); break;
+      default: k_fma_chains<8><<<blocks, threads, 0, st>>>(out, iters, 0.9999999, 1e-7); break;
+    }
+    cudaEventRecord(e1, st);
+    rc = cuda_check(cudaEventSynchronize(e1), "chain probe kernel");
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(&t, e0, e1), "elapsed");
+  }
+  if (!rc) {
+    *ns_per_step = (double)t * 1e6 / iters;
+    if (gflops) *gflops = 2.0 * chains * (double)iters * threads * blocks / (t * 1e-3) / 1e9;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

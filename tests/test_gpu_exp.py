@@ -1,4 +1,5 @@
-"""The library's table-driven exp against CUDA's exp and the host libm."""
+"""The library's table-driven exp and log against CUDA's and the host libm, and
+the FP64 chain probe."""
 import ctypes as C
 
 import numpy as np
@@ -53,3 +54,23 @@ def test_log_tab_absolute_accuracy():
     scale = np.maximum(1.0, np.abs(y_cuda[fin]))
     assert np.max(np.abs(y[fin] - y_cuda[fin]) / scale) <= 2 * 2.0 ** -52
     assert y[x.size - 1] == np.inf and y[x.size - 2] == -np.inf
+
+
+def test_fp64_chain_probe():
+    """df_probe_fp64_chains: rejects bad arguments; more warps and more
+    independent chains never lower the FP64 throughput it reports."""
+    import ctypes as C
+    from paper_2210_07094_gb300 import _lib
+    L = _lib.load()
+    ns, gf = C.c_double(), C.c_double()
+    assert L.df_probe_fp64_chains(0, 1, 100, C.byref(ns), C.byref(gf)) == -1
+    assert L.df_probe_fp64_chains(1, 3, 100, C.byref(ns), C.byref(gf)) == -1
+    assert L.df_probe_fp64_chains(1, 1, 0, C.byref(ns), C.byref(gf)) == -1
+    res = {}
+    for warps, chains in ((1, 1), (4, 1), (4, 8), (8, 8)):
+        _lib.check(L.df_probe_fp64_chains(warps, chains, 2000, C.byref(ns), C.byref(gf)), "df_probe_fp64_chains")
+        assert ns.value > 0 and gf.value > 0
+        res[(warps, chains)] = gf.value
+    assert res[(4, 1)] >= 0.9 * res[(1, 1)]
+    assert res[(4, 8)] >= 0.9 * res[(4, 1)]
+    assert res[(8, 8)] >= 0.9 * res[(4, 8)]
