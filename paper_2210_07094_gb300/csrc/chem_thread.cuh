@@ -77,12 +77,7 @@ __device__ __forceinline__ RxSlots load_slots(const double* r) {
   return s;
 }
 
-// Rate of one reaction (Sec. 2.3 eq. (sourceeq) bracket, with the Arrhenius
-// K_f, K_r = K_f/K_c, third-body [M] and Troe falloff) at temperature T and
-// concentrations C.  S is the scalar type (double, or Dual for directional
-// derivatives); Vec is any indexable vector of S.  NS > 0 fixes the species
-// count at compile time; otherwise Nrt is used.  With WITH_J it also returns
-// the pieces of dq/dT|_C and dq/dC.
+// exp of two arguments (two independent dependency chains for the scheduler)
 __device__ __forceinline__ void exp_pair(double a, double b, const double2* tab, double& ea, double& eb) {
   exp_tang2(a, b, tab, ea, eb);
 }
@@ -91,6 +86,8 @@ __device__ __forceinline__ void exp_pair(const Dual& a, const Dual& b, const dou
   eb = exp_tang(b, tab);
 }
 
+// Result of the rate of one reaction; with J also the pieces of dq/dT|_C and
+// dq/dC.
 template <class S>
 struct RateOutT {
   bool active;
@@ -104,33 +101,40 @@ struct RateOutT {
 };
 typedef RateOutT<double> RateOut;
 
+// Everything rate_one reads from memory for reaction j: its record, the
+// concentrations of its species, sum_k nu_kj g_k/RT (and h_k/RT with J) and,
+// for a third-body or falloff reaction, [M] = sum_l eps_l C_l.  Gathering the
+// next reaction's inputs before the current reaction's production rates are
+// stored keeps the shared-memory loads off the FP64 dependency chain (the
+// concentrations and g/RT do not change during the reaction loop).
+template <class S>
+struct RxIn {
+  double lnA, beta, EaR;
+  RxMeta mt;
+  RxSlots sl;
+  S cr[3], cp[3];  // reactant / product concentrations (1 where absent)
+  S sg, sh;        // sum nu g/RT, sum nu h/RT (products minus reactants)
+  S Mc;            // [M] (third body, falloff)
+};
+
 template <int NS, bool WITH_J, class S, class Vec>
-__device__ __forceinline__ void rate_one(const MechView& mv, const double* r, int Nrt, S T, S lnT, S invT,
-                                         S lnP0RT, const Vec& C, const Vec& gRT, const Vec& hRT,
-                                         RateOutT<S>& o) {
+__device__ __forceinline__ void rate_gather(const MechView& mv, const double* r, int Nrt, const Vec& C,
+                                            const Vec& gRT, const Vec& hRT, RxIn<S>& g) {
   const int N = NS > 0 ? NS : Nrt;
-  o.active = false;
-  const double lnA = r[0];
-  if (lnA == -INFINITY) return;  // A = 0: no rate
-  const double beta = r[1], EaR = r[2];
-  const RxMeta mt = load_meta(r);
-  o.mt = mt;
+  g.lnA = r[0];
+  g.beta = r[1];
+  g.EaR = r[2];
+  g.mt = load_meta(r);
+  g.sl = load_slots(r);
+  const RxMeta mt = g.mt;
   const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
-  const int type = mt.flags & 3;
-  const bool rev = (mt.flags & 4) != 0;
-  const S lnkf = lnA + beta * lnT - EaR * invT;
   const S one(1.0);
-  const S cr0 = C[mt.reac[0]];
-  const S cr1 = nr > 1 ? S(C[mt.reac[1]]) : one;
-  const S cr2 = nr > 2 ? S(C[mt.reac[2]]) : one;
-  const S cp0 = C[mt.prod[0]];
-  const S cp1 = np > 1 ? S(C[mt.prod[1]]) : one;
-  const S cp2 = np > 2 ? S(C[mt.prod[2]]) : one;
-  o.cr[0] = cr0; o.cr[1] = cr1; o.cr[2] = cr2;
-  o.cp[0] = cp0; o.cp[1] = cp1; o.cp[2] = cp2;
-  const S Pf = cr0 * cr1 * cr2;
-  const S Pb = cp0 * cp1 * cp2;
-  // sum_k nu_kj g_k/RT and sum_k nu_kj h_k/RT (products minus reactants)
+  g.cr[0] = C[mt.reac[0]];
+  g.cr[1] = nr > 1 ? S(C[mt.reac[1]]) : one;
+  g.cr[2] = nr > 2 ? S(C[mt.reac[2]]) : one;
+  g.cp[0] = C[mt.prod[0]];
+  g.cp[1] = np > 1 ? S(C[mt.prod[1]]) : one;
+  g.cp[2] = np > 2 ? S(C[mt.prod[2]]) : one;
   S sg = gRT[mt.prod[0]] - gRT[mt.reac[0]];
   S sh(0.0);
   if (WITH_J) sh = hRT[mt.prod[0]] - hRT[mt.reac[0]];
@@ -138,17 +142,46 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
   if (np > 2) { sg += gRT[mt.prod[2]]; if (WITH_J) sh += hRT[mt.prod[2]]; }
   if (nr > 1) { sg -= gRT[mt.reac[1]]; if (WITH_J) sh -= hRT[mt.reac[1]]; }
   if (nr > 2) { sg -= gRT[mt.reac[2]]; if (WITH_J) sh -= hRT[mt.reac[2]]; }
-  const int dnu = np - nr;
-  const S lnKcinv = sg - (double)dnu * lnP0RT;  // ln(1/K_c)
-  S kf, kr, mult(1.0), dqdM(0.0), dlnk(0.0);
-  const RxSlots sl = load_slots(r);
-  o.sl = sl;
-  if (type == 2) {
-    const double* tr = mv.tr + TR_REC * sl.troe;
-    const double* ef = mv.eff + N * sl.eff;
+  g.sg = sg;
+  g.sh = sh;
+  g.Mc = S(0.0);
+  if ((mt.flags & 3) != 0) {
+    const double* ef = mv.eff + N * g.sl.eff;
     S Mc(0.0);
 #pragma unroll
     for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
+    g.Mc = Mc;
+  }
+}
+
+// The rate of one reaction from its gathered inputs: Arrhenius K_f, K_r = K_f/K_c,
+// third-body [M] and Troe falloff; with WITH_J also dq/dT at fixed C and dq/d[M].
+template <int NS, bool WITH_J, class S>
+__device__ __forceinline__ void rate_compute(const MechView& mv, const RxIn<S>& g, S T, S lnT, S invT,
+                                             S lnP0RT, RateOutT<S>& o) {
+  o.active = false;
+  const double lnA = g.lnA;
+  if (lnA == -INFINITY) return;  // A = 0: no rate
+  const double beta = g.beta, EaR = g.EaR;
+  const RxMeta mt = g.mt;
+  o.mt = mt;
+  const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
+  const int type = mt.flags & 3;
+  const bool rev = (mt.flags & 4) != 0;
+  const S lnkf = lnA + beta * lnT - EaR * invT;
+  o.cr[0] = g.cr[0]; o.cr[1] = g.cr[1]; o.cr[2] = g.cr[2];
+  o.cp[0] = g.cp[0]; o.cp[1] = g.cp[1]; o.cp[2] = g.cp[2];
+  const S Pf = g.cr[0] * g.cr[1] * g.cr[2];
+  const S Pb = g.cp[0] * g.cp[1] * g.cp[2];
+  const S sg = g.sg, sh = g.sh;
+  const int dnu = np - nr;
+  const S lnKcinv = sg - (double)dnu * lnP0RT;  // ln(1/K_c)
+  S kf, kr, mult(1.0), dqdM(0.0), dlnk(0.0);
+  const RxSlots sl = g.sl;
+  o.sl = sl;
+  if (type == 2) {
+    const double* tr = mv.tr + TR_REC * sl.troe;
+    const S Mc = g.Mc;
     const S lnk0 = lnA + tr[0] + tr[1] * lnT - tr[2] * invT;
     // Pr = k0 [M] / kinf, as exp(ln k0 - ln kinf) [M] (no division); the
     // exponentials in pairs (see exp_pair)
@@ -181,23 +214,19 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
       const S df1_dLc = (-0.67 * den - x * (-1.27 + 0.67 * 0.14)) / (den * den);
       const S dlogF_dL = -2.0 * Lc * f1 * df1_dL * q1 * q1;
       const S dlogF_dLc = q1 - 2.0 * Lc * f1 * df1_dLc * q1 * q1;
-      const S g = onePr + dlogF_dL;  // d ln k / d ln Pr
+      const S gpr = onePr + dlogF_dL;  // d ln k / d ln Pr
       const S dlnkinf = (beta + EaR * invT) * invT;
       const S dlnk0 = (tr[1] + tr[2] * invT) * invT;
       const S dFc = -(1.0 - tr[3]) * tr[4] * e3 - tr[3] * tr[5] * e1 + tr[6] * invT * invT * e2;
-      dlnk = dlnkinf + g * (dlnk0 - dlnkinf) + dlogF_dLc * dFc / Fc;
-      // dk/d[M] = k0 F g / (1 + Pr); rate per unit k is (Pf - Pb/K_c)
-      dqdM = k0 * F * g * onePr * (Pf - Pb * invKc);
+      dlnk = dlnkinf + gpr * (dlnk0 - dlnkinf) + dlogF_dLc * dFc / Fc;
+      // dk/d[M] = k0 F gpr / (1 + Pr); rate per unit k is (Pf - Pb/K_c)
+      dqdM = k0 * F * gpr * onePr * (Pf - Pb * invKc);
     }
   } else {
     exp_pair(lnkf, lnkf + lnKcinv, mv.etab, kf, kr);
     if (!rev) kr = S(0.0);
     if (type == 1) {
-      const double* ef = mv.eff + N * sl.eff;
-      S Mc(0.0);
-#pragma unroll
-      for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
-      mult = Mc;
+      mult = g.Mc;
       dqdM = kf * Pf - kr * Pb;
     }
     if (WITH_J) dlnk = (beta + EaR * invT) * invT;
@@ -213,6 +242,21 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
   } else {
     o.dqdT = S(0.0);
   }
+}
+
+
+// Rate of one reaction (Sec. 2.3 eq. (sourceeq) bracket, with the Arrhenius
+// K_f, K_r = K_f/K_c, third-body [M] and Troe falloff) at temperature T and
+// concentrations C: rate_gather then rate_compute.  S is the scalar type
+// (double, or Dual for directional derivatives); Vec is any indexable vector of
+// S.  NS > 0 fixes the species count at compile time; otherwise Nrt is used.
+template <int NS, bool WITH_J, class S, class Vec>
+__device__ __forceinline__ void rate_one(const MechView& mv, const double* r, int Nrt, S T, S lnT, S invT,
+                                         S lnP0RT, const Vec& C, const Vec& gRT, const Vec& hRT,
+                                         RateOutT<S>& o) {
+  RxIn<S> g;
+  rate_gather<NS, WITH_J>(mv, r, Nrt, C, gRT, hRT, g);
+  rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, o);
 }
 
 // Optional accumulation of d/d ln A_j of a weighted sum of the right-hand side
