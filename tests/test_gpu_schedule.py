@@ -40,10 +40,11 @@ def test_autotune_choice_and_shape_independence():
     assert best.order_by_T in (0, 1) and best.path == 1 and ms > 0
     ref = _run(m, T0, p, Y0, f["dt"], best)
     assert int(ref[2].abs().sum()) == 0
-    # zero shape fields take the cached choice; explicit shapes and both work
-    # orders give bitwise the same cells
+    # zero shape fields take the cached choice; explicit shapes (the 32/64/128-
+    # thread kernels with a compile-time stride, 96 with the run-time one) and
+    # both work orders give bitwise the same cells
     assert _same(ref, _run(m, T0, p, Y0, f["dt"]))
-    for bt, bps, order in ((32, 1, 0), (128, 0, 1), (96, 2, 0)):
+    for bt, bps, order in ((32, 1, 0), (64, 2, 1), (128, 0, 1), (96, 2, 0)):
         o = df.default_opts()
         o.block_threads, o.blocks_per_sm, o.order_by_T = bt, bps, order
         assert _same(ref, _run(m, T0, p, Y0, f["dt"], o)), (bt, bps, order)
