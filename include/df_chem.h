@@ -84,7 +84,16 @@ typedef struct df_integ_opts {
                              df_chem_integrate_steps, df_chem_autotune; the
                              adjoint and the DNN integrator are constant
                              pressure and reject 1 with DF_EUNSUPPORTED)       */
-  int32_t reserved;
+  int32_t jit;            /* 0 (default): on the thread-per-cell path at constant
+                             pressure, use a kernel generated for the loaded
+                             mechanism (its reaction structure as straight-line
+                             code, compiled with NVRTC on first use and cached;
+                             32- and 64-thread blocks; the same operations as
+                             the mechanism-independent kernel, cells equal to
+                             rounding), falling back to
+                             that kernel when runtime compilation is
+                             unavailable (df_chem_jit_info says why); 1: always
+                             the mechanism-independent kernel                 */
 } df_integ_opts;
 
 void df_integ_opts_default(df_integ_opts* opts);
@@ -248,6 +257,22 @@ int df_chem_integrate_steps(const df_mech* mech, int64_t ncells, double* T, cons
 int df_chem_autotune(df_mech* mech, int64_t ncells, const double* T, const double* p, const double* Y,
                      double dt, const df_integ_opts* base, int64_t sample, df_integ_opts* best,
                      float* best_ms, df_stream_t stream);
+
+/* The kernel generated for this mechanism (df_integ_opts.jit): *used = 1 when
+ * the last thread-per-cell integrator launch on this handle ran it, else 0;
+ * detail (may be NULL, n bytes, NUL-terminated) receives its state: the NVRTC
+ * compile time, or why it is unavailable (NVRTC or the device headers not
+ * found, a compilation failure) -- then the mechanism-independent kernel ran.
+ * Errors: DF_EINVAL (null handle or used). */
+int df_chem_jit_info(const df_mech* mech, int32_t* used, char* detail, size_t n);
+
+/* The CUDA C++ source of the kernel generated for a mechanism file (what
+ * df_integ_opts.jit = 0 compiles; host only, no device needed), for
+ * inspection and for compiling it ahead of use.  The file is parsed as by
+ * df_mech_load.  buf (may be NULL) receives up to n bytes, NUL-terminated;
+ * *needed (may be NULL) the full size including the NUL.  Errors: DF_EINVAL,
+ * DF_EMECH (file or content). */
+int df_mech_generated_source(const char* mech_json_path, char* buf, size_t n, size_t* needed);
 
 /* Work counters of the last df_chem_integrate on this handle (host values; the
  * call synchronises `stream`): accepted and rejected substeps summed over all

@@ -86,6 +86,14 @@ class Mechanism:
                    "df_chem_last_stats")
         return a.value, r.value
 
+    def jit_info(self):
+        """(used, detail): whether the last thread-path integrator launch ran the
+        kernel generated for this mechanism, and its state (compile time or
+        why it is unavailable)."""
+        used = C.c_int32()
+        buf = C.create_string_buffer(4096)
+        _lib.check(_lib.load().df_chem_jit_info(self._h, C.byref(used), buf, 4096), "df_chem_jit_info")
+        return bool(used.value), buf.value.decode()
     def autotune(self, T, p, Y, dt: float, opts: IntegOpts | None = None, sample: int = 0, stream=None):
         """Time the integrator's launch shapes on (a copy of) the first `sample`
         cells and cache the fastest in the handle (df_chem_autotune).

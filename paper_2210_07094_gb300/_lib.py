@@ -23,7 +23,7 @@ class IntegOpts(C.Structure):
                 ("h0", C.c_double), ("h_min", C.c_double), ("max_substeps", C.c_int32),
                 ("method", C.c_int32), ("block_threads", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("order_by_T", C.c_int32), ("path", C.c_int32), ("reactor", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("jit", C.c_int32)]
 
 
 class DnnOpts(C.Structure):
@@ -53,6 +53,8 @@ SIGNATURES = [
     ("df_chem_jacobian", _i, [_p, _i64, _p, _p, _p, _p, _p]),
     ("df_chem_integrate", _i, [_p, _i64, _p, _p, _p, _d, _p, _p, _p, _p]),
     ("df_chem_last_stats", _i, [_p, _p, _p, _p]),
+    ("df_chem_jit_info", _i, [_p, _p, C.c_char_p, _sz]),
+    ("df_mech_generated_source", _i, [C.c_char_p, C.c_char_p, _sz, _p]),
     ("df_chem_autotune", _i, [_p, _i64, _p, _p, _p, _d, _p, _i64, _p, _p, _p]),
     ("df_chem_integrate_steps", _i, [_p, _i64, _p, _p, _p, _d, C.c_int32, _p, _p, _p, _p, _p]),
     ("df_chem_adjoint_workspace_size", _i, [_p, _i64, C.c_int32, _p]),

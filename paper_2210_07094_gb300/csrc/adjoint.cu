@@ -30,6 +30,7 @@
 #include <mutex>
 #include <string>
 
+#include "common.cuh"
 #include "rosenbrock.cuh"
 
 namespace df {

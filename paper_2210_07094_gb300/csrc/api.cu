@@ -1,6 +1,7 @@
 // C-ABI entry points: argument checks, handle life cycle, error reporting.
 // Every compute step runs in the kernels of integrate.cu (and the other .cu
 // files); this file only validates and forwards.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -273,6 +274,32 @@ int df_chem_adjoint(const df_mech* m, int64_t ncells, const double* T0, const do
     return set_error(DF_EINVAL, "df_chem_adjoint: invalid options");
   return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub,
                         workspace, ws_bytes, true, (cudaStream_t)stream);
+}
+
+int df_mech_generated_source(const char* path, char* buf, size_t n, size_t* needed) {
+  if (!path) return set_error(DF_EINVAL, "df_mech_generated_source: null path");
+  df_mech m;
+  int rc = parse_mechanism(path, &m);
+  if (rc) return rc;
+  const std::string src = jit_thread_source(&m);
+  if (needed) *needed = src.size() + 1;
+  if (buf && n > 0) {
+    const size_t k = std::min(n - 1, src.size());
+    memcpy(buf, src.data(), k);
+    buf[k] = '\0';
+  }
+  return DF_OK;
+}
+
+int df_chem_jit_info(const df_mech* m, int32_t* used, char* detail, size_t n) {
+  if (!m || !used) return set_error(DF_EINVAL, "df_chem_jit_info: null handle or output");
+  *used = m->jit_used;
+  if (detail && n > 0) {
+    const size_t k = std::min(n - 1, m->jit_note.size());
+    memcpy(detail, m->jit_note.data(), k);
+    detail[k] = '\0';
+  }
+  return DF_OK;
 }
 
 int df_chem_last_stats(const df_mech* m, int64_t* accepted, int64_t* rejected, df_stream_t stream) {

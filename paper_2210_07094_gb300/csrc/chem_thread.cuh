@@ -17,7 +17,7 @@
 //   dT/dt = -sum_k H_k wdot_k / (rho cp)   (constant-pressure adiabatic 0D reactor,
 //                                           Sec. 2.2 df0DFoam; h conserved)
 #pragma once
-#include "common.cuh"
+#include "dev_common.cuh"
 #include "fastexp.cuh"
 #include "fastlog.cuh"
 #include "dual.cuh"

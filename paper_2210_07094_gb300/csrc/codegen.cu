@@ -1,0 +1,465 @@
+// Mechanism-specific thread-per-cell integrator, generated and compiled at run
+// time.
+//
+// The mechanism-independent kernel reads each reaction's species indices,
+// stoichiometry and type from the mechanism blob and keeps the per-thread
+// species vectors (C, wdot, g/RT, h/RT, cp/R) in shared memory, because those
+// indices are only known at run time.  For a loaded mechanism the library can
+// instead emit the evaluation of f and J as straight-line code with the
+// species indices, the reactant / product counts and the reaction types as
+// literals (the numbers -- ln A, beta, Ea/R, efficiencies, Troe parameters,
+// NASA-7 coefficients -- are still read from the blob, so df_mech_set_lnA keeps
+// working), compile it with NVRTC into a module holding the same persistent
+// kernel (integrate_thread.cuh) with that evaluation policy, and launch it
+// through the driver API.  The species vectors then live in registers, no
+// reaction metadata is decoded and no branch depends on the reaction, and the
+// shared memory per thread drops to J and the six stage vectors.  The
+// operations are the mechanism-independent kernel's, in the same order; the
+// two compilations may contract different multiply-adds, so cells agree to
+// rounding.
+//
+// NVRTC is opened at run time (dlopen); the driver entry points come through
+// cudaGetDriverEntryPointByVersion.  If either is missing, the headers cannot
+// be found, or the compilation fails, the integrator uses the
+// mechanism-independent kernel and df_chem_jit_info reports why.
+#include <dlfcn.h>
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "integrate_thread.cuh"
+
+namespace df {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// source generation
+// ---------------------------------------------------------------------------
+RxMeta meta_of(const df_mech* m, int j) {
+  RxMeta mt;
+  memcpy(&mt, &m->blob_host[m->dims.off_rx + RX_REC * j + 3], 8);
+  return mt;
+}
+RxSlots slots_of(const df_mech* m, int j) {
+  RxSlots sl;
+  memcpy(&sl, &m->blob_host[m->dims.off_rx + RX_REC * j + 4], 8);
+  return sl;
+}
+
+// f and J of the loaded mechanism as straight-line code: the mechanism-
+// independent eval_thread (chem_thread.cuh) at constant pressure with every
+// reaction's indices and type resolved, in the same order of operations
+void emit_eval(std::ostringstream& o, const df_mech* m) {
+  const int N = m->dims.N, n = N + 1, M = m->dims.M;
+  o << "template <bool WITH_J, int ST>\n"
+    << "__device__ __forceinline__ double gen_eval(const MechView& mv, const double pc, const double (&y)[" << n
+    << "], double (&f)[" << n << "], SVT<double, ST> Jv) {\n"
+    << "  constexpr int NS = " << N << ";\n  constexpr int n = NS + 1;\n"
+    << "  const double T = y[0];\n  const double lnT = fast_log(T);\n  const double invT = 1.0 / T;\n"
+    << "  double C[NS], wdot[NS], gRT[NS], hRT[NS], cpR[NS];\n"
+    << "  double sumYW = 0.0, cpm = 0.0;\n"
+    << "#pragma unroll\n"
+    << "  for (int k = 0; k < NS; ++k) {\n"
+    << "    const double* a = mv.sp + SP_REC * k + 2;\n"
+    << "    const double* ah = mv.sp + SP_REC * k + SP_H;\n"
+    << "    const double* as = mv.sp + SP_REC * k + SP_S;\n"
+    << "    const double cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));\n"
+    << "    cpR[k] = cpk;\n"
+    << "    const double hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;\n"
+    << "    const double sk = a[0] * lnT + T * (a[1] + T * (as[0] + T * (as[1] + T * as[2]))) + a[6];\n"
+    << "    hRT[k] = hk;\n    gRT[k] = hk - sk;\n"
+    << "    sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];\n"
+    << "    cpm += y[1 + k] * cpk * mv.sp[SP_REC * k + 1];\n"
+    << "  }\n"
+    << "  cpm = cpm * RU;\n"
+    << "  const double rho = pc * invT / (RU * sumYW);\n"
+    << "  const double invrho = 1.0 / rho;\n  const double invcp = 1.0 / cpm;\n"
+    << "#pragma unroll\n"
+    << "  for (int k = 0; k < NS; ++k) {\n    C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];\n    wdot[k] = 0.0;\n  }\n"
+    << "  if (WITH_J) {\n#pragma unroll\n    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;\n  }\n"
+    << "  const double lnP0RT = LOG_PSTD_RU - lnT;\n";
+  for (int j = 0; j < M; ++j) {
+    const RxMeta mt = meta_of(m, j);
+    const RxSlots sl = slots_of(m, j);
+    const int nr = mt.nrnp & 15, np = mt.nrnp >> 4, type = mt.flags & 3;
+    const int r[3] = {mt.reac[0], mt.reac[1], mt.reac[2]};
+    const int p[3] = {mt.prod[0], mt.prod[1], mt.prod[2]};
+    o << "  {  // reaction " << j << "\n"
+      << "    RxIn<double> g;\n    const double* r = mv.rx + RX_REC * " << j << ";\n"
+      << "    g.lnA = r[0];\n    g.beta = r[1];\n    g.EaR = r[2];\n";
+    for (int i = 0; i < 3; ++i) o << "    g.mt.reac[" << i << "] = " << r[i] << ";\n";
+    for (int i = 0; i < 3; ++i) o << "    g.mt.prod[" << i << "] = " << p[i] << ";\n";
+    o << "    g.mt.nrnp = " << (int)mt.nrnp << ";\n    g.mt.flags = " << (int)mt.flags << ";\n"
+      << "    g.sl.eff = " << sl.eff << ";\n    g.sl.troe = " << sl.troe << ";\n";
+    for (int i = 0; i < 3; ++i)
+      o << "    g.cr[" << i << "] = " << (i < nr ? "C[" + std::to_string(r[i]) + "]" : std::string("1.0")) << ";\n";
+    for (int i = 0; i < 3; ++i)
+      o << "    g.cp[" << i << "] = " << (i < np ? "C[" + std::to_string(p[i]) + "]" : std::string("1.0")) << ";\n";
+    // sum nu g/RT and h/RT in rate_gather's order
+    o << "    double sg = gRT[" << p[0] << "] - gRT[" << r[0] << "];\n"
+      << "    double sh = 0.0;\n    if (WITH_J) sh = hRT[" << p[0] << "] - hRT[" << r[0] << "];\n";
+    for (int i = 1; i < np; ++i) o << "    sg += gRT[" << p[i] << "];\n    if (WITH_J) sh += hRT[" << p[i] << "];\n";
+    for (int i = 1; i < nr; ++i) o << "    sg -= gRT[" << r[i] << "];\n    if (WITH_J) sh -= hRT[" << r[i] << "];\n";
+    o << "    g.sg = sg;\n    g.sh = sh;\n";
+    if (type != 0) {
+      o << "    {\n      const double* ef = mv.eff + NS * " << sl.eff << ";\n      double Mc = 0.0;\n"
+        << "#pragma unroll\n      for (int l = 0; l < NS; ++l) Mc += ef[l] * C[l];\n      g.Mc = Mc;\n    }\n";
+    } else {
+      o << "    g.Mc = 0.0;\n";
+    }
+    o << "    RateOutT<double> ro;\n    rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, ro);\n"
+      << "    if (ro.active) {\n      const double q = ro.q;\n";
+    for (int i = 0; i < nr; ++i) o << "      wdot[" << r[i] << "] -= q;\n";
+    for (int i = 0; i < np; ++i) o << "      wdot[" << p[i] << "] += q;\n";
+    o << "      if (WITH_J) {\n"
+      << "        const double dr0 = ro.fk * ro.cr[1] * ro.cr[2];\n"
+      << "        const double dr1 = ro.fk * ro.cr[0] * ro.cr[2];\n"
+      << "        const double dr2 = ro.fk * ro.cr[0] * ro.cr[1];\n"
+      << "        const double dp0 = -(ro.rk * ro.cp[1] * ro.cp[2]);\n"
+      << "        const double dp1 = -(ro.rk * ro.cp[0] * ro.cp[2]);\n"
+      << "        const double dp2 = -(ro.rk * ro.cp[0] * ro.cp[1]);\n"
+      << "        (void)dr1; (void)dr2; (void)dp1; (void)dp2;\n";
+    for (int a = 0; a < nr + np; ++a) {
+      const bool isr = a < nr;
+      const int row = 1 + (isr ? r[a] : p[a - nr]);
+      const char* sg = isr ? "-" : "";
+      o << "        Jv[" << row * n << "] += " << sg << "(ro.dqdT);\n";
+      for (int i = 0; i < nr; ++i) o << "        Jv[" << row * n + 1 + r[i] << "] += " << sg << "(dr" << i << ");\n";
+      for (int i = 0; i < np; ++i) o << "        Jv[" << row * n + 1 + p[i] << "] += " << sg << "(dp" << i << ");\n";
+      if (type != 0)
+        o << "        {\n          const double* ef = mv.eff + NS * " << sl.eff << ";\n          const double cM = " << sg
+          << "(ro.dqdM);\n#pragma unroll\n          for (int l = 0; l < NS; ++l) Jv[" << row * n + 1
+          << " + l] += cM * ef[l];\n        }\n";
+    }
+    o << "      }\n    }\n  }\n";
+  }
+  o << "  double Hw = 0.0;\n#pragma unroll\n  for (int k = 0; k < NS; ++k) Hw += hRT[k] * wdot[k];\n"
+    << "  Hw = Hw * (RU * T);\n"
+    << "#pragma unroll\n  for (int k = 0; k < NS; ++k) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;\n"
+    << "  f[0] = -(Hw * invrho * invcp);\n"
+    << "  if (WITH_J) {\n"
+    << "    const double Wbar = 1.0 / sumYW;\n"
+    << "#pragma unroll 1\n"
+    << "    for (int k = 0; k < NS; ++k) {\n"
+    << "      const int row = (1 + k) * n;\n      const double Wk = mv.sp[SP_REC * k];\n"
+    << "      double s = 0.0;\n#pragma unroll\n      for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * C[l];\n"
+    << "      const double wk = wdot[k];\n      const double a = Wk * Wbar * invrho * (wk - s);\n"
+    << "#pragma unroll\n      for (int i = 0; i < NS; ++i) {\n        const double iWi = mv.sp[SP_REC * i + 1];\n"
+    << "        Jv[row + 1 + i] = (Wk * Jv[row + 1 + i] + a) * iWi;\n      }\n"
+    << "      Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);\n    }\n"
+    << "    double dcp = 0.0, cpf = 0.0;\n#pragma unroll\n    for (int k = 0; k < NS; ++k) {\n"
+    << "      const double* a = mv.sp + SP_REC * k + 2;\n      const double iW = mv.sp[SP_REC * k + 1];\n"
+    << "      dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;\n"
+    << "      cpf += cpR[k] * iW * f[1 + k];\n    }\n"
+    << "    dcp = dcp * RU;\n    cpf = cpf * RU;\n"
+    << "#pragma unroll 1\n    for (int jc = 0; jc < n; ++jc) {\n      double acc = 0.0;\n"
+    << "#pragma unroll\n      for (int k = 0; k < NS; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];\n"
+    << "      acc = acc * (RU * T);\n"
+    << "      if (jc == 0) {\n        Jv[0] = -(invcp * (acc + cpf)) - f[0] * dcp * invcp;\n      } else {\n"
+    << "        const double iWj = mv.sp[SP_REC * (jc - 1) + 1];\n        const double cpj = RU * cpR[jc - 1] * iWj;\n"
+    << "        Jv[jc] = -(invcp * acc) - f[0] * cpj * invcp;\n      }\n    }\n  }\n"
+    << "  return -Hw;\n}\n\n";
+}
+
+}  // namespace
+
+std::string jit_thread_source(const df_mech* m) {
+  std::ostringstream o;
+  o << "// generated for a " << m->dims.N << "-species / " << m->dims.M << "-reaction mechanism\n"
+    << "#include \"integrate_thread.cuh\"\n\nnamespace df {\n\n";
+  emit_eval(o, m);
+  o << "struct GenEval {\n"
+    << "  static constexpr bool kSpeciesVectors = false;\n"
+    << "  template <int NS, bool WITH_J, bool CONSTV, int ST>\n"
+    << "  __device__ __forceinline__ static double run(const MechView& mv, double pc, const double (&y)[NS + 1],\n"
+    << "                                               double (&f)[NS + 1], SVT<double, ST>, SVT<double, ST>,\n"
+    << "                                               SVT<double, ST>, SVT<double, ST>, SVT<double, ST>,\n"
+    << "                                               SVT<double, ST> Jv) {\n"
+    << "    static_assert(!CONSTV, \"generated evaluation: constant pressure\");\n"
+    << "    return gen_eval<WITH_J, ST>(mv, pc, y, f, Jv);\n  }\n};\n\n}  // namespace df\n";
+  return o.str();
+}
+
+std::string jit_kernel_name(int N, int threads) {
+  return "df::k_integrate_thread<" + std::to_string(N) + ", false, " + std::to_string(threads) + ", df::GenEval>";
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// NVRTC (opened at run time) and the driver entry points
+// ---------------------------------------------------------------------------
+typedef int (*nvrtcCreateProgram_t)(void**, const char*, const char*, int, const char* const*, const char* const*);
+typedef int (*nvrtcCompileProgram_t)(void*, int, const char* const*);
+typedef int (*nvrtcGetSize_t)(void*, size_t*);
+typedef int (*nvrtcGetBuf_t)(void*, char*);
+typedef int (*nvrtcDestroyProgram_t)(void**);
+typedef int (*nvrtcAddNameExpression_t)(void*, const char*);
+typedef int (*nvrtcGetLoweredName_t)(void*, const char*, const char**);
+
+struct Nvrtc {
+  bool ok = false;
+  std::string why;
+  nvrtcCreateProgram_t create = nullptr;
+  nvrtcCompileProgram_t compile = nullptr;
+  nvrtcGetSize_t log_size = nullptr, cubin_size = nullptr;
+  nvrtcGetBuf_t log = nullptr, cubin = nullptr;
+  nvrtcDestroyProgram_t destroy = nullptr;
+  nvrtcAddNameExpression_t add_name = nullptr;
+  nvrtcGetLoweredName_t lowered = nullptr;
+};
+
+const Nvrtc& nvrtc() {
+  static Nvrtc r;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"};
+    void* h = nullptr;
+    for (const char* nm : names)
+      if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+      r.why = "NVRTC library not found";
+      return;
+    }
+    r.create = (nvrtcCreateProgram_t)dlsym(h, "nvrtcCreateProgram");
+    r.compile = (nvrtcCompileProgram_t)dlsym(h, "nvrtcCompileProgram");
+    r.log_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetProgramLogSize");
+    r.log = (nvrtcGetBuf_t)dlsym(h, "nvrtcGetProgramLog");
+    r.cubin_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetCUBINSize");
+    r.cubin = (nvrtcGetBuf_t)dlsym(h, "nvrtcGetCUBIN");
+    r.destroy = (nvrtcDestroyProgram_t)dlsym(h, "nvrtcDestroyProgram");
+    r.add_name = (nvrtcAddNameExpression_t)dlsym(h, "nvrtcAddNameExpression");
+    r.lowered = (nvrtcGetLoweredName_t)dlsym(h, "nvrtcGetLoweredName");
+    r.ok = r.create && r.compile && r.log_size && r.log && r.cubin_size && r.cubin && r.destroy && r.add_name &&
+           r.lowered;
+    if (!r.ok) r.why = "NVRTC library lacks an entry point";
+  });
+  return r;
+}
+
+typedef CUresult (*cuModuleLoadData_t)(CUmodule*, const void*);
+typedef CUresult (*cuModuleGetFunction_t)(CUfunction*, CUmodule, const char*);
+typedef CUresult (*cuModuleGetGlobal_t)(CUdeviceptr*, size_t*, CUmodule, const char*);
+typedef CUresult (*cuLaunchKernel_t)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned,
+                                     unsigned, CUstream, void**, void**);
+typedef CUresult (*cuFuncSetAttribute_t)(CUfunction, CUfunction_attribute, int);
+typedef CUresult (*cuOccupancy_t)(int*, CUfunction, int, size_t);
+
+struct Driver {
+  bool ok = false;
+  cuModuleLoadData_t load = nullptr;
+  cuModuleGetFunction_t get_function = nullptr;
+  cuModuleGetGlobal_t get_global = nullptr;
+  cuLaunchKernel_t launch = nullptr;
+  cuFuncSetAttribute_t set_attr = nullptr;
+  cuOccupancy_t occupancy = nullptr;
+};
+
+void* entry(const char* name) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return p;
+}
+
+const Driver& driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    d.load = (cuModuleLoadData_t)entry("cuModuleLoadData");
+    d.get_function = (cuModuleGetFunction_t)entry("cuModuleGetFunction");
+    d.get_global = (cuModuleGetGlobal_t)entry("cuModuleGetGlobal");
+    d.launch = (cuLaunchKernel_t)entry("cuLaunchKernel");
+    d.set_attr = (cuFuncSetAttribute_t)entry("cuFuncSetAttribute");
+    d.occupancy = (cuOccupancy_t)entry("cuOccupancyMaxActiveBlocksPerMultiprocessor");
+    d.ok = d.load && d.get_function && d.get_global && d.launch && d.set_attr && d.occupancy;
+  });
+  return d;
+}
+
+// directory of the library's device headers: next to the shared library
+// (<package>/_build/lib*.so -> <package>/csrc)
+std::string header_dir() {
+  Dl_info info;
+  if (!dladdr((void*)&header_dir, &info) || !info.dli_fname) return "";
+  std::string so = info.dli_fname;
+  const size_t cut = so.find_last_of('/');
+  if (cut == std::string::npos) return "";
+  std::string dir = so.substr(0, cut);
+  const size_t up = dir.find_last_of('/');
+  if (up == std::string::npos) return "";
+  std::string cs = dir.substr(0, up) + "/csrc";
+  std::string probe = cs + "/integrate_thread.cuh";
+  if (FILE* f = fopen(probe.c_str(), "r")) {
+    fclose(f);
+    return cs;
+  }
+  return "";
+}
+
+// one compiled module per (device, generated source)
+struct Module {
+  bool ok = false;
+  std::string why;
+  CUmodule mod = nullptr;
+  std::map<int, CUfunction> fn;  // threads per block -> kernel
+  size_t compile_ms = 0;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, std::string>, Module> g_modules;
+
+constexpr int kThreads[] = {32, 64};
+
+Module build_module(int dev, const df_mech* m, const std::string& src) {
+  Module r;
+  const Nvrtc& nv = nvrtc();
+  if (!nv.ok) {
+    r.why = nv.why;
+    return r;
+  }
+  const Driver& drv = driver();
+  if (!drv.ok) {
+    r.why = "driver entry points for module loading unavailable";
+    return r;
+  }
+  const std::string inc = header_dir();
+  if (inc.empty()) {
+    r.why = "device headers (csrc) not found next to the library";
+    return r;
+  }
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    r.why = "device attributes unavailable";
+    return r;
+  }
+  const std::string arch = "--gpu-architecture=sm_" + std::to_string(major * 10 + minor) + "a";
+  const std::string incopt = "-I" + inc;
+  const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
+                        "-diag-suppress=177"};
+  void* prog = nullptr;
+  if (nv.create(&prog, src.c_str(), "df_generated.cu", 0, nullptr, nullptr) != 0) {
+    r.why = "nvrtcCreateProgram failed";
+    return r;
+  }
+  std::vector<std::string> names;
+  for (int t : kThreads) names.push_back(jit_kernel_name(m->dims.N, t));
+  names.push_back("&df::c_tab");
+  for (auto& s : names) nv.add_name(prog, s.c_str());
+  const auto t0 = std::chrono::steady_clock::now();
+  const int rc = nv.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+  r.compile_ms = (size_t)std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0)
+                     .count();
+  if (rc != 0) {
+    size_t n = 0;
+    nv.log_size(prog, &n);
+    std::string log(n, '\0');
+    if (n) nv.log(prog, &log[0]);
+    r.why = "NVRTC compilation failed: " + log.substr(0, 2000);
+    nv.destroy(&prog);
+    return r;
+  }
+  size_t nb = 0;
+  nv.cubin_size(prog, &nb);
+  std::vector<char> cubin(nb);
+  nv.cubin(prog, cubin.data());
+  std::vector<std::string> lowered;
+  for (auto& s : names) {
+    const char* l = nullptr;
+    nv.lowered(prog, s.c_str(), &l);
+    lowered.push_back(l ? std::string(l) : std::string());
+  }
+  nv.destroy(&prog);
+  if (drv.load(&r.mod, cubin.data()) != CUDA_SUCCESS) {
+    r.why = "cuModuleLoadData failed";
+    return r;
+  }
+  for (size_t i = 0; i < sizeof(kThreads) / sizeof(kThreads[0]); ++i) {
+    CUfunction f = nullptr;
+    if (lowered[i].empty() || drv.get_function(&f, r.mod, lowered[i].c_str()) != CUDA_SUCCESS) {
+      r.why = "generated kernel not found in the module";
+      return r;
+    }
+    r.fn[kThreads[i]] = f;
+  }
+  CUdeviceptr tab = 0;
+  size_t tab_bytes = 0;
+  if (lowered.back().empty() || drv.get_global(&tab, &tab_bytes, r.mod, lowered.back().c_str()) != CUDA_SUCCESS ||
+      tab_bytes != 2 * sizeof(RosTab)) {
+    r.why = "Rosenbrock table not found in the module";
+    return r;
+  }
+  RosTab t[2] = {make_rodas4(), make_rodas3()};
+  if (cudaMemcpy((void*)tab, t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    r.why = "upload of the Rosenbrock tables failed";
+    return r;
+  }
+  r.ok = true;
+  return r;
+}
+
+}  // namespace
+
+int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cudaStream_t st, bool* launched) {
+  *launched = false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DF_OK;
+  const std::string src = jit_thread_source(m);
+  Module* md = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto key = std::make_pair(dev, src);
+    auto it = g_modules.find(key);
+    if (it == g_modules.end()) it = g_modules.emplace(key, build_module(dev, m, src)).first;
+    md = &it->second;
+  }
+  m->jit_note = md->ok ? "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms" : md->why;
+  if (!md->ok) return DF_OK;
+  auto f = md->fn.find(threads);
+  if (f == md->fn.end()) return DF_OK;  // no generated kernel for this block size
+  const Driver& drv = driver();
+  const int N = m->dims.N;
+  const int per_thread = (N + 1) * (N + 1) + 6 * (N + 1);  // J and the stage vectors
+  IntegArgs args = a;
+  args.stage_blob = 1;
+  size_t sm = sizeof(double) * (128 + (size_t)blob_smem_doubles(m->dims) + (size_t)per_thread * threads);
+  if (sm > m->max_smem_optin) {
+    args.stage_blob = 0;
+    sm = sizeof(double) * (128 + (size_t)per_thread * threads);
+  }
+  if (sm > m->max_smem_optin) return DF_OK;
+  if (drv.set_attr(f->second, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)sm) != CUDA_SUCCESS)
+    return set_error(DF_ECUDA, "generated integrator: shared-memory attribute");
+  int occ = 0;
+  if (drv.occupancy(&occ, f->second, threads, sm) != CUDA_SUCCESS || occ < 1)
+    return set_error(DF_ECUDA, "generated integrator: occupancy query");
+  const int per_sm = bps > 0 ? std::min(bps, occ) : occ;
+  int64_t blocks = (int64_t)m->num_sms * per_sm;
+  const int64_t need = (args.nwork + threads - 1) / threads;
+  if (blocks > need) blocks = std::max<int64_t>(1, need);
+  int rc = cuda_check(cudaMemsetAsync(m->counters, 0, 4 * sizeof(unsigned long long), st), "reset work counter");
+  if (rc) return rc;
+  void* params[] = {&args};
+  if (drv.launch(f->second, (unsigned)blocks, 1, 1, (unsigned)threads, 1, 1, (unsigned)sm, (CUstream)st, params,
+                 nullptr) != CUDA_SUCCESS)
+    return set_error(DF_ECUDA, "generated integrator launch");
+  *launched = true;
+  m->jit_used = 1;
+  return DF_OK;
+}
+
+}  // namespace df

@@ -1,10 +1,6 @@
-// Internal definitions shared by the library's translation units.
-//
-// Mechanism blob: one contiguous FP64 array holding the species and reaction
-// data of a mechanism (Sec. 2.3 eq. (reaction): nu'_{aj}, nu''_{aj}; Arrhenius
-// K_f; third-body efficiencies; Troe falloff; NASA-7 thermo).  The same bytes
-// live in device memory and are staged into shared memory by the kernels, so
-// every record has a fixed size and an 8-byte alignment.
+// Internal definitions shared by the library's translation units (host side;
+// the device-side definitions and the mechanism blob layout are in
+// dev_common.cuh).
 #pragma once
 #include <cstdint>
 #include <cstring>
@@ -15,68 +11,8 @@
 
 #include "../../include/df_chem.h"
 
-namespace df {
+#include "dev_common.cuh"
 
-// physical constants (cgs inside the kernels)
-constexpr double RU = 8.314462618e7;         // erg/(mol K)
-constexpr double RU_SI = 8.314462618;        // J/(mol K)
-constexpr double P_STD = 1.01325e6;          // standard-state pressure, dyn/cm^2
-constexpr double LN10 = 2.302585092994045684;
-constexpr double LOG_PSTD_RU = -4.4074185890025275;     // ln(P_STD / RU), RU in erg/(mol K)
-
-constexpr int MAX_SPECIES = 64;
-constexpr int MAX_REACTIONS = 4096;
-constexpr int THREAD_PATH_MAX_N = 16;   // N <= this runs one cell per thread
-
-// --- blob layout (all in doubles) -----------------------------------------
-// species record k (SP_REC doubles):   W, 1/W, a1..a7, then the NASA-7
-//   coefficients as the enthalpy and entropy polynomials use them:
-//   a2/2, a3/3, a4/4, a5/5 (h/RT) and a3/2, a4/3, a5/4 (s/R)
-constexpr int SP_REC = 16;
-constexpr int SP_H = 9;   // offset of a2/2 .. a5/5
-constexpr int SP_S = 13;  // offset of a3/2 .. a5/4
-// reaction record j (RX_REC doubles):  lnA, beta, Ea/R, meta0, meta1
-//   meta0 (8 bytes): reac[3], prod[3] species indices, nr | np << 4, flags
-//     flags: bit0-1 type (0 elementary, 1 third-body, 2 Troe), bit2 reversible
-//   meta1 (8 bytes): int32 effslot (-1: none), int32 troeslot (-1: none)
-constexpr int RX_REC = 5;
-// Troe record (TR_REC doubles): lnA0 - lnA, beta0, Ea0/R, alpha, 1/T***, 1/T*, T**, pad
-constexpr int TR_REC = 8;
-// efficiency record: N doubles per third-body / falloff reaction
-
-struct RxMeta {
-  uint8_t reac[3];
-  uint8_t prod[3];
-  uint8_t nrnp;
-  uint8_t flags;
-};
-static_assert(sizeof(RxMeta) == 8, "meta layout");
-struct RxSlots {
-  int32_t eff;
-  int32_t troe;
-};
-static_assert(sizeof(RxSlots) == 8, "slot layout");
-
-struct MechDims {
-  int N, M, n_eff, n_troe;
-  int off_sp, off_rx, off_tr, off_eff, total;  // offsets in doubles
-};
-
-inline MechDims mech_dims(int N, int M, int n_eff, int n_troe) {
-  MechDims d;
-  d.N = N;
-  d.M = M;
-  d.n_eff = n_eff;
-  d.n_troe = n_troe;
-  d.off_sp = 0;
-  d.off_rx = d.off_sp + SP_REC * N;
-  d.off_tr = d.off_rx + RX_REC * M;
-  d.off_eff = d.off_tr + TR_REC * n_troe;
-  d.total = d.off_eff + n_eff * N;
-  return d;
-}
-
-}  // namespace df
 
 // the opaque handle
 struct df_mech {
@@ -100,6 +36,10 @@ struct df_mech {
   int64_t tuned_for_ncells = -1;
   int num_sms = 0;
   size_t max_smem_optin = 0;
+  // generated thread-path kernel (codegen.cu): 1 when the last thread-path
+  // launch used it, and its state (compile time, or why it is unavailable)
+  int jit_used = 0;
+  std::string jit_note;
 };
 
 namespace df {
@@ -131,6 +71,14 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
                           const df_integ_opts& o, int32_t* status, int32_t* nsub, const int32_t* order,
                           int64_t nwork, cudaStream_t st, const unsigned long long* nwork_dev = nullptr,
                           int nsteps = 1, double* t_ign = nullptr);
+
+// generated thread-per-cell integrator (codegen.cu)
+struct IntegArgs;
+std::string jit_thread_source(const df_mech* m);
+// launch the kernel generated for m with `threads` per block if it can (NVRTC
+// available, the module compiled, a generated kernel for that block size);
+// *launched says whether it did.  Errors only for a failed launch.
+int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cudaStream_t st, bool* launched);
 
 // adjoint (adjoint.cu)
 // with_stages: also room for the stored stages and LU factors of every

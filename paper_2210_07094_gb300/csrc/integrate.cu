@@ -16,12 +16,12 @@
 #include <algorithm>
 #include <cmath>
 
+#include "common.cuh"
 #include "chem_warp.cuh"
-#include "rosenbrock.cuh"
+#include "integrate_thread.cuh"
 
 namespace df {
 
-static __constant__ RosTab c_tab[2];
 
 static bool g_tab_ready[64] = {false};
 
@@ -34,184 +34,6 @@ static int ensure_tables(int dev) {
   return rc;
 }
 
-struct IntegArgs {
-  const double* blob;
-  MechDims d;
-  int64_t ncells;
-  double* T;
-  const double* p;
-  double* Y;
-  double dt;
-  double rtol, atolY, atolT, h0, hmin;
-  int max_sub;
-  int method;
-  int32_t* status;
-  int32_t* nsub;
-  const int32_t* order;            // optional list of the cell indices to advance
-  int64_t nwork;                   // number of cells to advance (entries of order)
-  const unsigned long long* nwork_dev;  // if set, the number of cells is read from here
-  unsigned long long* counters;    // [0] next cell, [1] accepted, [2] rejected
-  int stage_blob;                  // 1: copy the blob into shared memory
-  int nsteps;                      // consecutive steps of dt per cell (>= 1)
-  double* t_ign;                   // optional: time of the largest dT/dt per cell
-};
-
-constexpr unsigned FULL = 0xffffffffu;
-
-// per-thread shared-memory doubles of the thread path
-template <int NS>
-__host__ __device__ constexpr int thread_ws_doubles() {
-  return 5 * NS + (NS + 1) * (NS + 1) + 6 * (NS + 1);
-}
-
-__host__ __device__ inline int blob_smem_doubles(const MechDims& d) { return (d.total + 1) & ~1; }
-
-// BT > 0: the kernel is launched with exactly BT threads per block, the
-// stride of the per-thread shared-memory vectors is a compile-time constant
-template <int NS, bool CONSTV = false, int BT = 0>
-__global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
-  constexpr int n = NS + 1;
-  extern __shared__ double smem[];
-  const int tid = threadIdx.x;
-  const int stride = BT > 0 ? BT : blockDim.x;
-  const double* blob = a.blob;
-  double2* etab = reinterpret_cast<double2*>(smem);
-  for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
-  int boff = 128;
-  if (a.stage_blob) {
-    for (int i = tid; i < a.d.total; i += stride) smem[boff + i] = a.blob[i];
-    blob = smem + boff;
-    boff += blob_smem_doubles(a.d);
-  }
-  __syncthreads();
-  const MechView mv = make_view(blob, a.d, etab);
-  double* ws = smem + boff + tid;
-  typedef SVT<double, BT> V;
-  V C{ws, stride};
-  V wdot{ws + NS * stride, stride};
-  V gRT{ws + 2 * NS * stride, stride};
-  V hRT{ws + 3 * NS * stride, stride};
-  V cpR{ws + 4 * NS * stride, stride};
-  V Jv{ws + 5 * NS * stride, stride};
-  V Kv{ws + (5 * NS + n * n) * stride, stride};
-  const RosTab& tb = c_tab[a.method];
-  const int lane = tid & 31;
-  const unsigned long long nwork = a.nwork_dev ? *a.nwork_dev : (unsigned long long)a.nwork;
-
-  int64_t cell = -1;
-  bool exhausted = false, done = false, last_rej = false;
-  int status = 0, nacc = 0, nrej = 0, istep = 0;
-  double y[n];
-  double t = 0.0, h = 0.0, fbest = -INFINITY, tbest = 0.0;
-  double prm = 0.0;  // pressure [dyn/cm^2], or the fixed density [g/cm^3] at constant volume
-  StepState ss{0.0, 1.0};
-  unsigned long long tot_acc = 0, tot_rej = 0;
-
-  for (;;) {
-    // finished cell: store
-    if (cell >= 0 && done) {
-      if (status == DF_CELL_OK) {
-        a.T[cell] = y[0];
-#pragma unroll
-        for (int k = 0; k < NS; ++k) a.Y[(int64_t)k * a.ncells + cell] = y[1 + k];
-      }
-      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? tbest : NAN;
-      a.status[cell] = status;
-      if (a.nsub) a.nsub[cell] = nacc;
-      tot_acc += nacc;
-      tot_rej += nrej;
-      cell = -1;
-    }
-    // lane refill from the device work counter
-    const bool want = (cell < 0) && !exhausted;
-    const unsigned m = __ballot_sync(FULL, want);
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(&a.counters[0], (unsigned long long)__popc(m));
-      base = __shfl_sync(FULL, base, leader);
-      if (want) {
-        const unsigned long long idx = base + __popc(m & ((1u << lane) - 1u));
-        if (idx < nwork) {
-          cell = a.order ? (int64_t)a.order[idx] : (int64_t)idx;
-          y[0] = a.T[cell];
-          bool ok = isfinite(y[0]) && y[0] > 0.0;
-#pragma unroll
-          for (int k = 0; k < NS; ++k) {
-            y[1 + k] = a.Y[(int64_t)k * a.ncells + cell];
-            ok = ok && isfinite(y[1 + k]);
-          }
-          const double pc = a.p[cell];
-          ok = ok && isfinite(pc) && pc > 0.0;
-          prm = 10.0 * pc;  // Pa -> dyn/cm^2
-          if (CONSTV) {  // density of the initial state, fixed from here on
-            double sYW = 0.0;
-#pragma unroll
-            for (int k = 0; k < NS; ++k) sYW += y[1 + k] * mv.sp[SP_REC * k + 1];
-            prm = prm / (RU * y[0] * sYW);
-            ok = ok && isfinite(prm) && prm > 0.0;
-          }
-          t = 0.0;
-          h = fmin(a.h0, a.dt);
-          nacc = nrej = istep = 0;
-          fbest = -INFINITY;
-          tbest = 0.0;
-          last_rej = false;
-          status = ok ? DF_CELL_OK : DF_CELL_NONFINITE;
-          done = !ok || !(a.dt > 0.0);
-        } else {
-          exhausted = true;
-        }
-      }
-    }
-    if (__ballot_sync(FULL, cell >= 0 || !exhausted) == 0) break;
-    if (cell < 0 || done) continue;
-
-    // ---- one substep attempt ------------------------------------------------
-    const double pc = prm;
-    bool last = false;
-    if (t + h >= a.dt) {
-      h = a.dt - t;
-      last = true;
-    }
-    double ys[n];
-    double en;
-    double fT;
-    const double t0 = t;
-    const bool ok = ros_attempt<NS, CONSTV, BT>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wdot, gRT, hRT,
-                                                cpR, Jv, Kv, stride, ys, en, nullptr, nacc == 0 && nrej == 0, &last,
-                                                &fT);
-    const int nacc0 = nacc;
-    step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
-    if (nacc > nacc0 && fT > fbest) {  // dT/dt at the start of an accepted substep
-      fbest = fT;
-      tbest = istep * a.dt + t0;
-    }
-    if (done && ++istep < a.nsteps) {  // next consecutive step of dt
-      done = false;
-      t = 0.0;
-    }
-    if (!done) {
-      if (nacc + nrej >= a.max_sub) {
-        status = DF_CELL_MAXSTEPS;
-        done = true;
-      } else if (h < a.hmin) {
-        status = DF_CELL_HMIN;
-        done = true;
-      }
-    }
-  }
-  // statistics: one atomic per warp
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    tot_acc += __shfl_down_sync(FULL, tot_acc, o);
-    tot_rej += __shfl_down_sync(FULL, tot_rej, o);
-  }
-  if (lane == 0) {
-    atomicAdd(&a.counters[1], tot_acc);
-    atomicAdd(&a.counters[2], tot_rej);
-  }
-}
 
 // ----------------------------------------------------------------------------
 // diagnostics: f and J per cell (one thread per cell)
@@ -573,7 +395,14 @@ int eval_dispatch(const df_mech* m, int64_t ncells, const double* T, const doubl
 }
 
 template <int NS>
-int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, int bps, bool constv) {
+int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, int bps, bool constv,
+                       bool jit) {
+  m->jit_used = 0;
+  if (jit && !constv) {  // the kernel generated for this mechanism, if it can run
+    bool launched = false;
+    const int rc = jit_thread_launch(m, threads, bps, a0, st, &launched);
+    if (rc || launched) return rc;
+  }
   IntegArgs a = a0;
   a.stage_blob = 1;
   size_t sm = thread_smem_bytes<NS>(m->dims, threads, true);
@@ -782,7 +611,7 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   switch (m->dims.N) {
 #define X(NS) \
   case NS:    \
-    return integrate_dispatch<NS>(m, a, st, threads, bps, o.reactor == 1);
+    return integrate_dispatch<NS>(m, a, st, threads, bps, o.reactor == 1, o.jit == 0);
     DF_THREAD_NS_LIST(X)
 #undef X
     default:

@@ -23,6 +23,7 @@ struct RosTab {
   int newf[6];
 };
 
+#ifndef __CUDACC_RTC__  // host-side table builders
 static RosTab make_rodas4() {
   RosTab t;
   memset(&t, 0, sizeof(t));
@@ -84,6 +85,7 @@ static RosTab make_rodas3() {
   t.newf[3] = 1;
   return t;
 }
+#endif
 
 
 // One Rosenbrock attempt from y over h: K stages in Kv (strided, s x n), the
@@ -106,7 +108,21 @@ __device__ __forceinline__ double first_step_limit(const double (&y)[n], const d
 
 // pc: the reactor's fixed state parameter, pressure [dyn/cm^2] (CONSTV false)
 // or density [g/cm^3] (CONSTV true; see eval_thread)
-template <int NS, bool CONSTV = false, int ST = 0>
+// Evaluation of f (and J) for ros_attempt: the mechanism-independent kernels
+// read the mechanism from its blob (eval_thread); a kernel generated for one
+// mechanism supplies its own policy with the same interface.
+struct BlobEval {
+  static constexpr bool kSpeciesVectors = true;  // uses the per-thread C, wdot, g, h, cp vectors
+  template <int NS, bool WITH_J, bool CONSTV, int ST>
+  __device__ __forceinline__ static double run(const MechView& mv, double pc, const double (&y)[NS + 1],
+                                               double (&f)[NS + 1], SVT<double, ST> C, SVT<double, ST> wdot,
+                                               SVT<double, ST> gRT, SVT<double, ST> hRT, SVT<double, ST> cpR,
+                                               SVT<double, ST> Jv) {
+    return eval_thread<NS, WITH_J, double, CONSTV, ST>(mv, pc, y, f, C, wdot, gRT, hRT, cpR, Jv);
+  }
+};
+
+template <int NS, bool CONSTV = false, int ST = 0, class EVAL = BlobEval>
 __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb, double pc, const double (&y)[NS + 1],
                                             double& h, double rtol, double atolY, double atolT, SVT<double, ST> C,
                                             SVT<double, ST> wdot, SVT<double, ST> gRT, SVT<double, ST> hRT,
@@ -115,7 +131,7 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
                                             bool first = false, bool* last = nullptr, double* fT = nullptr) {
   constexpr int n = NS + 1;
   double fs[n];
-  eval_thread<NS, true, double, CONSTV, ST>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
+  EVAL::template run<NS, true, CONSTV, ST>(mv, pc, y, fs, C, wdot, gRT, hRT, cpR, Jv);
   if (fT) *fT = fs[0];
   if (first) {
     const double hl = first_step_limit<n>(y, fs);
@@ -142,7 +158,7 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
         for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
         ynew[i] = acc;
       }
-      eval_thread<NS, false, double, CONSTV, ST>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
+      EVAL::template run<NS, false, CONSTV, ST>(mv, pc, ynew, fs, C, wdot, gRT, hRT, cpR, Jv);
     }
     // stage right-hand side, solved in place in the K slot of this stage
     SVT<double, ST> Ks{&Kv[s * n], stride};

@@ -1,0 +1,120 @@
+"""The integrator kernel generated for a loaded mechanism (df_integ_opts.jit):
+it runs on the thread-per-cell path at constant pressure, agrees with the
+mechanism-independent kernel to rounding (the same operations in the same
+order; the two compilations may contract different multiply-adds, which can
+move a step-size decision that sits on the error threshold), follows
+df_mech_set_lnA (the rate parameters stay in the blob), and agrees with the
+oracle.  With jit = 1, and for the constant-volume reactor, the
+mechanism-independent kernel runs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2210_07094_gb300 as df  # noqa: E402
+from oracle.oracle import Mech  # noqa: E402
+from paper_2210_07094_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _dev(f):
+    return (torch.tensor(f["T"], device=DEV), torch.tensor(f["p"], device=DEV),
+            torch.tensor(np.ascontiguousarray(f["Y"]), device=DEV))
+
+
+def _run(m, T0, p, Y0, dt, bt, jit, reactor=0):
+    o = df.default_opts()
+    o.block_threads, o.blocks_per_sm, o.path, o.jit, o.reactor = bt, 0, 1, jit, reactor
+    T, Y = T0.clone(), Y0.clone()
+    st, ns = df.integrate(m, T, p, Y, dt, o)
+    used, detail = m.jit_info()
+    return (T, Y, st, ns), used, detail
+
+
+def _close(a, b):
+    """Same statuses; T within 1e-6 K and Y within 1e-9 of the cell's largest
+    mass fraction (the integrator's own error against the oracle is ~1e-7 K);
+    at most 1% of the cells with another number of substeps."""
+    (T1, Y1, s1, n1), (T2, Y2, s2, n2) = a, b
+    assert torch.equal(s1, s2)
+    dT = (T1 - T2).abs().max().item()
+    dY = ((Y1 - Y2).abs() / Y1.abs().amax(dim=0)).max().item()
+    moved = (n1 != n2).float().mean().item()
+    assert dT <= 1e-6 and dY <= 1e-9 and moved <= 0.01, (dT, dY, moved)
+    return dT, dY, moved
+
+
+@pytest.fixture(scope="module")
+def h2():
+    mech = synth.h2_air_mechanism()
+    return mech, df.Mechanism(mech)
+
+
+def test_generated_kernel_runs_and_matches_the_generic_kernel(h2):
+    mech, m = h2
+    f = synth.field(1, mech, 12000, seed=77)
+    T0, p, Y0 = _dev(f)
+    ref, used, _ = _run(m, T0, p, Y0, f["dt"], 32, 1)
+    assert not used and int(ref[2].abs().sum()) == 0
+    for bt in (32, 64):
+        out, used, detail = _run(m, T0, p, Y0, f["dt"], bt, 0)
+        assert used, detail
+        assert "compiled" in detail
+        print("generated vs mechanism-independent", bt, _close(ref, out))
+    # block sizes without a generated kernel run the mechanism-independent one
+    out, used, _ = _run(m, T0, p, Y0, f["dt"], 128, 0)
+    assert not used and all(torch.equal(x, y) for x, y in zip(ref, out))
+
+
+def test_generated_kernel_follows_set_lnA(h2):
+    mech, m = h2
+    f = synth.field(0, mech, 3000, seed=78)
+    T0, p, Y0 = _dev(f)
+    rng = np.random.default_rng(3)
+    lnA0 = np.log([r["A"] for r in mech["reactions"]])
+    lnA = torch.tensor(lnA0 + rng.uniform(-0.5, 0.5, lnA0.size), device=DEV)
+    m.set_lnA(lnA)
+    try:
+        ref, _, _ = _run(m, T0, p, Y0, f["dt"], 64, 1)
+        out, used, detail = _run(m, T0, p, Y0, f["dt"], 64, 0)
+        assert used, detail
+        _close(ref, out)
+    finally:
+        m.set_lnA(None)
+    base, used, _ = _run(m, T0, p, Y0, f["dt"], 64, 0)
+    assert used and not torch.equal(base[0], out[0])
+
+
+def test_generated_kernel_matches_the_oracle(h2):
+    mech, m = h2
+    o = Mech(mech)
+    f = synth.field(0, mech, 600, seed=79)
+    T0, p, Y0 = _dev(f)
+    (T, Y, st, _), used, detail = _run(m, T0, p, Y0, f["dt"], 32, 0)
+    assert used, detail
+    assert int(st.abs().sum()) == 0
+    To, Yo, so, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"])
+    assert np.all(so == 0)
+    assert np.abs(T.cpu().numpy() - To).max() <= 1e-3
+    assert (np.abs(Y.cpu().numpy() - Yo) / Yo.max(axis=0)).max() <= 1e-7
+
+
+def test_three_species_mechanism_and_constant_volume():
+    mech = synth.isomer_mechanism()
+    m = df.Mechanism(mech)
+    n = 700
+    T0 = torch.full((n,), 1100.0, dtype=torch.float64, device=DEV)
+    p = torch.full((n,), 101325.0, dtype=torch.float64, device=DEV)
+    Y0 = torch.zeros((m.n_species, n), dtype=torch.float64, device=DEV)
+    Y0[0] = torch.linspace(0.1, 0.9, n, dtype=torch.float64, device=DEV)
+    Y0[1] = 0.05
+    Y0[2] = 1.0 - Y0[0] - Y0[1]
+    ref, used, _ = _run(m, T0, p, Y0, 1e-5, 64, 1)
+    out, used, detail = _run(m, T0, p, Y0, 1e-5, 64, 0)
+    assert used, detail
+    _close(ref, out)
+    # the constant-volume reactor has no generated kernel
+    _, used, _ = _run(m, T0, p, Y0, 1e-5, 64, 0, reactor=1)
+    assert not used
