@@ -33,12 +33,13 @@ METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
 UNIT = "cell-steps/s"
 # FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
 # 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
-# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.6911e10) of one timed
-# launch on the 2^20-cell field divided by the 2199716 attempts that launch
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.6612e10) of one timed
+# launch on the 2^20-cell field (the kernel generated for the mechanism, in the
+# autotuned 32-thread shape) divided by the 2199716 attempts that launch
 # counted (profiles/integrator_thread9_h2air_bimodal.md).
-FLOP_PER_SUBSTEP = 21326
+FLOP_PER_SUBSTEP = 21190
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 181079808 + 212591616
+TRAFFIC_PER_LAUNCH = 234065920 + 237065472
 
 
 def _rank_info():
@@ -317,7 +318,8 @@ def profile_case(args):
     DFMA chains per thread (FP64 dependent latency against throughput).
     h2: two thread-per-cell integrator launches (warm-up, measured) on 2^18
     cells of the bimodal 9-species field, in the launch shape the autotuner
-    picks for the full field (64 threads x 2 blocks per SM, hottest first)."""
+    picks for the full field (32-thread blocks, as many per SM as fit, hottest
+    first; the kernel generated for the mechanism)."""
     import ctypes as C
     import torch
     from paper_2210_07094_gb300 import _lib
@@ -352,7 +354,7 @@ def profile_case(args):
         f = synth.field(1, mech, 1 << 18)
         T0, p, Y0 = (torch.tensor(f[k], device="cuda") for k in ("T", "p", "Y"))
         o = df.default_opts()
-        o.block_threads, o.blocks_per_sm, o.order_by_T, o.path = 64, 2, 1, 1
+        o.block_threads, o.blocks_per_sm, o.order_by_T, o.path = 32, 0, 1, 1
         for rep in range(2):
             T, Y = T0.clone(), Y0.clone()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -580,9 +582,9 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
                 "frac": achieved / (fp64_peak / 1e3),
                 "traffic": TRAFFIC_PER_LAUNCH if ncells == NCELLS else None,
-                "traffic_note": "ncu DRAM bytes of one 2^20-cell launch; 2.2x the 180 MB of cell state read "
+                "traffic_note": "ncu DRAM bytes of one 2^20-cell launch; 2.6x the 180 MB of cell state read "
                                 "and written, from 8-byte accesses in hottest-first cell order (32-byte sectors); "
-                                "0.07% of HBM bandwidth over the launch",
+                                "0.1% of HBM bandwidth over the launch",
                 "peak_source": "measured FP64 DFMA throughput (df_probe_fp64_peak), this GPU, this run",
                 "flop_per_substep": FLOP_PER_SUBSTEP}
     line = {

@@ -38,16 +38,30 @@ def test_autotune_choice_and_shape_independence():
     assert torch.equal(T0, Tc) and torch.equal(Y0, Yc)  # inputs untouched
     assert best.block_threads in (32, 64, 96, 128) and best.blocks_per_sm in (0, 1, 2)
     assert best.order_by_T in (0, 1) and best.path == 1 and ms > 0
-    ref = _run(m, T0, p, Y0, f["dt"], best)
-    assert int(ref[2].abs().sum()) == 0
-    # zero shape fields take the cached choice; explicit shapes (the 32/64/128-
-    # thread kernels with a compile-time stride, 96 with the run-time one) and
-    # both work orders give bitwise the same cells
-    assert _same(ref, _run(m, T0, p, Y0, f["dt"]))
+    tuned = _run(m, T0, p, Y0, f["dt"], best)
+    assert int(tuned[2].abs().sum()) == 0
+    # zero shape fields take the cached choice
+    assert _same(tuned, _run(m, T0, p, Y0, f["dt"]))
+    # the mechanism-independent kernel: explicit shapes (32/64/128 threads with a
+    # compile-time stride, 96 with the run-time one) and both work orders give
+    # bitwise the same cells
+    gen = df.default_opts()
+    gen.block_threads, gen.blocks_per_sm, gen.order_by_T, gen.jit = best.block_threads, best.blocks_per_sm, 1, 1
+    ref = _run(m, T0, p, Y0, f["dt"], gen)
     for bt, bps, order in ((32, 1, 0), (64, 2, 1), (128, 0, 1), (96, 2, 0)):
         o = df.default_opts()
-        o.block_threads, o.blocks_per_sm, o.order_by_T = bt, bps, order
+        o.block_threads, o.blocks_per_sm, o.order_by_T, o.jit = bt, bps, order, 1
         assert _same(ref, _run(m, T0, p, Y0, f["dt"], o)), (bt, bps, order)
+    # the kernel generated for the mechanism (the default at 32 and 64 threads)
+    # agrees with it to rounding, in either work order
+    for bt, order in ((32, 0), (64, 1)):
+        o = df.default_opts()
+        o.block_threads, o.blocks_per_sm, o.order_by_T = bt, 0, order
+        T, Y, st, ns = _run(m, T0, p, Y0, f["dt"], o)
+        assert torch.equal(st, ref[2])
+        assert (T - ref[0]).abs().max().item() <= 1e-6
+        assert ((Y - ref[1]).abs() / ref[1].abs().amax(dim=0)).max().item() <= 1e-9
+        assert (ns != ref[3]).float().mean().item() <= 0.01
 
 
 def test_autotune_warp_path():
