@@ -56,9 +56,28 @@ RxSlots slots_of(const df_mech* m, int j) {
   return sl;
 }
 
+// exact decimal-free spelling of a double (C++17 hexadecimal literal)
+std::string lit(double v) {
+  char b[64];
+  snprintf(b, sizeof b, "%a", v);
+  return std::string("(") + b + ")";
+}
+
+// Horner form c[0] + x (c[1] + x (c[2] + ...)) with the trailing coefficients
+// that are exactly zero dropped (for finite x they add exactly zero)
+std::string horner(const std::vector<double>& c, const char* x) {
+  int top = (int)c.size() - 1;
+  while (top > 0 && c[top] == 0.0) --top;
+  std::string e = lit(c[top]);
+  for (int i = top - 1; i >= 0; --i) e = lit(c[i]) + " + " + x + " * (" + e + ")";
+  return e;
+}
+
 // f and J of the loaded mechanism as straight-line code: the mechanism-
 // independent eval_thread (chem_thread.cuh) at constant pressure with every
-// reaction's indices and type resolved, in the same order of operations
+// reaction's indices and type resolved and the mechanism's numbers as literals
+// (except ln A, read from the blob so that df_mech_set_lnA applies, and the
+// Troe parameters), in the same order of operations
 void emit_eval(std::ostringstream& o, const df_mech* m) {
   const int N = m->dims.N, n = N + 1, M = m->dims.M;
   o << "template <bool WITH_J, int ST>\n"
@@ -67,25 +86,31 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "  constexpr int NS = " << N << ";\n  constexpr int n = NS + 1;\n"
     << "  const double T = y[0];\n  const double lnT = fast_log(T);\n  const double invT = 1.0 / T;\n"
     << "  double C[NS], wdot[NS], gRT[NS], hRT[NS], cpR[NS];\n"
-    << "  double sumYW = 0.0, cpm = 0.0;\n"
-    << "#pragma unroll\n"
-    << "  for (int k = 0; k < NS; ++k) {\n"
-    << "    const double* a = mv.sp + SP_REC * k + 2;\n"
-    << "    const double* ah = mv.sp + SP_REC * k + SP_H;\n"
-    << "    const double* as = mv.sp + SP_REC * k + SP_S;\n"
-    << "    const double cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));\n"
-    << "    cpR[k] = cpk;\n"
-    << "    const double hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;\n"
-    << "    const double sk = a[0] * lnT + T * (a[1] + T * (as[0] + T * (as[1] + T * as[2]))) + a[6];\n"
-    << "    hRT[k] = hk;\n    gRT[k] = hk - sk;\n"
-    << "    sumYW += y[1 + k] * mv.sp[SP_REC * k + 1];\n"
-    << "    cpm += y[1 + k] * cpk * mv.sp[SP_REC * k + 1];\n"
-    << "  }\n"
-    << "  cpm = cpm * RU;\n"
+    << "  double sumYW = 0.0, cpm = 0.0;\n";
+  auto sp = [&](int k, int i) { return m->blob_host[m->dims.off_sp + SP_REC * k + i]; };
+  for (int k = 0; k < N; ++k) {
+    const std::vector<double> a = {sp(k, 2), sp(k, 3), sp(k, 4), sp(k, 5), sp(k, 6)};
+    const std::vector<double> ah = {sp(k, SP_H), sp(k, SP_H + 1), sp(k, SP_H + 2), sp(k, SP_H + 3)};
+    const std::vector<double> as = {sp(k, SP_S), sp(k, SP_S + 1), sp(k, SP_S + 2)};
+    std::vector<double> hs = {sp(k, 2)};
+    hs.insert(hs.end(), ah.begin(), ah.end());
+    std::vector<double> ss = {sp(k, 3)};
+    ss.insert(ss.end(), as.begin(), as.end());
+    o << "  {  // species " << k << "\n"
+      << "    const double cpk = " << horner(a, "T") << ";\n    cpR[" << k << "] = cpk;\n"
+      << "    const double hk = " << horner(hs, "T") << " + " << lit(sp(k, 7)) << " * invT;\n"
+      << "    const double sk = " << lit(sp(k, 2)) << " * lnT + T * (" << horner(ss, "T") << ") + " << lit(sp(k, 8))
+      << ";\n"
+      << "    hRT[" << k << "] = hk;\n    gRT[" << k << "] = hk - sk;\n"
+      << "    sumYW += y[" << 1 + k << "] * " << lit(sp(k, 1)) << ";\n"
+      << "    cpm += y[" << 1 + k << "] * cpk * " << lit(sp(k, 1)) << ";\n  }\n";
+  }
+  o << "  cpm = cpm * RU;\n"
     << "  const double rho = pc * invT / (RU * sumYW);\n"
-    << "  const double invrho = 1.0 / rho;\n  const double invcp = 1.0 / cpm;\n"
-    << "#pragma unroll\n"
-    << "  for (int k = 0; k < NS; ++k) {\n    C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];\n    wdot[k] = 0.0;\n  }\n"
+    << "  const double invrho = 1.0 / rho;\n  const double invcp = 1.0 / cpm;\n";
+  for (int k = 0; k < N; ++k)
+    o << "  C[" << k << "] = rho * y[" << 1 + k << "] * " << lit(sp(k, 1)) << ";\n  wdot[" << k << "] = 0.0;\n";
+  o
     << "  if (WITH_J) {\n#pragma unroll\n    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;\n  }\n"
     << "  const double lnP0RT = LOG_PSTD_RU - lnT;\n";
   for (int j = 0; j < M; ++j) {
@@ -96,7 +121,8 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     const int p[3] = {mt.prod[0], mt.prod[1], mt.prod[2]};
     o << "  {  // reaction " << j << "\n"
       << "    RxIn<double> g;\n    const double* r = mv.rx + RX_REC * " << j << ";\n"
-      << "    g.lnA = r[0];\n    g.beta = r[1];\n    g.EaR = r[2];\n";
+      << "    g.lnA = r[0];\n    g.beta = " << lit(m->blob_host[m->dims.off_rx + RX_REC * j + 1])
+      << ";\n    g.EaR = " << lit(m->blob_host[m->dims.off_rx + RX_REC * j + 2]) << ";\n";
     for (int i = 0; i < 3; ++i) o << "    g.mt.reac[" << i << "] = " << r[i] << ";\n";
     for (int i = 0; i < 3; ++i) o << "    g.mt.prod[" << i << "] = " << p[i] << ";\n";
     o << "    g.mt.nrnp = " << (int)mt.nrnp << ";\n    g.mt.flags = " << (int)mt.flags << ";\n"
@@ -111,9 +137,11 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     for (int i = 1; i < np; ++i) o << "    sg += gRT[" << p[i] << "];\n    if (WITH_J) sh += hRT[" << p[i] << "];\n";
     for (int i = 1; i < nr; ++i) o << "    sg -= gRT[" << r[i] << "];\n    if (WITH_J) sh -= hRT[" << r[i] << "];\n";
     o << "    g.sg = sg;\n    g.sh = sh;\n";
+    auto eff = [&](int l) { return m->blob_host[m->dims.off_eff + N * sl.eff + l]; };
     if (type != 0) {
-      o << "    {\n      const double* ef = mv.eff + NS * " << sl.eff << ";\n      double Mc = 0.0;\n"
-        << "#pragma unroll\n      for (int l = 0; l < NS; ++l) Mc += ef[l] * C[l];\n      g.Mc = Mc;\n    }\n";
+      o << "    {\n      double Mc = 0.0;\n";
+      for (int l = 0; l < N; ++l) o << "      Mc += " << lit(eff(l)) << " * C[" << l << "];\n";
+      o << "      g.Mc = Mc;\n    }\n";
     } else {
       o << "    g.Mc = 0.0;\n";
     }
@@ -136,16 +164,20 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
       o << "        Jv[" << row * n << "] += " << sg << "(ro.dqdT);\n";
       for (int i = 0; i < nr; ++i) o << "        Jv[" << row * n + 1 + r[i] << "] += " << sg << "(dr" << i << ");\n";
       for (int i = 0; i < np; ++i) o << "        Jv[" << row * n + 1 + p[i] << "] += " << sg << "(dp" << i << ");\n";
-      if (type != 0)
-        o << "        {\n          const double* ef = mv.eff + NS * " << sl.eff << ";\n          const double cM = " << sg
-          << "(ro.dqdM);\n#pragma unroll\n          for (int l = 0; l < NS; ++l) Jv[" << row * n + 1
-          << " + l] += cM * ef[l];\n        }\n";
+      if (type != 0) {
+        o << "        {\n          const double cM = " << sg << "(ro.dqdM);\n";
+        for (int l = 0; l < N; ++l)
+          o << "          Jv[" << row * n + 1 + l << "] += cM * " << lit(eff(l)) << ";\n";
+        o << "        }\n";
+      }
     }
     o << "      }\n    }\n  }\n";
   }
   o << "  double Hw = 0.0;\n#pragma unroll\n  for (int k = 0; k < NS; ++k) Hw += hRT[k] * wdot[k];\n"
     << "  Hw = Hw * (RU * T);\n"
-    << "#pragma unroll\n  for (int k = 0; k < NS; ++k) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;\n"
+    ;
+  for (int k = 0; k < N; ++k) o << "  f[" << 1 + k << "] = " << lit(sp(k, 0)) << " * wdot[" << k << "] * invrho;\n";
+  o
     << "  f[0] = -(Hw * invrho * invcp);\n"
     << "  if (WITH_J) {\n"
     << "    const double Wbar = 1.0 / sumYW;\n"
@@ -157,10 +189,13 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "#pragma unroll\n      for (int i = 0; i < NS; ++i) {\n        const double iWi = mv.sp[SP_REC * i + 1];\n"
     << "        Jv[row + 1 + i] = (Wk * Jv[row + 1 + i] + a) * iWi;\n      }\n"
     << "      Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);\n    }\n"
-    << "    double dcp = 0.0, cpf = 0.0;\n#pragma unroll\n    for (int k = 0; k < NS; ++k) {\n"
-    << "      const double* a = mv.sp + SP_REC * k + 2;\n      const double iW = mv.sp[SP_REC * k + 1];\n"
-    << "      dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;\n"
-    << "      cpf += cpR[k] * iW * f[1 + k];\n    }\n"
+    << "    double dcp = 0.0, cpf = 0.0;\n";
+  for (int k = 0; k < N; ++k) {
+    const std::vector<double> d = {sp(k, 3), 2.0 * sp(k, 4), 3.0 * sp(k, 5), 4.0 * sp(k, 6)};
+    o << "    dcp += y[" << 1 + k << "] * (" << horner(d, "T") << ") * " << lit(sp(k, 1)) << ";\n"
+      << "    cpf += cpR[" << k << "] * " << lit(sp(k, 1)) << " * f[" << 1 + k << "];\n";
+  }
+  o
     << "    dcp = dcp * RU;\n    cpf = cpf * RU;\n"
     << "#pragma unroll 1\n    for (int jc = 0; jc < n; ++jc) {\n      double acc = 0.0;\n"
     << "#pragma unroll\n      for (int k = 0; k < NS; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];\n"
