@@ -75,8 +75,13 @@ typedef struct df_integ_opts {
   int32_t order_by_T;     /* 1 (default): hand out cells hottest first (a device
                              counting sort; longest work first, lanes refilled
                              together get cells of similar stiffness)          */
-  int32_t path;           /* 0: auto (thread per cell if N <= 16), 1: thread per
-                             cell, 2: warp per cell                            */
+  int32_t path;           /* 0: auto -- the path df_chem_autotune chose, else
+                             thread per cell where a thread kernel exists (the
+                             built species counts 3 and 9; with jit = 0 at
+                             constant pressure the generated kernel for any
+                             N <= 16, the warp path if it cannot be compiled),
+                             else warp per cell; 1: thread per cell (error if
+                             no thread kernel can run), 2: warp per cell       */
   int32_t reactor;        /* 0 (default): constant pressure, p[c] fixed and h
                              conserved; 1: constant volume (Sec. 2.2), the
                              density fixed from the initial p[c], T, Y and the

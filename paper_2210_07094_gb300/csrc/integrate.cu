@@ -596,17 +596,36 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   a.nwork = nwork;
   a.nwork_dev = nwork_dev;
   a.counters = m->counters;
+  // thread-per-cell kernels: built for the species counts of
+  // DF_THREAD_NS_LIST; for any other N <= 16 only the kernel generated for the
+  // mechanism (constant pressure, jit on)
   const bool thread_ok = has_thread_kernel(m->dims.N);
-  if (o.path == 1 && !thread_ok)
-    return set_error(DF_EUNSUPPORTED, "no thread-per-cell kernel built for this species count");
-  const bool warp_path = o.path == 2 || !thread_ok;
-  // zero shape fields: the shape df_chem_autotune chose for this path, if any
-  int bt = o.block_threads, bps = o.blocks_per_sm;
-  if (bt == 0 && bps == 0 && m->tuned_threads > 0 && m->tuned_path == (warp_path ? 2 : 1)) {
+  const bool gen_only = !thread_ok && o.jit == 0 && o.reactor == 0 && m->dims.N <= THREAD_PATH_MAX_N;
+  if (o.path == 1 && !thread_ok && !gen_only)
+    return set_error(DF_EUNSUPPORTED, "no thread-per-cell kernel for this species count and options");
+  // zero shape fields: the path and shape df_chem_autotune chose, if any
+  int bt = o.block_threads, bps = o.blocks_per_sm, path = o.path;
+  const bool tuned = bt == 0 && bps == 0 && m->tuned_threads > 0;
+  if (tuned && path == 0) path = m->tuned_path;
+  const bool warp_path = path == 2 || (!thread_ok && !gen_only);
+  if (tuned && m->tuned_path == (warp_path ? 2 : 1)) {
     bt = m->tuned_threads;
     bps = m->tuned_bps;
   }
-  if (warp_path) return integrate_warp_dispatch(m, a, st, bt, o.reactor == 1);
+  if (warp_path) {
+    m->jit_used = 0;
+    return integrate_warp_dispatch(m, a, st, bt, o.reactor == 1);
+  }
+  if (!thread_ok) {  // the generated kernel only (32- or 64-thread blocks)
+    bool launched = false;
+    m->jit_used = 0;
+    const int rc = jit_thread_launch(m, bt == 64 ? 64 : 32, bps, a, st, &launched);
+    if (rc || launched) return rc;
+    if (o.path == 1)
+      return set_error(DF_EUNSUPPORTED, "thread-per-cell path: the generated kernel is unavailable (" +
+                                            m->jit_note + ")");
+    return integrate_warp_dispatch(m, a, st, 0, false);
+  }
   const int threads = bt > 0 ? bt : 64;
   switch (m->dims.N) {
 #define X(NS) \
@@ -650,6 +669,10 @@ int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double
                        cudaStream_t st) {
   const int N = m->dims.N;
   const int64_t n = std::min<int64_t>(ncells, sample > 0 ? sample : 65536);
+  // species counts without a compiled thread kernel: the generated thread
+  // kernel (if it can run) competes with the warp path
+  const bool gen_only = !has_thread_kernel(N) && base.jit == 0 && base.reactor == 0 && N <= THREAD_PATH_MAX_N &&
+                        base.path != 2;
   const bool warp_path = base.path == 2 || !has_thread_kernel(N);
   double *T0 = nullptr, *p0 = nullptr, *Y0 = nullptr, *Tw = nullptr, *Yw = nullptr;
   int32_t* stt = nullptr;
@@ -672,6 +695,17 @@ int autotune_integrate(df_mech* m, int64_t ncells, const double* T, const double
                     "copy Y");
   std::vector<df_integ_opts> cand;
   for (int order = 0; order <= 1; ++order) {
+    if (gen_only) {
+      for (int bt : {32, 64})
+        for (int bps : {0, 1, 2}) {
+          df_integ_opts o = base;
+          o.block_threads = bt;
+          o.blocks_per_sm = bps;
+          o.order_by_T = order;
+          o.path = 1;
+          cand.push_back(o);
+        }
+    }
     if (warp_path) {
       for (int bt : {64, 128, 256}) {
         df_integ_opts o = base;

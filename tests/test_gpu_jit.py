@@ -118,3 +118,43 @@ def test_three_species_mechanism_and_constant_volume():
     # the constant-volume reactor has no generated kernel
     _, used, _ = _run(m, T0, p, Y0, 1e-5, 64, 0, reactor=1)
     assert not used
+
+
+def test_thread_path_for_a_species_count_without_a_built_kernel():
+    """14 species (no compiled thread kernel): with jit the automatic path runs
+    the generated thread-per-cell kernel; it agrees with the warp path and the
+    oracle; with jit = 1 the automatic path is the warp path and an explicit
+    thread path is refused."""
+    mech = synth.hydrocarbon_mechanism(n_species=12, M=40, n_tb=4, n_troe=2)
+    m = df.Mechanism(mech)
+    assert m.n_species == 14
+    f = synth.field(2, mech, 300, seed=5)
+    T0, p, Y0 = _dev(f)
+    T, Y = T0.clone(), Y0.clone()
+    st, _ = df.integrate(m, T, p, Y, f["dt"])
+    used, detail = m.jit_info()
+    assert used, detail
+    assert int(st.abs().sum()) == 0
+    o = df.default_opts()
+    o.path = 2
+    Tw, Yw = T0.clone(), Y0.clone()
+    df.integrate(m, Tw, p, Yw, f["dt"], o)
+    assert torch.max(torch.abs(T - Tw)).item() <= 1e-6
+    assert torch.max(torch.abs(Y - Yw)).item() <= 1e-10
+    idx = np.arange(0, 300, 5)
+    To, Yo, so, _ = Mech(mech).integrate(f["T"][idx], f["p"][idx], f["Y"][:, idx], f["dt"])
+    assert np.all(so == 0)
+    assert np.abs(T.cpu().numpy()[idx] - To).max() <= 1e-3
+    assert (np.abs(Y.cpu().numpy()[:, idx] - Yo) / Yo.max(axis=0)).max() <= 1e-7
+    o = df.default_opts()
+    o.jit = 1
+    Tg, Yg = T0.clone(), Y0.clone()
+    df.integrate(m, Tg, p, Yg, f["dt"], o)
+    assert not m.jit_info()[0]
+    assert torch.equal(Tg, Tw) and torch.equal(Yg, Yw)
+    o.path = 1
+    with pytest.raises(df._lib.DFError):
+        df.integrate(m, T0.clone(), p, Y0.clone(), f["dt"], o)
+    # the autotuner weighs the generated thread kernel against the warp path
+    best, ms = m.autotune(T0, p, Y0, f["dt"])
+    assert best.path in (1, 2) and ms > 0
