@@ -33,13 +33,13 @@ METRIC = "cell-steps/s (9-species chemistry substep, FP64 integrator)"
 UNIT = "cell-steps/s"
 # FP64 operations per Rosenbrock substep attempt (accepted or rejected) of the
 # 9-species / 25-reaction mechanism on the thread-per-cell path: ncu's executed
-# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.6612e10) of one timed
+# DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.3845e10) of one timed
 # launch on the 2^20-cell field (the kernel generated for the mechanism, in the
 # autotuned 32-thread shape) divided by the 2199716 attempts that launch
 # counted (profiles/integrator_thread9_h2air_bimodal.md).
-FLOP_PER_SUBSTEP = 21190
+FLOP_PER_SUBSTEP = 19932
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 234065920 + 237065472
+TRAFFIC_PER_LAUNCH = 232478208 + 236807424
 
 
 def _rank_info():

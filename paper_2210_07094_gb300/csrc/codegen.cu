@@ -76,8 +76,8 @@ std::string horner(const std::vector<double>& c, const char* x) {
 // f and J of the loaded mechanism as straight-line code: the mechanism-
 // independent eval_thread (chem_thread.cuh) at constant pressure with every
 // reaction's indices and type resolved and the mechanism's numbers as literals
-// (except ln A, read from the blob so that df_mech_set_lnA applies, and the
-// Troe parameters), in the same order of operations
+// (except ln A, read from the blob so that df_mech_set_lnA applies), in the
+// same order of operations
 void emit_eval(std::ostringstream& o, const df_mech* m) {
   const int N = m->dims.N, n = N + 1, M = m->dims.M;
   o << "template <bool WITH_J, int ST>\n"
@@ -145,7 +145,16 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     } else {
       o << "    g.Mc = 0.0;\n";
     }
-    o << "    RateOutT<double> ro;\n    rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, ro);\n"
+    if (type == 2) {  // the falloff parameters as literals too (a one-record table)
+      const double* tr = &m->blob_host[m->dims.off_tr + TR_REC * sl.troe];
+      o << "    const double trp[" << TR_REC << "] = {";
+      for (int i = 0; i < TR_REC; ++i) o << (i ? ", " : "") << lit(tr[i]);
+      o << "};\n    MechView mvt = mv;\n    mvt.tr = trp;\n    g.sl.troe = 0;\n"
+        << "    RateOutT<double> ro;\n    rate_compute<NS, WITH_J>(mvt, g, T, lnT, invT, lnP0RT, ro);\n";
+    } else {
+      o << "    RateOutT<double> ro;\n    rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, ro);\n";
+    }
+    o
       << "    if (ro.active) {\n      const double q = ro.q;\n";
     for (int i = 0; i < nr; ++i) o << "      wdot[" << r[i] << "] -= q;\n";
     for (int i = 0; i < np; ++i) o << "      wdot[" << p[i] << "] += q;\n";
