@@ -68,7 +68,7 @@ typedef struct df_integ_opts {
   int32_t max_substeps; /* accepted + rejected substeps allowed per cell       */
   int32_t method;       /* 0: RODAS4 (Hairer & Wanner), 1: RODAS3 (Sandu 1997) */
   int32_t block_threads;  /* 0 (with blocks_per_sm 0): the shape df_chem_autotune
-                             chose for this mechanism and path, else 64; >0:
+                             chose for this mechanism and path, else 32; >0:
                              threads per block (a multiple of 32)             */
   int32_t blocks_per_sm;  /* 0: as many resident blocks as fit (or the tuned
                              value, see block_threads); >0: at most this many */

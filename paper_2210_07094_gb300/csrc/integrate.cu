@@ -626,7 +626,9 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
                                             m->jit_note + ")");
     return integrate_warp_dispatch(m, a, st, 0, false);
   }
-  const int threads = bt > 0 ? bt : 64;
+  // default block: 32 threads (5 warps per SM for the generated kernel; the
+  // mechanism-independent kernel runs as fast at 32 as at 64)
+  const int threads = bt > 0 ? bt : 32;
   switch (m->dims.N) {
 #define X(NS) \
   case NS:    \
