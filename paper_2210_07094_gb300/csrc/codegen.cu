@@ -461,17 +461,18 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
 int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cudaStream_t st, bool* launched) {
   *launched = false;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return DF_OK;
-  const std::string src = jit_thread_source(m);
-  Module* md = nullptr;
-  {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DF_OK;
+  Module* md = static_cast<Module*>(m->jit_module[dev]);
+  if (!md) {  // first launch on this device: generate, and compile unless cached
+    const std::string src = jit_thread_source(m);
     std::lock_guard<std::mutex> lock(g_mu);
     auto key = std::make_pair(dev, src);
     auto it = g_modules.find(key);
     if (it == g_modules.end()) it = g_modules.emplace(key, build_module(dev, m, src)).first;
     md = &it->second;
+    m->jit_module[dev] = md;
+    m->jit_note = md->ok ? "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms" : md->why;
   }
-  m->jit_note = md->ok ? "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms" : md->why;
   if (!md->ok) return DF_OK;
   auto f = md->fn.find(threads);
   if (f == md->fn.end()) return DF_OK;  // no generated kernel for this block size

@@ -40,6 +40,9 @@ struct df_mech {
   // launch used it, and its state (compile time, or why it is unavailable)
   int jit_used = 0;
   std::string jit_note;
+  // the module compiled for this mechanism on each device (owned by the
+  // process-wide cache in codegen.cu; null until the first launch)
+  void* jit_module[64] = {nullptr};
 };
 
 namespace df {
