@@ -299,10 +299,12 @@ typedef CUresult (*cuLaunchKernel_t)(CUfunction, unsigned, unsigned, unsigned, u
                                      unsigned, CUstream, void**, void**);
 typedef CUresult (*cuFuncSetAttribute_t)(CUfunction, CUfunction_attribute, int);
 typedef CUresult (*cuOccupancy_t)(int*, CUfunction, int, size_t);
+typedef CUresult (*cuModuleUnload_t)(CUmodule);
 
 struct Driver {
   bool ok = false;
   cuModuleLoadData_t load = nullptr;
+  cuModuleUnload_t unload = nullptr;
   cuModuleGetFunction_t get_function = nullptr;
   cuModuleGetGlobal_t get_global = nullptr;
   cuLaunchKernel_t launch = nullptr;
@@ -324,12 +326,13 @@ const Driver& driver() {
   static std::once_flag once;
   std::call_once(once, [] {
     d.load = (cuModuleLoadData_t)entry("cuModuleLoadData");
+    d.unload = (cuModuleUnload_t)entry("cuModuleUnload");
     d.get_function = (cuModuleGetFunction_t)entry("cuModuleGetFunction");
     d.get_global = (cuModuleGetGlobal_t)entry("cuModuleGetGlobal");
     d.launch = (cuLaunchKernel_t)entry("cuLaunchKernel");
     d.set_attr = (cuFuncSetAttribute_t)entry("cuFuncSetAttribute");
     d.occupancy = (cuOccupancy_t)entry("cuOccupancyMaxActiveBlocksPerMultiprocessor");
-    d.ok = d.load && d.get_function && d.get_global && d.launch && d.set_attr && d.occupancy;
+    d.ok = d.load && d.unload && d.get_function && d.get_global && d.launch && d.set_attr && d.occupancy;
   });
   return d;
 }
@@ -430,12 +433,15 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
   nv.destroy(&prog);
   if (drv.load(&r.mod, cubin.data()) != CUDA_SUCCESS) {
     r.why = "cuModuleLoadData failed";
+    r.mod = nullptr;
     return r;
   }
   for (size_t i = 0; i < sizeof(kThreads) / sizeof(kThreads[0]); ++i) {
     CUfunction f = nullptr;
     if (lowered[i].empty() || drv.get_function(&f, r.mod, lowered[i].c_str()) != CUDA_SUCCESS) {
       r.why = "generated kernel not found in the module";
+      drv.unload(r.mod);
+      r.mod = nullptr;
       return r;
     }
     r.fn[kThreads[i]] = f;
@@ -445,11 +451,15 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
   if (lowered.back().empty() || drv.get_global(&tab, &tab_bytes, r.mod, lowered.back().c_str()) != CUDA_SUCCESS ||
       tab_bytes != 2 * sizeof(RosTab)) {
     r.why = "Rosenbrock table not found in the module";
+    drv.unload(r.mod);
+    r.mod = nullptr;
     return r;
   }
   RosTab t[2] = {make_rodas4(), make_rodas3()};
   if (cudaMemcpy((void*)tab, t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) {
     r.why = "upload of the Rosenbrock tables failed";
+    drv.unload(r.mod);
+    r.mod = nullptr;
     return r;
   }
   r.ok = true;
