@@ -1,11 +1,13 @@
 """The mechanism-specific integrator source (df_mech_generated_source) on the
 host: one straight-line block per reaction with the mechanism's species
-indices, and a source that NVRTC compiles for sm_103a with the library's
-device headers (skipped when the NVRTC library is absent)."""
+indices, the mechanism's numbers as its literals, and a source that NVRTC
+compiles for sm_103a with the library's device headers (skipped when the
+NVRTC library is absent)."""
 import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2210_07094_gb300 import _lib, synth
@@ -76,3 +78,54 @@ def test_generated_source_compiles_with_nvrtc(tmp_path):
         low = C.c_char_p()
         assert nv.nvrtcGetLoweredName(prog, nm, C.byref(low)) == 0 and low.value
     nv.nvrtcDestroyProgram(C.byref(prog))
+
+
+_HEX = re.compile(r"\((-?0x[0-9a-fA-F.]+p[+-]?\d+)\)")
+
+
+def _lits(line):
+    return [float.fromhex(x) for x in _HEX.findall(line)]
+
+
+def test_generated_literals_are_the_mechanism_numbers(tmp_path):
+    """The numbers the generator writes as literals are the mechanism's:
+    NASA-7 coefficients (cp/R, h/RT and s/R polynomials, exactly-zero terms
+    dropped), 1/W, W, beta, Ea/R, third-body efficiencies and Troe records."""
+    mech = synth.h2_air_mechanism()
+    src = _source(mech, tmp_path)
+    R = 8.314462618
+    for k, sp in enumerate(mech["species"]):
+        a = sp["nasa7"]
+        blk = src.split(f"// species {k}\n")[1].split("}")[0]
+        cp = _lits([ln for ln in blk.splitlines() if "cpk =" in ln][0])
+        top = max(i for i in range(5) if a[i] != 0.0 or i == 0)
+        assert cp == a[: top + 1]
+        h = _lits([ln for ln in blk.splitlines() if "hk =" in ln][0])
+        hpoly = [a[0]] + [a[i] / (i + 1) for i in range(1, 5)]
+        htop = max(i for i in range(5) if hpoly[i] != 0.0 or i == 0)
+        assert h == pytest.approx(hpoly[: htop + 1] + [a[5]], rel=1e-15)
+        s = _lits([ln for ln in blk.splitlines() if "sk =" in ln][0])
+        spoly = [a[1]] + [a[i] / i for i in range(2, 5)]
+        stop = max(i for i in range(4) if spoly[i] != 0.0 or i == 0)
+        assert s == pytest.approx([a[0]] + spoly[: stop + 1] + [a[6]], rel=1e-15)
+        iw = _lits([ln for ln in blk.splitlines() if "sumYW +=" in ln][0])
+        assert iw == [pytest.approx(1.0 / sp["W"], rel=1e-15)]
+        fl = [ln for ln in src.splitlines() if ln.strip().startswith(f"f[{1 + k}] =")][0]
+        assert _lits(fl) == [sp["W"]]
+    names = [s["name"] for s in mech["species"]]
+    for j, r in enumerate(mech["reactions"]):
+        blk = src.split(f"// reaction {j}\n")[1].split("// reaction")[0]
+        beta = _lits([ln for ln in blk.splitlines() if "g.beta =" in ln][0])
+        ear = _lits([ln for ln in blk.splitlines() if "g.EaR =" in ln][0])
+        assert beta == [r["b"]]
+        assert ear == [pytest.approx(r["Ea"] * 1e3 / R, rel=1e-15)]
+        if r["type"] != "elementary":
+            mc = [_lits(ln)[0] for ln in blk.splitlines() if "Mc +=" in ln]
+            eff = [r.get("efficiencies", {}).get(nm, 1.0) for nm in names]
+            assert mc == eff
+        if r["type"] == "falloff-troe":
+            trp = _lits([ln for ln in blk.splitlines() if "trp[" in ln][0])
+            lo, tr = r["low"], r["troe"]
+            expect = [np.log(lo["A"]) - np.log(r["A"]), lo["b"], lo["Ea"] * 1e3 / R, tr["alpha"],
+                      1.0 / tr["T3"], 1.0 / tr["T1"], tr["T2"], 0.0]
+            assert trp == pytest.approx(expect, rel=1e-14, abs=1e-300)
