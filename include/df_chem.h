@@ -97,8 +97,14 @@ typedef struct df_integ_opts {
                              the mechanism-independent kernel, cells equal to
                              rounding), falling back to
                              that kernel when runtime compilation is
-                             unavailable (df_chem_jit_info says why); 1: always
-                             the mechanism-independent kernel                 */
+                             unavailable (df_chem_jit_info says why); compiled
+                             modules are kept in an on-disk cache
+                             ($DF_JIT_CACHE, "0" disables; else
+                             $XDG_CACHE_HOME/df_chem_jit or
+                             ~/.cache/df_chem_jit) keyed by the generated
+                             source, the device headers, the architecture and
+                             the NVRTC version; 1: always the
+                             mechanism-independent kernel                     */
 } df_integ_opts;
 
 void df_integ_opts_default(df_integ_opts* opts);

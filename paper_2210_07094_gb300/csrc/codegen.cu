@@ -23,6 +23,8 @@
 // be found, or the compilation fails, the integrator uses the
 // mechanism-independent kernel and df_chem_jit_info reports why.
 #include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
 
 #include <cuda.h>
 
@@ -250,6 +252,7 @@ typedef int (*nvrtcGetBuf_t)(void*, char*);
 typedef int (*nvrtcDestroyProgram_t)(void**);
 typedef int (*nvrtcAddNameExpression_t)(void*, const char*);
 typedef int (*nvrtcGetLoweredName_t)(void*, const char*, const char**);
+typedef int (*nvrtcVersion_t)(int*, int*);
 
 struct Nvrtc {
   bool ok = false;
@@ -261,6 +264,7 @@ struct Nvrtc {
   nvrtcDestroyProgram_t destroy = nullptr;
   nvrtcAddNameExpression_t add_name = nullptr;
   nvrtcGetLoweredName_t lowered = nullptr;
+  int version = 0;  // major * 1000 + minor
 };
 
 const Nvrtc& nvrtc() {
@@ -287,6 +291,10 @@ const Nvrtc& nvrtc() {
     r.lowered = (nvrtcGetLoweredName_t)dlsym(h, "nvrtcGetLoweredName");
     r.ok = r.create && r.compile && r.log_size && r.log && r.cubin_size && r.cubin && r.destroy && r.add_name &&
            r.lowered;
+    if (auto ver = (nvrtcVersion_t)dlsym(h, "nvrtcVersion")) {
+      int ma = 0, mi = 0;
+      if (ver(&ma, &mi) == 0) r.version = ma * 1000 + mi;
+    }
     if (!r.ok) r.why = "NVRTC library lacks an entry point";
   });
   return r;
@@ -364,6 +372,7 @@ struct Module {
   CUmodule mod = nullptr;
   std::map<int, CUfunction> fn;  // threads per block -> kernel
   size_t compile_ms = 0;
+  bool from_cache = false;
 };
 
 std::mutex g_mu;
@@ -371,13 +380,123 @@ std::map<std::pair<int, std::string>, Module> g_modules;
 
 constexpr int kThreads[] = {32, 64};
 
+// ---------------------------------------------------------------------------
+// on-disk cache of compiled modules: <dir>/<key>.cubin and <key>.names (the
+// lowered names of the kernels and of the table), key = FNV-1a hash of the
+// generated source, the device headers it includes, the target architecture
+// and the NVRTC version.  Directory: $DF_JIT_CACHE ("0" disables), else
+// $XDG_CACHE_HOME/df_chem_jit, else $HOME/.cache/df_chem_jit.
+// ---------------------------------------------------------------------------
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ull) {
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+bool read_file(const std::string& path, std::string* out) {
+  FILE* f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  std::string d;
+  char buf[65536];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) d.append(buf, k);
+  const bool ok = !ferror(f);
+  fclose(f);
+  if (ok) *out = std::move(d);
+  return ok;
+}
+
+bool write_file_atomic(const std::string& path, const std::string& data) {
+  const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)getpid());
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return false;
+  const bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+  if (fclose(f) != 0 || !ok) {
+    remove(tmp.c_str());
+    return false;
+  }
+  return rename(tmp.c_str(), path.c_str()) == 0;
+}
+
+std::string cache_dir() {
+  const char* e = getenv("DF_JIT_CACHE");
+  std::string d;
+  if (e) {
+    if (!*e || std::string(e) == "0") return "";
+    d = e;
+  } else if (const char* x = getenv("XDG_CACHE_HOME")) {
+    d = std::string(x) + "/df_chem_jit";
+  } else if (const char* hm = getenv("HOME")) {
+    d = std::string(hm) + "/.cache/df_chem_jit";
+  } else {
+    return "";
+  }
+  // create the directory and its parents
+  for (size_t pos = 1; pos <= d.size(); ++pos)
+    if (pos == d.size() || d[pos] == '/') mkdir(d.substr(0, pos).c_str(), 0755);
+  return d;
+}
+
+// the device headers' contents, hashed once per process
+uint64_t headers_hash(const std::string& inc) {
+  static uint64_t h = 0;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    uint64_t acc = 1469598103934665603ull;
+    const char* files[] = {"integrate_thread.cuh", "rosenbrock.cuh", "chem_thread.cuh", "dev_common.cuh",
+                           "fastexp.cuh", "fastlog.cuh", "fastlog_table.inc", "dual.cuh"};
+    for (const char* fn : files) {
+      std::string d;
+      read_file(inc + "/" + fn, &d);
+      acc = fnv1a(std::string(fn) + d, acc);
+    }
+    h = acc;
+  });
+  return h;
+}
+
+// resolve the kernels and the table of a loaded cubin, upload the tables
+bool finish_module(Module& r, const Driver& drv, const std::vector<char>& cubin,
+                   const std::vector<std::string>& lowered) {
+  if (drv.load(&r.mod, cubin.data()) != CUDA_SUCCESS) {
+    r.why = "cuModuleLoadData failed";
+    r.mod = nullptr;
+    return false;
+  }
+  for (size_t i = 0; i < sizeof(kThreads) / sizeof(kThreads[0]); ++i) {
+    CUfunction f = nullptr;
+    if (i >= lowered.size() || lowered[i].empty() || drv.get_function(&f, r.mod, lowered[i].c_str()) != CUDA_SUCCESS) {
+      r.why = "generated kernel not found in the module";
+      drv.unload(r.mod);
+      r.mod = nullptr;
+      return false;
+    }
+    r.fn[kThreads[i]] = f;
+  }
+  CUdeviceptr tab = 0;
+  size_t tab_bytes = 0;
+  if (lowered.back().empty() || drv.get_global(&tab, &tab_bytes, r.mod, lowered.back().c_str()) != CUDA_SUCCESS ||
+      tab_bytes != 2 * sizeof(RosTab)) {
+    r.why = "Rosenbrock table not found in the module";
+    drv.unload(r.mod);
+    r.mod = nullptr;
+    return false;
+  }
+  RosTab t[2] = {make_rodas4(), make_rodas3()};
+  if (cudaMemcpy((void*)tab, t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    r.why = "upload of the Rosenbrock tables failed";
+    drv.unload(r.mod);
+    r.mod = nullptr;
+    return false;
+  }
+  r.ok = true;
+  return true;
+}
+
 Module build_module(int dev, const df_mech* m, const std::string& src) {
   Module r;
-  const Nvrtc& nv = nvrtc();
-  if (!nv.ok) {
-    r.why = nv.why;
-    return r;
-  }
   const Driver& drv = driver();
   if (!drv.ok) {
     r.why = "driver entry points for module loading unavailable";
@@ -394,7 +513,37 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
     r.why = "device attributes unavailable";
     return r;
   }
+  const Nvrtc& nv = nvrtc();
   const std::string arch = "--gpu-architecture=sm_" + std::to_string(major * 10 + minor) + "a";
+  std::vector<std::string> names;
+  for (int t : kThreads) names.push_back(jit_kernel_name(m->dims.N, t));
+  names.push_back("&df::c_tab");
+  // the on-disk cache
+  const std::string dir = cache_dir();
+  char key[32] = {0};
+  snprintf(key, sizeof key, "%016llx",
+           (unsigned long long)fnv1a(src + arch + std::to_string(nv.version), headers_hash(inc)));
+  const std::string base = dir.empty() ? std::string() : dir + "/" + key;
+  if (!base.empty()) {
+    std::string bin, nm;
+    if (read_file(base + ".cubin", &bin) && read_file(base + ".names", &nm) && !bin.empty()) {
+      std::vector<std::string> lowered;
+      std::istringstream in(nm);
+      for (std::string line; std::getline(in, line);) lowered.push_back(line);
+      if (lowered.size() == names.size()) {
+        std::vector<char> cubin(bin.begin(), bin.end());
+        if (finish_module(r, drv, cubin, lowered)) {
+          r.from_cache = true;
+          return r;
+        }
+        r = Module();  // unusable entry: compile afresh
+      }
+    }
+  }
+  if (!nv.ok) {
+    r.why = nv.why;
+    return r;
+  }
   const std::string incopt = "-I" + inc;
   const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
                         "-diag-suppress=177"};
@@ -403,9 +552,6 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
     r.why = "nvrtcCreateProgram failed";
     return r;
   }
-  std::vector<std::string> names;
-  for (int t : kThreads) names.push_back(jit_kernel_name(m->dims.N, t));
-  names.push_back("&df::c_tab");
   for (auto& s : names) nv.add_name(prog, s.c_str());
   const auto t0 = std::chrono::steady_clock::now();
   const int rc = nv.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
@@ -431,38 +577,13 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
     lowered.push_back(l ? std::string(l) : std::string());
   }
   nv.destroy(&prog);
-  if (drv.load(&r.mod, cubin.data()) != CUDA_SUCCESS) {
-    r.why = "cuModuleLoadData failed";
-    r.mod = nullptr;
-    return r;
+  if (!finish_module(r, drv, cubin, lowered)) return r;
+  if (!base.empty()) {  // best effort: a failed write only costs the next process a compile
+    std::string nm;
+    for (auto& l : lowered) nm += l + "\n";
+    if (write_file_atomic(base + ".cubin", std::string(cubin.begin(), cubin.end())))
+      write_file_atomic(base + ".names", nm);
   }
-  for (size_t i = 0; i < sizeof(kThreads) / sizeof(kThreads[0]); ++i) {
-    CUfunction f = nullptr;
-    if (lowered[i].empty() || drv.get_function(&f, r.mod, lowered[i].c_str()) != CUDA_SUCCESS) {
-      r.why = "generated kernel not found in the module";
-      drv.unload(r.mod);
-      r.mod = nullptr;
-      return r;
-    }
-    r.fn[kThreads[i]] = f;
-  }
-  CUdeviceptr tab = 0;
-  size_t tab_bytes = 0;
-  if (lowered.back().empty() || drv.get_global(&tab, &tab_bytes, r.mod, lowered.back().c_str()) != CUDA_SUCCESS ||
-      tab_bytes != 2 * sizeof(RosTab)) {
-    r.why = "Rosenbrock table not found in the module";
-    drv.unload(r.mod);
-    r.mod = nullptr;
-    return r;
-  }
-  RosTab t[2] = {make_rodas4(), make_rodas3()};
-  if (cudaMemcpy((void*)tab, t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) {
-    r.why = "upload of the Rosenbrock tables failed";
-    drv.unload(r.mod);
-    r.mod = nullptr;
-    return r;
-  }
-  r.ok = true;
   return r;
 }
 
@@ -481,7 +602,9 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
     if (it == g_modules.end()) it = g_modules.emplace(key, build_module(dev, m, src)).first;
     md = &it->second;
     m->jit_module[dev] = md;
-    m->jit_note = md->ok ? "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms" : md->why;
+    m->jit_note = !md->ok          ? md->why
+                  : md->from_cache ? std::string("generated kernel loaded from the on-disk cache")
+                                   : "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms";
   }
   if (!md->ok) return DF_OK;
   auto f = md->fn.find(threads);

@@ -61,7 +61,7 @@ def test_generated_kernel_runs_and_matches_the_generic_kernel(h2):
     for bt in (32, 64):
         out, used, detail = _run(m, T0, p, Y0, f["dt"], bt, 0)
         assert used, detail
-        assert "compiled" in detail
+        assert "compiled" in detail or "cache" in detail
         print("generated vs mechanism-independent", bt, _close(ref, out))
     # block sizes without a generated kernel run the mechanism-independent one
     out, used, _ = _run(m, T0, p, Y0, f["dt"], 128, 0)
@@ -158,3 +158,43 @@ def test_thread_path_for_a_species_count_without_a_built_kernel():
     # the autotuner weighs the generated thread kernel against the warp path
     best, ms = m.autotune(T0, p, Y0, f["dt"])
     assert best.path in (1, 2) and ms > 0
+
+
+_CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_2210_07094_gb300 as df
+from paper_2210_07094_gb300 import synth
+mech = synth.isomer_mechanism(kind="three-body", A=3e10, eff={"D": 2.5})
+m = df.Mechanism(mech)
+n = 64
+T = torch.full((n,), 1250.0, dtype=torch.float64, device="cuda")
+p = torch.full((n,), 101325.0, dtype=torch.float64, device="cuda")
+Y = torch.tensor(np.tile([[0.6], [0.1], [0.3]], (1, n)), device="cuda")
+df.integrate(m, T, p, Y, 1e-6)
+used, detail = m.jit_info()
+print(json.dumps({"used": used, "detail": detail, "Y0": Y[0].cpu().tolist()}))
+"""
+
+
+def test_compiled_module_is_cached_on_disk(tmp_path):
+    """A second process finds the module the first one compiled in the cache
+    directory (DF_JIT_CACHE) and gives bitwise the same cells."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DF_JIT_CACHE=str(tmp_path / "cache"))
+    out = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _CHILD, root], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert out[0]["used"] and "compiled" in out[0]["detail"], out[0]["detail"]
+    assert out[1]["used"] and "cache" in out[1]["detail"], out[1]["detail"]
+    assert out[0]["Y0"] == out[1]["Y0"]
+    assert sorted(os.listdir(tmp_path / "cache"))[0].endswith(".cubin")
+
