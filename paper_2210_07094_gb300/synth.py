@@ -422,6 +422,12 @@ def _fuel_air_Y(mech, phi, rng):
     return Y
 
 
+# The synthetic workloads, by index: 0 the 9-species H2/air parity field (4096
+# cells, 900-1500 K, 1 atm); 1 the uneven-stiffness field of the throughput
+# benchmark (2^20 cells, half 700-1000 K and half 1800-2500 K interleaved,
+# 1-10 atm); 2 the 50-species CHON field (262144 cells, 800-2200 K, 1 atm); 3
+# the adjoint field (65536 cells, as 0); 4 the surrogate's field (2^22 cells,
+# as 1).  dt = 1 us throughout.
 CONFIGS = {
     0: dict(ncells=4096, T=("uniform", 900.0, 1500.0), p=("const", 1.0), mech="h2"),
     1: dict(ncells=1 << 20, T=("bimodal", 700.0, 1000.0, 1800.0, 2500.0), p=("uniform", 1.0, 10.0),
