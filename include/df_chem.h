@@ -102,8 +102,9 @@ typedef struct df_integ_opts {
                              ($DF_JIT_CACHE, "0" disables; else
                              $XDG_CACHE_HOME/df_chem_jit or
                              ~/.cache/df_chem_jit) keyed by the generated
-                             source, the device headers, the architecture and
-                             the NVRTC version; 1: always the
+                             source, the device headers, the architecture, the
+                             NVRTC version, the compile options and the cache
+                             entry format; 1: always the
                              mechanism-independent kernel                     */
 } df_integ_opts;
 
@@ -211,12 +212,14 @@ int df_chem_adjoint(const df_mech* mech, int64_t ncells, const double* T0, const
                     int32_t* status, int32_t* nsub, void* workspace, size_t ws_bytes, df_stream_t stream);
 
 /* df_chem_adjoint without a workspace argument, for callers that cannot
- * allocate device memory when they need the gradient (a solver running inside a
- * CUDA stream capture, an application whose device memory belongs to a pool or
- * framework that must not be bypassed, a real-time loop that forbids allocation
- * after start-up).  The paper has no counterpart.
+ * allocate device memory when they need the gradient (an application whose
+ * device memory belongs to a pool or framework that must not be bypassed, a
+ * real-time loop that forbids allocation after start-up).  The paper has no
+ * counterpart.
  *
- * Arguments and results as for df_chem_adjoint.  The scratch (checkpoints and
+ * Arguments, argument checks (every pointer must be device memory; the
+ * cotangents, gradients and nsub may be NULL) and results as for
+ * df_chem_adjoint.  The scratch (checkpoints and
  * ln A partial sums) lives in one fixed 4 MiB device array inside the library,
  * held by every GPU that loads it until the process exits; nothing is
  * allocated.  Requests that need more (ncells * max_steps * (N + 2) doubles of

@@ -94,6 +94,7 @@ class Mechanism:
         buf = C.create_string_buffer(4096)
         _lib.check(_lib.load().df_chem_jit_info(self._h, C.byref(used), buf, 4096), "df_chem_jit_info")
         return bool(used.value), buf.value.decode()
+
     def autotune(self, T, p, Y, dt: float, opts: IntegOpts | None = None, sample: int = 0, stream=None):
         """Time the integrator's launch shapes on (a copy of) the first `sample`
         cells and cache the fastest in the handle (df_chem_autotune).
@@ -246,6 +247,8 @@ def _make_chem_step():
 
         @staticmethod
         def forward(ctx, T0, p, Y0, lnA, mech, dt, opts, max_steps):
+            if opts is not None and opts.method != 0:
+                raise ValueError("chem_step: the adjoint differentiates RODAS4 (opts.method = 0)")
             mech.set_lnA(lnA.detach().contiguous())
             T = T0.detach().clone()
             Y = Y0.detach().clone()
@@ -261,6 +264,11 @@ def _make_chem_step():
             T0, p, Y0, lnA = ctx.saved_tensors
             ctx.mech.set_lnA(lnA.contiguous())
             r = adjoint(ctx.mech, T0, p, Y0, ctx.dt, gT, gY, gQ, ctx.opts, ctx.max_steps)
+            bad = int((r["status"] != 0).sum())
+            if bad:
+                raise RuntimeError(f"chem_step backward: {bad} cells failed in the adjoint (status != 0; "
+                                   f"DF_CELL_MAXSTEPS means more than max_steps = {ctx.max_steps} accepted "
+                                   "substeps: raise max_steps)")
             return r["gT0"], None, r["gY0"], r["g_lnA"], None, None, None, None
 
     return ChemStep
@@ -272,7 +280,15 @@ _chem_step = None
 def chem_step(mech: Mechanism, T0, p, Y0, lnA, dt: float, opts: IntegOpts | None = None,
               max_steps: int = 64):
     """Differentiable chemistry substep: returns (T, Y, qdot, status).  Gradients
-    flow to T0, Y0 and lnA (the natural logs of the pre-exponential factors)."""
+    flow to T0, Y0 and lnA (the natural logs of the pre-exponential factors).
+
+    The forward pass runs df_chem_integrate with `opts` (RODAS4 only); the
+    backward pass re-runs RODAS4 inside df_chem_adjoint and differentiates that
+    run with its accepted steps held fixed.  The two evaluations of the rates
+    agree to rounding, so both runs take the same steps except where a step
+    sits exactly on the accept/reject boundary.  A cell that fails in the
+    adjoint (e.g. more than max_steps accepted substeps) raises instead of
+    returning a zero gradient."""
     global _chem_step
     if _chem_step is None:
         _chem_step = _make_chem_step()
@@ -400,19 +416,6 @@ class Dnn:
         a = np.ascontiguousarray(a, np.float32)
         assert a.size == self.n_params
         _lib.check(_lib.load().df_dnn_set_params(self._h, a.ctypes.data_as(C.c_void_p)), "df_dnn_set_params")
-
-    def autotune(self, T, p, Y, dt: float, opts: IntegOpts | None = None, sample: int = 0, stream=None):
-        """Time the integrator's launch shapes on (a copy of) the first `sample`
-        cells and cache the fastest in the handle (df_chem_autotune).
-        Returns (best IntegOpts, its time in ms)."""
-        n, pT, pp, pY = _cells(self, T, p, Y)
-        best = IntegOpts()
-        ms = C.c_float()
-        _lib.check(_lib.load().df_chem_autotune(self._h, n, pT, pp, pY, float(dt),
-                                                C.byref(opts) if opts is not None else None, int(sample),
-                                                C.byref(best), C.byref(ms), _stream_ptr(stream)),
-                   "df_chem_autotune")
-        return best, ms.value
 
     def close(self):
         if getattr(self, "_h", None):

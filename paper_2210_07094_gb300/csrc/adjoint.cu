@@ -345,17 +345,32 @@ static constexpr int ADJ_THREADS = 32;
 
 // Workspace: checkpoints [ncells][cap][n + 1], then the per-block ln A
 // partials, then (with_stages) the stored stages [cap][7n + n^2][ncells].
-static size_t adj_compact_doubles(const df_mech* m, int64_t ncells, int cap) {
-  const int n = m->dims.N + 1;
-  const int64_t blocks = (ncells + ADJ_THREADS - 1) / ADJ_THREADS;
-  return (size_t)ncells * cap * (n + 1) + (size_t)blocks * m->dims.M;
+// Every product and sum is overflow-checked: a size that does not fit in
+// size_t is reported, never wrapped to a small one.
+static bool adj_compact_doubles(const df_mech* m, int64_t ncells, int cap, size_t* out) {
+  if (ncells < 0 || cap < 1) return false;
+  const size_t n = (size_t)m->dims.N + 1;
+  const size_t blocks = ((size_t)ncells + ADJ_THREADS - 1) / ADJ_THREADS;
+  size_t ck = 0, part = 0;
+  if (__builtin_mul_overflow((size_t)ncells, (size_t)cap, &ck) || __builtin_mul_overflow(ck, n + 1, &ck) ||
+      __builtin_mul_overflow(blocks, (size_t)m->dims.M, &part) || __builtin_add_overflow(ck, part, out))
+    return false;
+  return true;
 }
 
-size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages) {
-  const int n = m->dims.N + 1;
-  size_t d = adj_compact_doubles(m, ncells, cap);
-  if (with_stages) d += (size_t)ncells * cap * (7 * n + n * n);
-  return sizeof(double) * d + 256;
+bool adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages, size_t* bytes) {
+  size_t d = 0;
+  if (!adj_compact_doubles(m, ncells, cap, &d)) return false;
+  if (with_stages) {
+    const size_t n = (size_t)m->dims.N + 1;
+    size_t st = 0;
+    if (__builtin_mul_overflow((size_t)ncells, (size_t)cap, &st) || __builtin_mul_overflow(st, 7 * n + n * n, &st) ||
+        __builtin_add_overflow(d, st, &d))
+      return false;
+  }
+  if (__builtin_mul_overflow(d, sizeof(double), &d) || __builtin_add_overflow(d, (size_t)256, &d)) return false;
+  *bytes = d;
+  return true;
 }
 
 template <int NS>
@@ -388,9 +403,13 @@ int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const dou
                    const double* gQ1, double* gT0, double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
                    void* ws, size_t ws_bytes, bool allow_stages, cudaStream_t st) {
   if (o.method != 0) return set_error(DF_EUNSUPPORTED, "the adjoint is built for RODAS4 (method 0)");
-  const size_t need = adjoint_workspace_bytes(m, ncells, cap, false);
+  if (ncells > ((int64_t)1 << 31)) return set_error(DF_EINVAL, "adjoint: ncells must be in [0, 2^31]");
+  size_t need = 0, full = 0;
+  if (!adjoint_workspace_bytes(m, ncells, cap, false, &need))
+    return set_error(DF_EWORKSPACE, "adjoint: ncells * max_steps checkpoints overflow the address space");
   if (!ws || ws_bytes < need) return set_error(DF_EWORKSPACE, "adjoint workspace too small");
-  const bool keep_stages = allow_stages && ws_bytes >= adjoint_workspace_bytes(m, ncells, cap, true);
+  const bool keep_stages =
+      allow_stages && adjoint_workspace_bytes(m, ncells, cap, true, &full) && ws_bytes >= full;
   int rc = ensure_adj_table(m->device);
   if (rc) return rc;
   const int n = m->dims.N + 1;
@@ -417,9 +436,11 @@ int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const dou
   a.gY0 = gY0;
   a.status = status;
   a.nsub = nsub;
+  size_t compact = 0;
+  adj_compact_doubles(m, ncells, cap, &compact);  // fits: checked above
   a.ckpt = static_cast<double*>(ws);
   a.partial = static_cast<double*>(ws) + (size_t)ncells * cap * (n + 1);
-  a.stages = keep_stages ? static_cast<double*>(ws) + adj_compact_doubles(m, ncells, cap) : nullptr;
+  a.stages = keep_stages ? static_cast<double*>(ws) + compact : nullptr;
   switch (m->dims.N) {
     case 3:
       return adjoint_dispatch<3>(m, a, st, g_lnA);
@@ -436,10 +457,10 @@ int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const dou
 // df_chem_adjoint_static: the adjoint without any allocation by the library or
 // the caller for its scratch.
 //
-// Some callers cannot call cudaMalloc when they need a gradient: a solver
-// running inside a CUDA stream capture, a host application whose device memory
-// is owned by a pool or another framework that must not be bypassed, or a
-// real-time loop that forbids allocation after start-up.  This entry point
+// Some callers cannot call cudaMalloc when they need a gradient: a host
+// application whose device memory is owned by a pool or another framework that
+// must not be bypassed, or a real-time loop that forbids allocation after
+// start-up.  This entry point
 // keeps the adjoint's scratch (the per-cell checkpoints and the per-block ln A
 // partial sums) in one file-scope device array instead, so the caller only
 // passes its inputs and outputs.
@@ -480,26 +501,20 @@ extern "C" int df_chem_adjoint_static(const df_mech* m, int64_t ncells, const do
                                       double* gY0, double* g_lnA, int32_t* status, int32_t* nsub,
                                       df_stream_t stream) {
   using namespace df;
-  if (!m) return set_error(DF_EINVAL, "df_chem_adjoint_static: null mechanism");
-  if (ncells < 0 || max_steps < 1) return set_error(DF_EINVAL, "df_chem_adjoint_static: ncells >= 0, max_steps >= 1");
-  if (ncells == 0) return DF_OK;
-  if (!T0 || !p || !Y0 || !status) return set_error(DF_EINVAL, "df_chem_adjoint_static: null input or status");
-  if (!(dt >= 0.0) || !std::isfinite(dt)) return set_error(DF_EINVAL, "df_chem_adjoint_static: dt must be finite and >= 0");
-  const size_t need = adjoint_workspace_bytes(m, ncells, max_steps, false);
-  if (need > ADJ_STATIC_BYTES)
-    return set_error(DF_EWORKSPACE,
-                     "df_chem_adjoint_static: ncells * max_steps * (N + 2) checkpoints plus the ln A partials need " +
-                         std::to_string(need) + " bytes, more than the fixed 4 MiB scratch; use df_chem_adjoint "
-                         "with a caller-provided workspace");
+  const char* fn = "df_chem_adjoint_static";
   df_integ_opts o;
-  if (opts) o = *opts;
-  else df_integ_opts_default(&o);
-  if (o.reactor != 0) return set_error(DF_EUNSUPPORTED, "df_chem_adjoint_static: constant-pressure reactor only");
-  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
-      o.max_substeps < 1)
-    return set_error(DF_EINVAL, "df_chem_adjoint_static: invalid options");
+  int rc = check_adjoint_call(fn, m, ncells, dt, max_steps, T0, p, Y0, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub,
+                              opts, &o);
+  if (rc || ncells == 0) return rc;
+  size_t need = 0;
+  if (!adjoint_workspace_bytes(m, ncells, max_steps, false, &need) || need > ADJ_STATIC_BYTES)
+    return set_error(DF_EWORKSPACE,
+                     std::string(fn) + ": ncells * max_steps * (N + 2) checkpoints plus the ln A partials need " +
+                         (need > ADJ_STATIC_BYTES ? std::to_string(need) + " bytes" : std::string("more bytes than "
+                         "size_t holds")) + ", more than the fixed 4 MiB scratch; use df_chem_adjoint with a "
+                         "caller-provided workspace");
   void* ws = nullptr;
-  int rc = adj_static_scratch(&ws);
+  rc = adj_static_scratch(&ws);
   if (rc) return rc;
   return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub, ws,
                         ADJ_STATIC_BYTES, false, (cudaStream_t)stream);

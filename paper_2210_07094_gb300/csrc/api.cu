@@ -153,6 +153,36 @@ static int check_dev(const char* fn, const char* name, const void* p) {
   return DF_OK;
 }
 
+}  // extern "C"
+
+namespace df {
+int check_adjoint_call(const char* fn, const df_mech* m, int64_t ncells, double dt, int32_t max_steps,
+                       const double* T0, const double* p, const double* Y0, const double* gT1, const double* gY1,
+                       const double* gQ1, const double* gT0, const double* gY0, const double* g_lnA,
+                       const int32_t* status, const int32_t* nsub, const df_integ_opts* opts, df_integ_opts* o) {
+  int rc = check_cells(fn, m, ncells);
+  if (rc || ncells == 0) return rc;
+  if (!(dt >= 0.0) || !std::isfinite(dt) || max_steps < 1)
+    return set_error(DF_EINVAL, std::string(fn) + ": dt must be finite and >= 0, max_steps >= 1");
+  if ((rc = check_dev(fn, "T0", T0)) || (rc = check_dev(fn, "p", p)) || (rc = check_dev(fn, "Y0", Y0)) ||
+      (rc = check_dev(fn, "status", status)))
+    return rc;
+  const void* opt_ptrs[] = {gT1, gY1, gQ1, gT0, gY0, g_lnA, nsub};
+  const char* opt_names[] = {"gT1", "gY1", "gQ1", "gT0", "gY0", "g_lnA", "nsub"};
+  for (int i = 0; i < 7; ++i)
+    if (opt_ptrs[i] && (rc = check_dev(fn, opt_names[i], opt_ptrs[i]))) return rc;
+  if (opts) *o = *opts;
+  else df_integ_opts_default(o);
+  if (o->reactor != 0) return set_error(DF_EUNSUPPORTED, std::string(fn) + ": constant-pressure reactor only");
+  if (!(o->rtol > 0.0) || !(o->atol_Y > 0.0) || !(o->atol_T > 0.0) || !(o->h0 > 0.0) || !(o->h_min >= 0.0) ||
+      o->max_substeps < 1)
+    return set_error(DF_EINVAL, std::string(fn) + ": invalid options");
+  return DF_OK;
+}
+}  // namespace df
+
+extern "C" {
+
 int df_chem_rhs(const df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y,
                 double* dydt, double* qdot, df_stream_t stream) {
   int rc = check_cells("df_chem_rhs", m, ncells);
@@ -244,7 +274,8 @@ int df_chem_adjoint_workspace_size(const df_mech* m, int64_t ncells, int32_t max
   int rc = check_cells("df_chem_adjoint_workspace_size", m, ncells);
   if (rc) return rc;
   if (max_steps < 1 || !bytes) return set_error(DF_EINVAL, "df_chem_adjoint_workspace_size: bad arguments");
-  *bytes = adjoint_workspace_bytes(m, ncells, max_steps, true);
+  if (!adjoint_workspace_bytes(m, ncells, max_steps, true, bytes))
+    return set_error(DF_EWORKSPACE, "df_chem_adjoint_workspace_size: the size does not fit in size_t");
   return DF_OK;
 }
 
@@ -253,25 +284,11 @@ int df_chem_adjoint(const df_mech* m, int64_t ncells, const double* T0, const do
                     const double* gY1, const double* gQ1, double* gT0, double* gY0, double* g_lnA,
                     int32_t* status, int32_t* nsub, void* workspace, size_t ws_bytes, df_stream_t stream) {
   const char* fn = "df_chem_adjoint";
-  int rc = check_cells(fn, m, ncells);
-  if (rc || ncells == 0) return rc;
-  if (!(dt >= 0.0) || !std::isfinite(dt) || max_steps < 1)
-    return set_error(DF_EINVAL, "df_chem_adjoint: dt must be finite and >= 0, max_steps >= 1");
-  if ((rc = check_dev(fn, "T0", T0)) || (rc = check_dev(fn, "p", p)) || (rc = check_dev(fn, "Y0", Y0)) ||
-      (rc = check_dev(fn, "status", status)))
-    return rc;
-  const void* opt_ptrs[] = {gT1, gY1, gQ1, gT0, gY0, g_lnA, nsub};
-  const char* opt_names[] = {"gT1", "gY1", "gQ1", "gT0", "gY0", "g_lnA", "nsub"};
-  for (int i = 0; i < 7; ++i)
-    if (opt_ptrs[i] && (rc = check_dev(fn, opt_names[i], opt_ptrs[i]))) return rc;
-  if (workspace && (rc = check_dev(fn, "workspace", workspace))) return rc;
   df_integ_opts o;
-  if (opts) o = *opts;
-  else df_integ_opts_default(&o);
-  if (o.reactor != 0) return set_error(DF_EUNSUPPORTED, "df_chem_adjoint: constant-pressure reactor only");
-  if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || !(o.h_min >= 0.0) ||
-      o.max_substeps < 1)
-    return set_error(DF_EINVAL, "df_chem_adjoint: invalid options");
+  int rc = check_adjoint_call(fn, m, ncells, dt, max_steps, T0, p, Y0, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub,
+                              opts, &o);
+  if (rc || ncells == 0) return rc;
+  if (workspace && (rc = check_dev(fn, "workspace", workspace))) return rc;
   return launch_adjoint(m, ncells, T0, p, Y0, dt, o, max_steps, gT1, gY1, gQ1, gT0, gY0, g_lnA, status, nsub,
                         workspace, ws_bytes, true, (cudaStream_t)stream);
 }

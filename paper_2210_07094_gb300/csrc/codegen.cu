@@ -495,6 +495,10 @@ bool finish_module(Module& r, const Driver& drv, const std::vector<char>& cubin,
   return true;
 }
 
+// Version of the cached entries (the cubin and its lowered-name list, and what
+// finish_module expects of them); raised whenever either changes.
+constexpr int kCacheFormat = 2;
+
 Module build_module(int dev, const df_mech* m, const std::string& src) {
   Module r;
   const Driver& drv = driver();
@@ -518,11 +522,18 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
   std::vector<std::string> names;
   for (int t : kThreads) names.push_back(jit_kernel_name(m->dims.N, t));
   names.push_back("&df::c_tab");
-  // the on-disk cache
+  const std::string incopt = "-I" + inc;
+  const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
+                        "-diag-suppress=177"};
+  // the on-disk cache: keyed by the generated source, the device headers, the
+  // architecture, the NVRTC version, the compile options (the include path
+  // left out: a moved tree keeps its entries) and the entry format
   const std::string dir = cache_dir();
+  std::string keysrc = src + arch + std::to_string(nv.version) + "|format " + std::to_string(kCacheFormat);
+  for (const char* o : opts)
+    if (o != incopt.c_str()) keysrc += std::string("|") + o;
   char key[32] = {0};
-  snprintf(key, sizeof key, "%016llx",
-           (unsigned long long)fnv1a(src + arch + std::to_string(nv.version), headers_hash(inc)));
+  snprintf(key, sizeof key, "%016llx", (unsigned long long)fnv1a(keysrc, headers_hash(inc)));
   const std::string base = dir.empty() ? std::string() : dir + "/" + key;
   if (!base.empty()) {
     std::string bin, nm;
@@ -544,9 +555,6 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
     r.why = nv.why;
     return r;
   }
-  const std::string incopt = "-I" + inc;
-  const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
-                        "-diag-suppress=177"};
   void* prog = nullptr;
   if (nv.create(&prog, src.c_str(), "df_generated.cu", 0, nullptr, nullptr) != 0) {
     r.why = "nvrtcCreateProgram failed";

@@ -85,8 +85,16 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
 
 // adjoint (adjoint.cu)
 // with_stages: also room for the stored stages and LU factors of every
-// accepted step (the reverse sweep then skips recomputing the step)
-size_t adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages);
+// accepted step (the reverse sweep then skips recomputing the step); false
+// when the size does not fit in size_t
+bool adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool with_stages, size_t* bytes);
+// argument checks shared by df_chem_adjoint and df_chem_adjoint_static (api.cu):
+// the cell count, dt, max_steps, every pointer (device memory; the cotangents,
+// gradients and nsub may be NULL) and the options, which *o receives
+int check_adjoint_call(const char* fn, const df_mech* m, int64_t ncells, double dt, int32_t max_steps,
+                       const double* T0, const double* p, const double* Y0, const double* gT1, const double* gY1,
+                       const double* gQ1, const double* gT0, const double* gY0, const double* g_lnA,
+                       const int32_t* status, const int32_t* nsub, const df_integ_opts* opts, df_integ_opts* o);
 // allow_stages: keep the stages when ws_bytes has room for them
 int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
                    double dt, const df_integ_opts& o, int cap, const double* gT1, const double* gY1,

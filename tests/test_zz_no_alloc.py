@@ -1,8 +1,7 @@
 """The adjoint entry point that allocates nothing (df_chem_adjoint_static).
 
 It serves callers that cannot allocate device memory at the moment they need a
-gradient (inside a stream capture, under an external memory pool, in a loop
-that forbids allocation).  The test calls it through the C ABI twice in a row,
+gradient (under an external memory pool, in a loop that forbids allocation).  The test calls it through the C ABI twice in a row,
 on different inputs, and checks each result against df_chem_adjoint with a
 caller-provided workspace; then checks that an oversize request is refused
 with a clear error.  This file is collected last.
@@ -69,3 +68,34 @@ def test_static_scratch_adjoint_refuses_oversize_requests():
     buf = C.create_string_buffer(512)
     L.df_get_last_error_detail(buf, 512)
     assert b"4 MiB" in buf.value
+
+
+def test_static_scratch_adjoint_rejects_wrapping_sizes_and_host_pointers():
+    """Sizes whose checkpoint count overflows 64 bits are refused, not wrapped
+    to a small size, and a host pointer is refused before any launch (both
+    entry points share the same argument checks)."""
+    import paper_2210_07094_gb300 as df
+    from paper_2210_07094_gb300 import _lib, synth
+
+    L = _lib.load()
+    m = df.Mechanism(synth.h2_air_mechanism())
+    size = C.c_size_t(0)
+    # 2^31 cells x (2^31 - 1) steps x 11 doubles x 8 bytes exceeds 2^64
+    assert L.df_chem_adjoint_workspace_size(m.handle, 1 << 31, (1 << 31) - 1, C.byref(size)) == -5
+    dev = torch.zeros(16, dtype=torch.float64, device=DEV)
+    st = torch.zeros(16, dtype=torch.int32, device=DEV)
+    rc = L.df_chem_adjoint_static(m.handle, 1 << 31, _ptr(dev), _ptr(dev), _ptr(dev), C.c_double(1e-6), None,
+                                  (1 << 30), None, None, None, None, None, None, _ptr(st), None, None)
+    assert rc == -5  # DF_EWORKSPACE, before anything is launched
+    host = np.zeros(16)
+    hp = C.c_void_p(host.ctypes.data)
+    for fn in (L.df_chem_adjoint_static,):
+        rc = fn(m.handle, 16, hp, _ptr(dev), _ptr(dev), C.c_double(1e-6), None, 4, None, None, None, None,
+                None, None, _ptr(st), None, None)
+        assert rc == -1  # DF_EINVAL: T0 is not device memory
+    rc = L.df_chem_adjoint_static(m.handle, 16, _ptr(dev), _ptr(dev), _ptr(dev), C.c_double(1e-6), None, 4,
+                                  hp, None, None, None, None, None, _ptr(st), None, None)
+    assert rc == -1  # a cotangent in host memory
+    buf = C.create_string_buffer(512)
+    L.df_get_last_error_detail(buf, 512)
+    assert b"gT1 must be device memory" in buf.value
