@@ -10,7 +10,14 @@ What it computes (numpy, FP64 unless a rounding point says otherwise):
   * a fully connected network with three hidden layers (Sec. 2.3), exact-erf
     GELU, and its gradient for the mean-squared error;
   * stage 3 of DNNInferencer.inference (Sec. 3.2): Y' = F^{-1}(F(Y) + u),
-    renormalised, and T' from h(T', Y') = h(T, Y) at fixed p (correctThermo).
+    renormalised, and T' from h(T', Y') = h(T, Y) at fixed p (correctThermo);
+    species that no reaction changes (net stoichiometric coefficient zero in
+    every reaction, e.g. an inert collider) keep their input mass fraction and
+    the renormalisation acts on the others (the paper is silent; this keeps
+    dY_k/dt = 0 for those species exact, as the kinetics has it);
+  * the optimiser the paper leaves open (Sec. 2.3 says only that the network
+    is trained): Adam, Kingma & Ba 2015, Algorithm 1, with bias-corrected
+    first and second moments, in FP64 on the FP32 master weights.
 
 Rounding points (``emulate=True``) follow the GPU path: features rounded to
 FP32 then to BF16, weights BF16, products accumulated in FP64 here (FP32 on
@@ -19,7 +26,10 @@ even); in the backward pass dU, dZ = (dH * gelu'(Z)) are rounded to BF16.
 ``emulate=False`` is the exact FP64 network, pinned by finite differences.
 
 Parity status: pinned (tests/test_oracle_mlp.py: finite differences of the
-exact network; BF16 rounding against a library conversion).
+exact network; BF16 rounding against a library conversion; the Box-Cox
+features against hand-computed values; Adam against a hand-worked two-step
+example and its closed-form first step; the post stage against its fixed
+points and the inert-species rule).
 """
 from __future__ import annotations
 
@@ -135,13 +145,51 @@ def loss_and_grads(params, X, tgt, N, emulate=True):
     return loss, g, U
 
 
-def post(T, p, Y, U, lam, norm, N, nasa, W):
+def inert_species(mech: dict) -> np.ndarray:
+    """Species whose net stoichiometric coefficient is zero in every reaction
+    of the mechanism (Sec. 2.3 eq. (sourceeq): their production rate is then
+    identically zero).  Boolean [N] in the mechanism's species order."""
+    names = [sp["name"] for sp in mech["species"]]
+    net = np.zeros(len(names))
+    seen = np.zeros(len(names), bool)
+    for r in mech["reactions"]:
+        nu = np.zeros(len(names))
+        for side, sgn in (("reactants", -1.0), ("products", 1.0)):
+            for name, c in r[side].items():
+                nu[names.index(name)] += sgn * c
+        seen |= nu != 0.0
+    return ~seen
+
+
+def adam_step(theta, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1), FP64:
+    m <- beta1 m + (1 - beta1) g;  v <- beta2 v + (1 - beta2) g^2;
+    m_hat = m / (1 - beta1^t);  v_hat = v / (1 - beta2^t);
+    theta <- theta - lr m_hat / (sqrt(v_hat) + eps).   t counts from 1.
+    Returns (theta, m, v)."""
+    theta, m, v, g = (np.asarray(a, np.float64) for a in (theta, m, v, g))
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def post(T, p, Y, U, lam, norm, N, nasa, W, inert=None):
     """Stage 3 of the inference (FP64): Y' = F^{-1}(F(Y) + u) renormalised, and T'
-    with h(T', Y') = h(T, Y).  nasa [N, 7], W [N] (g/mol)."""
+    with h(T', Y') = h(T, Y).  nasa [N, 7], W [N] (g/mol).  inert [N] (bool,
+    optional): species kept at their input mass fraction; the others are
+    scaled so that the mass fractions sum to one."""
     u = U[:, :N] * norm["std_out"][:N] + norm["mean_out"][:N]
     z = np.maximum(Y.T, 0.0) ** lam + lam * u
     Yn = np.where(z > 0, np.maximum(z, 0.0) ** (1.0 / lam), 0.0)
-    Yn = Yn / Yn.sum(axis=1, keepdims=True)
+    if inert is None or not np.any(inert):
+        Yn = Yn / Yn.sum(axis=1, keepdims=True)
+    else:
+        inert = np.asarray(inert, bool)
+        Yn[:, inert] = Y.T[:, inert]
+        rest = 1.0 - Yn[:, inert].sum(axis=1, keepdims=True)
+        Yn[:, ~inert] = Yn[:, ~inert] * (rest / Yn[:, ~inert].sum(axis=1, keepdims=True))
 
     def h_mass(Tk, Yk):  # h / R per unit mass, sum_k Y_k/W_k * H_k/R
         a = nasa

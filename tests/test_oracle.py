@@ -459,3 +459,27 @@ def test_constant_volume_jacobian_vs_finite_differences(h2):
         fv = h2.rhs_v(rho, y)[0]
         fp = h2.rhs(f["p"][c], y)[0]
         assert np.allclose(fv[1:], fp[1:], rtol=1e-12, atol=0)
+
+
+def test_parity_check_rejects_a_kernel_that_returns_its_input():
+    """The acceptance check used by every integrator parity test must fail a
+    'kernel' that returns its input unchanged, on the 0D H2/air field where
+    the whole change over dt is below the absolute bar (1e-3 K, 1e-7 max Y),
+    and one that takes a slightly wrong step (dt * (1 - 1e-2)); the oracle's
+    own result at a tighter tolerance passes."""
+    from oracle.parity import check_integrator
+    mech = synth.h2_air_mechanism()
+    o = Mech(mech)
+    f = synth.field(0, mech, 300)
+    To, Yo, so, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"])
+    assert np.all(so == 0)
+    # the absolute bar alone cannot tell: the whole change is below it
+    assert np.abs(To - f["T"]).max() < 1e-3
+    assert (np.abs(Yo - f["Y"]).max(axis=0) / Yo.max(axis=0)).max() < 1e-7
+    with pytest.raises(AssertionError):
+        check_integrator(f["T"], f["Y"], f["T"], f["Y"], To, Yo)
+    Tw, Yw, _, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"] * (1 - 1e-2))
+    with pytest.raises(AssertionError):
+        check_integrator(f["T"], f["Y"], Tw, Yw, To, Yo)
+    Tt, Yt, _, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"], rtol=1e-12, atolT=1e-12)
+    check_integrator(f["T"], f["Y"], Tt, Yt, To, Yo)

@@ -80,3 +80,80 @@ def test_post_inverts_the_transform_and_keeps_enthalpy():
         assert abs(o.enthalpy_mass(T2[c], Y2[:, c]) - o.enthalpy_mass(f["T"][c], f["Y"][:, c])) <= \
             1e-9 * 1.5e3 * f["T"][c]
     assert np.allclose(Y2.sum(axis=0), 1.0, rtol=1e-14)
+
+
+def test_box_cox_features_hand_values():
+    """F(Y) = (max(Y, 0)^lambda - 1) / lambda at lambda = 0.1 (Sec. 2.3, Box-Cox):
+    F(1) = 0, F(0) = -1/lambda, F(1e-6) = (10^-0.6 - 1)/0.1, F(0.01) = (10^-0.2 - 1)/0.1,
+    a negative mass fraction clipped to F(0); then the z-score in FP32."""
+    N = 5
+    Y = np.array([[1.0], [0.0], [1e-6], [0.01], [-1e-3]])
+    T = np.array([1500.0])
+    p = np.array([101325.0])
+    norm = {"mean_in": np.r_[1200.0, 101325.0, -5.0, -5.0, -5.0, -5.0, -5.0, np.zeros(9)],
+            "std_in": np.r_[300.0, 1.0, 2.5, 2.5, 2.5, 2.5, 2.5, np.ones(9)]}
+    f, x = mlp.features(T, p, Y, 0.1, norm, N)
+    expect_F = [0.0, -10.0, -7.4881135684904199, -3.6904265551980675, -10.0]
+    assert f[0, 0] == 1500.0 and f[0, 1] == 101325.0
+    assert np.allclose(f[0, 2:2 + N], expect_F, rtol=1e-14, atol=1e-14)
+    # z-score in FP32: (1500 - 1200)/300 = 1, (101325 - 101325)/1 = 0, (F + 5)/2.5
+    assert x.dtype == np.float32
+    assert x[0, 0] == np.float32(1.0) and x[0, 1] == np.float32(0.0)
+    zs = [(np.float32(v) - np.float32(-5.0)) / np.float32(2.5) for v in expect_F]
+    assert np.allclose(x[0, 2:2 + N], zs, rtol=2e-7, atol=2e-7)
+    assert np.all(x[0, 2 + N:] == 0.0)
+
+
+def test_adam_hand_worked_two_steps():
+    """theta0 = 1, gradients 0.5 then -0.25, lr 0.1, beta 0.9 / 0.999, eps 1e-8
+    (Kingma & Ba 2015, Algorithm 1), worked by hand in exact fractions:
+    step 1: m = 1/20, v = 1/4000, m_hat = 1/2, v_hat = 1/4,
+            theta = 1 - 0.1 * 0.5 / (0.5 + 1e-8) = 0.90000000199999996...
+    step 2: m = 1/50, v = 1249/4000000, m_hat = 2/19, v_hat = 1249/7996,
+            sqrt(v_hat) = 0.39522538070166418..., theta = 0.87336629870784616..."""
+    th, m, v = np.array([1.0]), np.zeros(1), np.zeros(1)
+    th, m, v = mlp.adam_step(th, m, v, np.array([0.5]), 1, 0.1)
+    # FP64 rounding of the decimal constants only: a few ulp
+    assert abs(m[0] - 0.05) <= 4e-15 * 0.05 and abs(v[0] - 0.00025) <= 4e-15 * 0.00025
+    assert abs(th[0] - 0.90000000199999996) <= 1e-15
+    th, m, v = mlp.adam_step(th, m, v, np.array([-0.25]), 2, 0.1)
+    assert abs(m[0] - 0.02) <= 4e-15 * 0.02 and abs(v[0] - 0.00031225) <= 4e-15 * 0.00031225
+    assert abs(th[0] - 0.87336629870784616) <= 1e-15
+
+
+def test_adam_closed_forms():
+    """With the bias corrections, the first step moves every parameter by
+    lr g/(|g| + eps) whatever beta1, beta2; a constant gradient keeps m_hat = g
+    and v_hat = g^2 at every step, so every step moves by the same amount."""
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal(1000) * 10 ** rng.uniform(-6, 2, 1000)
+    th0 = rng.standard_normal(1000)
+    for b1, b2 in ((0.9, 0.999), (0.5, 0.9)):
+        th, m, v = mlp.adam_step(th0, np.zeros(1000), np.zeros(1000), g, 1, 1e-3, b1, b2)
+        assert np.allclose(th, th0 - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    th, m, v = th0.copy(), np.zeros(1000), np.zeros(1000)
+    for t in range(1, 51):
+        th_prev = th
+        th, m, v = mlp.adam_step(th, m, v, g, t, 1e-3)
+        assert np.allclose(th_prev - th, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-9, atol=1e-18)
+
+
+def test_inert_species_keep_their_mass_fraction():
+    """N2 takes part in no reaction of the 9-species mechanism (a collider only),
+    so its mass fraction must not change; the renormalisation acts on the rest
+    and the mass fractions still sum to one."""
+    mech = synth.h2_air_mechanism()
+    inert = mlp.inert_species(mech)
+    names = [s["name"] for s in mech["species"]]
+    assert [names[k] for k in np.where(inert)[0]] == ["N2"]
+    o = Mech(mech)
+    f = synth.field(1, mech, 20)
+    U = np.zeros((20, 16))
+    U[:, :9] = np.random.default_rng(6).standard_normal((20, 9)) * 0.01
+    norm = {"mean_out": np.zeros(16), "std_out": np.ones(16)}
+    T2, Y2 = mlp.post(f["T"], f["p"], f["Y"], U, 0.1, norm, 9, o.nasa, o.W, inert=inert)
+    assert np.array_equal(Y2[inert], f["Y"][inert])
+    assert np.allclose(Y2.sum(axis=0), 1.0, rtol=1e-14)
+    for c in range(20):
+        assert abs(o.enthalpy_mass(T2[c], Y2[:, c]) - o.enthalpy_mass(f["T"][c], f["Y"][:, c])) <= \
+            1e-9 * 1.5e3 * f["T"][c]
