@@ -349,6 +349,37 @@ int df_dnn_fit_norm(df_dnn* dnn, int64_t n, const double* T, const double* p, co
 int df_dnn_train_step(df_dnn* dnn, int64_t n, const double* T, const double* p, const double* Y,
                       const double* Y_next, float lr, float* loss_out, df_stream_t stream);
 
+/* The training step in two halves, for data-parallel training over several
+ * GPUs (each rank holds a shard of the training pairs; the paper names
+ * multi-GPU DNN work as future work, Sec. 6):
+ *  df_dnn_grad: the forward and backward pass of df_dnn_train_step on n pairs
+ *    (same arguments, no lr), leaving in the handle's FP32 gradient buffer the
+ *    gradient of this shard's share of a loss averaged over n_total >= n rows:
+ *    sum over the n rows and N outputs of the squared error / (n_total N).
+ *    With n_total = n it is df_dnn_train_step's gradient; with n_total the
+ *    rows of all ranks, summing the buffers over the ranks gives the gradient
+ *    of the whole batch (every row's output gradient, and its BF16 rounding,
+ *    the same as in one pass over the union).  loss_out (host, may be NULL):
+ *    this shard's share of the loss, same normalisation.  The parameters are
+ *    not changed.
+ *  df_dnn_grad_buffer: *grads receives the device address of that buffer
+ *    (df_dnn_param_count() floats, layout of df_dnn_get_params), *count (may be
+ *    NULL) its length, so the caller can all-reduce it in place (sum over the
+ *    ranks) between the two halves.  The handle owns the buffer.
+ *  df_dnn_adam_step: one Adam step (the handle's step counter advances, as in
+ *    df_dnn_train_step) with the gradient now in the buffer, then the BF16
+ *    weight copies.
+ * df_dnn_grad (n_total = n) then df_dnn_adam_step equals df_dnn_train_step.
+ * Asynchronous on `stream` except for loss_out, which synchronises it. */
+int df_dnn_grad(df_dnn* dnn, int64_t n, int64_t n_total, const double* T, const double* p, const double* Y,
+                const double* Y_next, float* loss_out, df_stream_t stream);
+int df_dnn_grad_buffer(df_dnn* dnn, float** grads, int64_t* count);
+int df_dnn_adam_step(df_dnn* dnn, float lr, df_stream_t stream);
+
+/* Adam state (host buffers of df_dnn_param_count() floats each, may be NULL):
+ * the first and second moment estimates, and the number of steps taken. */
+int df_dnn_get_adam_state(const df_dnn* dnn, float* m1, float* m2, int64_t* step);
+
 /* Advance ncells cells over dt with the network (T, Y in/out, device).  Cells
  * whose inputs leave the training range [in_min, in_max] (widened by
  * range_margin) are advanced by df_chem_integrate with fallback_opts (NULL =

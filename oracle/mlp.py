@@ -119,8 +119,10 @@ def forward(params, X, emulate=True):
     return U, cache
 
 
-def loss_and_grads(params, X, tgt, N, emulate=True):
-    """Mean squared error over the first N outputs and its parameter gradients."""
+def loss_and_grads(params, X, tgt, N, emulate=True, return_cache=False):
+    """Mean squared error over the first N outputs and its parameter gradients.
+    return_cache: also return the forward cache and the backward products
+    dZ_l (and dU), for scale estimates in tests."""
     P = params
     n = X.shape[0]
     U, c = forward(P, X, emulate)
@@ -135,13 +137,17 @@ def loss_and_grads(params, X, tgt, N, emulate=True):
     g["b4"] = dU.sum(axis=0)
     W = {l: (bf16(P[f"W{l}"]).astype(np.float64) if emulate else P[f"W{l}"]) for l in (1, 2, 3, 4)}
     dH = dU @ W[4]
+    c["dZ4"] = dU
     for l in (3, 2, 1):
         dZ = dH * gelu_grad(c[f"Z{l}"])
         if emulate:
             dZ = bf16(dZ).astype(np.float64)
+        c[f"dZ{l}"] = dZ
         g[f"W{l}"] = dZ.T @ c[f"H{l - 1}"]
         g[f"b{l}"] = dZ.sum(axis=0)
         dH = dZ @ W[l]
+    if return_cache:
+        return loss, g, U, c
     return loss, g, U
 
 

@@ -390,6 +390,47 @@ class Dnn:
                    "df_dnn_infer")
         return nfb.value, used_fallback, status
 
+    def grad(self, T, p, Y, Y_next, n_total: int | None = None, want_loss: bool = True, stream=None):
+        """Forward and backward pass without an update (df_dnn_grad): the
+        gradient of this batch's share of a loss averaged over n_total rows
+        (default: this batch) is left in grad_tensor().  Returns the loss share."""
+        torch = _torch()
+        n = T.numel()
+        loss = C.c_float()
+        _lib.check(_lib.load().df_dnn_grad(self._h, n, int(n_total if n_total is not None else n),
+                                           _dptr(T, "T", torch.float64), _dptr(p, "p"), _dptr(Y, "Y"),
+                                           _dptr(Y_next, "Y_next"), C.byref(loss) if want_loss else None,
+                                           _stream_ptr(stream)), "df_dnn_grad")
+        return loss.value if want_loss else None
+
+    def grad_tensor(self):
+        """The handle's FP32 gradient buffer as a CUDA tensor (no copy; valid
+        while the handle lives), for an in-place all-reduce between grad()
+        and adam_step()."""
+        torch = _torch()
+        ptr, cnt = C.c_void_p(), C.c_int64()
+        _lib.check(_lib.load().df_dnn_grad_buffer(self._h, C.byref(ptr), C.byref(cnt)), "df_dnn_grad_buffer")
+
+        class _Buf:
+            __cuda_array_interface__ = {"shape": (cnt.value,), "typestr": "<f4", "data": (ptr.value, False),
+                                        "version": 3, "strides": None}
+        return torch.as_tensor(_Buf(), device=torch.device("cuda", torch.cuda.current_device()))
+
+    def adam_step(self, lr: float, stream=None):
+        """One Adam step with the gradient in grad_tensor() (df_dnn_adam_step)."""
+        _lib.check(_lib.load().df_dnn_adam_step(self._h, float(lr), _stream_ptr(stream)), "df_dnn_adam_step")
+
+    def adam_state(self):
+        """(m1, m2, step): Adam's moment estimates (host float32) and step count."""
+        import numpy as np
+        m1 = np.zeros(self.n_params, np.float32)
+        m2 = np.zeros(self.n_params, np.float32)
+        st = C.c_int64()
+        _lib.check(_lib.load().df_dnn_get_adam_state(self._h, m1.ctypes.data_as(C.c_void_p),
+                                                     m2.ctypes.data_as(C.c_void_p), C.byref(st)),
+                   "df_dnn_get_adam_state")
+        return m1, m2, st.value
+
     def forward_raw(self, X, stream=None):
         """Network output U [n, 16] f32 for prepared bf16 features X [n, 16]."""
         torch = _torch()

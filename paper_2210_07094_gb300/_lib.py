@@ -69,6 +69,10 @@ SIGNATURES = [
     ("df_dnn_get_norm", _i, [_p, _p, _p, _p, _p, _p, _p]),
     ("df_dnn_fit_norm", _i, [_p, _i64, _p, _p, _p, _p, _p]),
     ("df_dnn_train_step", _i, [_p, _i64, _p, _p, _p, _p, C.c_float, _p, _p]),
+    ("df_dnn_grad", _i, [_p, _i64, _i64, _p, _p, _p, _p, _p, _p]),
+    ("df_dnn_grad_buffer", _i, [_p, _p, _p]),
+    ("df_dnn_adam_step", _i, [_p, C.c_float, _p]),
+    ("df_dnn_get_adam_state", _i, [_p, _p, _p, _p]),
     ("df_dnn_infer", _i, [_p, _p, _i64, _p, _p, _p, _d, _p, _p, _p, _p, _p]),
     ("df_dnn_forward_raw", _i, [_p, _i64, _p, _p, _p]),
     ("df_dnn_param_count", _i64, [_p]),

@@ -342,15 +342,17 @@ __global__ void k_dnn_zero_rows(__nv_bfloat16* X, __nv_bfloat16* XT, int64_t ldT
   }
 }
 
-// loss = mean over rows < n and outputs < N of (U - tgt)^2; dU = dloss/dU as
-// bf16 [rows][16] and its transpose [16][ldT]; per-block partial loss sums
-__global__ void k_dnn_loss(const float* U, const float* tgt, int64_t n, int64_t nrows, int N,
+// loss = sum over rows < n and outputs < N of (U - tgt)^2 / (n_norm N) (the
+// mean when n_norm = n; a shard's share of the mean over n_norm rows
+// otherwise); dU = dloss/dU as bf16 [rows][16] and its transpose [16][ldT];
+// per-block partial sums of the squared errors
+__global__ void k_dnn_loss(const float* U, const float* tgt, int64_t n, int64_t n_norm, int64_t nrows, int N,
                            __nv_bfloat16* dU, __nv_bfloat16* dUT, int64_t ldT, double* part) {
   __shared__ double red[256];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (i < nrows) {
-    const double scale = 2.0 / ((double)n * N);
+    const double scale = 2.0 / ((double)n_norm * N);
 #pragma unroll
     for (int k = 0; k < DNN_OUT; ++k) {
       float g = 0.0f;
@@ -437,10 +439,13 @@ struct PostArgs {
   int32_t* status;
   int32_t* list;
   unsigned long long* counter;
+  uint32_t inert;  // bit k: species k has a zero net stoichiometric coefficient in every reaction
 };
 
 // Stage 3 of the inference: Y' = F^{-1}(F(Y) + u), renormalised, and T' from
-// h(T', Y') = h(T, Y) at fixed p.
+// h(T', Y') = h(T, Y) at fixed p.  Species that no reaction changes (bits of
+// a.inert) keep their input mass fraction exactly, as the kinetics has it; the
+// others are scaled so that the mass fractions sum to one.
 //
 // Y' is formed as Y + dY.  With z = Y^lambda and r = lambda u / z, Y' = Y (1 + r)^m
 // (m = 1/lambda) exactly, so for |r| <= 1/2 dY = Y expm1(m log1p(r)) carries the
@@ -478,12 +483,17 @@ __global__ void k_dnn_post(PostArgs a) {
   const float lamf = (float)a.lam;
   const float m = (float)a.inv_lam;
   double Yo[DNN_OUT], Yn[DNN_OUT];
-  double s = 0.0;
+  double s = 0.0, s_inert = 0.0;
 #pragma unroll
   for (int k = 0; k < DNN_OUT; ++k) {
     if (k < a.N) {
       const double y = a.Y[(int64_t)k * a.ncells + c];
       Yo[k] = y;
+      if ((a.inert >> k) & 1u) {
+        Yn[k] = y;
+        s_inert += y;
+        continue;
+      }
       const float lu = lamf * fmaf(a.U[i * DNN_OUT + k], std_out[k], mean_out[k]);
       const float z = a.Yl[(int64_t)k * a.ldYl + i];
       double yn;
@@ -497,11 +507,12 @@ __global__ void k_dnn_post(PostArgs a) {
       s += yn;
     }
   }
-  // 1 / s: FP32 reciprocal and one Newton step (s is within rounding of 1)
+  // (1 - s_inert) / s: FP32 reciprocal of s and one Newton step (s is within
+  // rounding of 1 - s_inert, far from zero when the reacting species carry mass)
   double is = 0.0;
   if (s > 0.0) {
     const double r0 = (double)__frcp_rn((float)s);
-    is = r0 * fma(-s, r0, 2.0);
+    is = (1.0 - s_inert) * (r0 * fma(-s, r0, 2.0));
   }
   const double T0 = a.T[c];
   const float Tf = (float)T0;
@@ -510,7 +521,7 @@ __global__ void k_dnn_post(PostArgs a) {
 #pragma unroll
   for (int k = 0; k < DNN_OUT; ++k) {
     if (k < a.N) {
-      Yn[k] *= is;
+      if (!((a.inert >> k) & 1u)) Yn[k] *= is;
       const float yf = (float)Yn[k];
       const float dy = (float)(Yo[k] - Yn[k]);
       float hk = hc[k][5];
@@ -965,8 +976,9 @@ int df_dnn_fit_norm(df_dnn* d, int64_t n, const double* T, const double* p, cons
   return rc;
 }
 
-// The kernels of one training step on the staged batch (bT, bp, bY, bYn).
-static int dnn_train_enqueue(df_dnn* d, int64_t n, cudaStream_t st) {
+// The kernels of one forward and backward pass on the staged batch (bT, bp,
+// bY, bYn): the loss partials and the gradients (d->grads), no update.
+static int dnn_grad_enqueue(df_dnn* d, int64_t n, int64_t n_norm, cudaStream_t st) {
   const DnnLayout& L = d->L;
   const int64_t B = d->B;
   const int64_t M = (n + 7) / 8 * 8;  // rows used by the GEMMs (K of the weight gradients)
@@ -1005,7 +1017,7 @@ static int dnn_train_enqueue(df_dnn* d, int64_t n, cudaStream_t st) {
               nullptr, 0, nullptr, 0, st);
   if (rc) return rc;
   const int nbl = (int)((M + 255) / 256);
-  k_dnn_loss<<<nbl, 256, 0, st>>>(d->U, d->tgt, n, M, N, d->dU, d->dUT, B, d->loss_part);
+  k_dnn_loss<<<nbl, 256, 0, st>>>(d->U, d->tgt, n, n_norm, M, N, d->dU, d->dUT, B, d->loss_part);
   k_sum_partials<<<1, 32, 0, st>>>(d->loss_part, nbl, d->loss_part + nbl);
   // backward: layer 4
   rc = gemm(d, d->dUT, (int)B, d->HT[2], (int)B, DNN_OUT, L.w[2], (int)M, EPI_F32, nullptr, G + L.off[6], L.w[2],
@@ -1026,25 +1038,58 @@ static int dnn_train_enqueue(df_dnn* d, int64_t n, cudaStream_t st) {
       rc = gemm(d, d->dZ[l], 0, d->wtb[l], 0, (int)M, L.w[l - 1], L.w[l], EPI_BWD_DZ, nullptr, nullptr, 0,
                 d->dZ[l - 1], L.w[l - 1], d->dZT[l - 1], (int)B, d->Z[l - 1], L.w[l - 1], st);
   }
-  if (rc) return rc;
-  // Adam (bias-corrected) on the master weights, then the bf16 copies
+  return cuda_check(cudaGetLastError(), "gradient kernels");
+}
+
+// Adam (bias-corrected, scalars of this step in train_sc) on the master
+// weights with the gradients in d->grads, then the bf16 copies.
+static int dnn_adam_enqueue(df_dnn* d, cudaStream_t st) {
+  const DnnLayout& L = d->L;
   const float b1 = (float)d->o.beta1, b2 = (float)d->o.beta2;
-  k_adam<<<(unsigned)((L.total + 255) / 256), 256, 0, st>>>(P, d->m1, d->m2, G, L.total, d->train_sc, b1, b2,
-                                                             (float)d->o.adam_eps);
-  rc = cuda_check(cudaGetLastError(), "train step kernels");
+  k_adam<<<(unsigned)((L.total + 255) / 256), 256, 0, st>>>(d->params, d->m1, d->m2, d->grads, L.total,
+                                                             d->train_sc, b1, b2, (float)d->o.adam_eps);
+  int rc = cuda_check(cudaGetLastError(), "Adam kernel");
   if (!rc) rc = dnn_cast_all(d, st);
   return rc;
 }
 
-// the mean loss of the step, when asked for (synchronises the stream)
-static int train_step_loss(df_dnn* d, int64_t n, int rc, float* loss_out, cudaStream_t st) {
+// The kernels of one training step on the staged batch.
+static int dnn_train_enqueue(df_dnn* d, int64_t n, cudaStream_t st) {
+  int rc = dnn_grad_enqueue(d, n, n, st);
+  if (!rc) rc = dnn_adam_enqueue(d, st);
+  return rc;
+}
+
+// Copy a batch into the library's staging buffers (the captured training step
+// reads it from there).
+static int dnn_stage_batch(df_dnn* d, int64_t n, const double* T, const double* p, const double* Y,
+                           const double* Yn, cudaStream_t st) {
+  const int N = d->o.n_species;
+  int rc = cuda_check(cudaMemcpyAsync(d->bT, T, n * 8, cudaMemcpyDeviceToDevice, st), "stage T");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bp, p, n * 8, cudaMemcpyDeviceToDevice, st), "stage p");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bY, Y, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bYn, Yn, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y_next");
+  return rc;
+}
+
+// this step's Adam scalars: lr and the bias corrections 1 - beta^t (t = d->step)
+static int dnn_set_step_scalars(df_dnn* d, float lr, cudaStream_t st) {
+  const float c1 = (float)(1.0 - std::pow(d->o.beta1, (double)d->step));
+  const float c2 = (float)(1.0 - std::pow(d->o.beta2, (double)d->step));
+  k_set_train_scalars<<<1, 1, 0, st>>>(d->train_sc, lr, c1, c2);
+  return cuda_check(cudaGetLastError(), "train scalars");
+}
+
+// the loss of the step (squared errors over n_norm * N), when asked for
+// (synchronises the stream)
+static int train_step_loss(df_dnn* d, int64_t n, int64_t n_norm, int rc, float* loss_out, cudaStream_t st) {
   if (!rc && loss_out) {
     const int64_t M = (n + 7) / 8 * 8;
     const int nbl = (int)((M + 255) / 256);
     double l = 0.0;
     rc = cuda_check(cudaMemcpyAsync(&l, d->loss_part + nbl, 8, cudaMemcpyDeviceToHost, st), "read loss");
     if (!rc) rc = check_err_flag(d, st);
-    *loss_out = (float)(l / ((double)n * d->o.n_species));
+    *loss_out = (float)(l / ((double)n_norm * d->o.n_species));
   }
   return rc;
 }
@@ -1055,19 +1100,10 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
     return set_error(DF_EINVAL, "df_dnn_train_step: bad arguments (1 <= n <= batch)");
   cudaStream_t st = (cudaStream_t)stream;
   int rc = dnn_train_buffers(d);
-  if (rc) return rc;
-  const int N = d->o.n_species;
-  // stage the batch and this step's scalars
-  rc = cuda_check(cudaMemcpyAsync(d->bT, T, n * 8, cudaMemcpyDeviceToDevice, st), "stage T");
-  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bp, p, n * 8, cudaMemcpyDeviceToDevice, st), "stage p");
-  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bY, Y, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y");
-  if (!rc) rc = cuda_check(cudaMemcpyAsync(d->bYn, Yn, n * N * 8, cudaMemcpyDeviceToDevice, st), "stage Y_next");
+  if (!rc) rc = dnn_stage_batch(d, n, T, p, Y, Yn, st);
   if (rc) return rc;
   d->step += 1;
-  const float c1 = (float)(1.0 - std::pow(d->o.beta1, (double)d->step));
-  const float c2 = (float)(1.0 - std::pow(d->o.beta2, (double)d->step));
-  k_set_train_scalars<<<1, 1, 0, st>>>(d->train_sc, lr, c1, c2);
-  rc = cuda_check(cudaGetLastError(), "train scalars");
+  rc = dnn_set_step_scalars(d, lr, st);
   if (rc) return rc;
   // The step's ~25 launches are captured once per batch size, on a private
   // stream (the caller's may be the legacy stream, which cannot be captured),
@@ -1078,7 +1114,7 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
   rc = cuda_check(cudaStreamIsCapturing(st, &cs), "capture status");
   if (rc) return rc;
   if (cs != cudaStreamCaptureStatusNone || d->step == 1 || d->no_graph)
-    return train_step_loss(d, n, dnn_train_enqueue(d, n, st), loss_out, st);
+    return train_step_loss(d, n, n, dnn_train_enqueue(d, n, st), loss_out, st);
   if (!d->train_exec || d->train_n != n) {
     if (d->train_exec) cudaGraphExecDestroy(d->train_exec);
     d->train_exec = nullptr;
@@ -1089,7 +1125,7 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
     if (cudaStreamBeginCapture(d->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
       cudaGetLastError();
       d->no_graph = true;  // capture unavailable: run the kernels as they are from now on
-      return train_step_loss(d, n, dnn_train_enqueue(d, n, st), loss_out, st);
+      return train_step_loss(d, n, n, dnn_train_enqueue(d, n, st), loss_out, st);
     }
     const int erc = dnn_train_enqueue(d, n, d->cap_stream);
     cudaGraph_t g = nullptr;
@@ -1104,7 +1140,45 @@ int df_dnn_train_step(df_dnn* d, int64_t n, const double* T, const double* p, co
     d->train_n = n;
   }
   rc = cuda_check(cudaGraphLaunch(d->train_exec, st), "launch training graph");
-  return train_step_loss(d, n, rc, loss_out, st);
+  return train_step_loss(d, n, n, rc, loss_out, st);
+}
+
+int df_dnn_grad(df_dnn* d, int64_t n, int64_t n_total, const double* T, const double* p, const double* Y,
+                const double* Yn, float* loss_out, df_stream_t stream) {
+  if (!d || n < 1 || n > d->o.batch || n_total < n || !T || !p || !Y || !Yn)
+    return set_error(DF_EINVAL, "df_dnn_grad: bad arguments (1 <= n <= batch, n_total >= n)");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = dnn_train_buffers(d);
+  if (!rc) rc = dnn_stage_batch(d, n, T, p, Y, Yn, st);
+  if (!rc) rc = dnn_grad_enqueue(d, n, n_total, st);
+  return train_step_loss(d, n, n_total, rc, loss_out, st);
+}
+
+int df_dnn_grad_buffer(df_dnn* d, float** grads, int64_t* count) {
+  if (!d || !grads) return set_error(DF_EINVAL, "df_dnn_grad_buffer: bad arguments");
+  *grads = d->grads;
+  if (count) *count = d->L.total;
+  return DF_OK;
+}
+
+int df_dnn_adam_step(df_dnn* d, float lr, df_stream_t stream) {
+  if (!d) return set_error(DF_EINVAL, "df_dnn_adam_step: null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = dnn_train_buffers(d);
+  if (rc) return rc;
+  d->step += 1;
+  rc = dnn_set_step_scalars(d, lr, st);
+  if (!rc) rc = dnn_adam_enqueue(d, st);
+  return rc;
+}
+
+int df_dnn_get_adam_state(const df_dnn* d, float* m1, float* m2, int64_t* step) {
+  if (!d) return set_error(DF_EINVAL, "df_dnn_get_adam_state: null handle");
+  int rc = DF_OK;
+  if (m1) rc = cuda_check(cudaMemcpy(m1, d->m1, d->L.total * 4, cudaMemcpyDeviceToHost), "read first moments");
+  if (!rc && m2) rc = cuda_check(cudaMemcpy(m2, d->m2, d->L.total * 4, cudaMemcpyDeviceToHost), "read second moments");
+  if (step) *step = d->step;
+  return rc;
 }
 
 int df_dnn_forward_raw(df_dnn* d, int64_t n, const void* X, float* U, df_stream_t stream) {
@@ -1167,6 +1241,9 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
   if (!rc) rc = cuda_check(cudaEventRecord(d->ev_fallback, d->side), "event");
   // 3. the network on the other cells, chunk by chunk
   const int inv = (int)std::lround(1.0 / d->o.lambda);
+  uint32_t inert = 0;  // species with an empty (reaction, net nu) list
+  for (int k = 0; k < m->dims.N && k < 32; ++k)
+    if (m->csr_host[k + 1] == m->csr_host[k]) inert |= 1u << k;
   for (int64_t c0 = 0; c0 < ncells && !rc; c0 += d->chunk) {
     const int64_t nc = std::min<int64_t>(d->chunk, ncells - c0);
     FeatInferArgs fa;
@@ -1206,6 +1283,7 @@ int df_dnn_infer(df_dnn* d, const df_mech* mc, int64_t ncells, double* T, const 
     pa.ldYl = d->chunk;
     pa.used_fallback = used_fallback;
     pa.status = status;
+    pa.inert = inert;
     k_dnn_post<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(pa);
     rc = cuda_check(cudaGetLastError(), "DNN pre/post kernels");
   }

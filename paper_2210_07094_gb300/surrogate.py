@@ -17,6 +17,48 @@ import numpy as np
 
 from . import Dnn, Mechanism, dnn_default_opts, integrate, synth
 
+# Acceptance bound of the learned integrator against the FP64 integrator on
+# held-out states (the paper gives none; Sec. 4 compares DNN and CVODE results
+# by eye): for every species, the mean absolute error of Y(t + dt) is at most
+# this fraction of the mean absolute change the integrator makes over dt, the
+# same for T; species that no reaction changes are exact.
+ERROR_BOUND = 0.10
+
+
+def inert_mask(mech_json: dict) -> np.ndarray:
+    """Species whose net stoichiometric coefficient is zero in every reaction
+    (their mass fraction cannot change)."""
+    names = [sp["name"] for sp in mech_json["species"]]
+    moves = np.zeros(len(names), bool)
+    for r in mech_json["reactions"]:
+        net = dict.fromkeys(names, 0)
+        for name, c in r["reactants"].items():
+            net[name] -= c
+        for name, c in r["products"].items():
+            net[name] += c
+        for k, name in enumerate(names):
+            moves[k] |= net[name] != 0
+    return ~moves
+
+
+def element_matrix(mech_json: dict) -> np.ndarray:
+    """[elements, species]: atoms of each element per unit mass of each
+    species, a_ek / W_k (mol/g)."""
+    elems = sorted({e for sp in mech_json["species"] for e in sp["composition"]})
+    return np.array([[sp["composition"].get(e, 0) / sp["W"] for sp in mech_json["species"]] for e in elems])
+
+
+def within_bound(ev: dict, inert, bound: float = ERROR_BOUND) -> dict:
+    """Check an evaluate() result against the acceptance bound; returns the
+    per-species ratios and ok."""
+    inert = np.asarray(inert, bool)
+    ratio = ev["mae_Y"] / np.maximum(ev["frozen_mae_Y"], 1e-300)
+    ok_species = np.where(inert, ev["max_Y"] == 0.0, ratio <= bound)
+    ratio_T = ev["mae_T"] / max(ev["frozen_mae_T"], 1e-300)
+    return {"ok": bool(ok_species.all() and ratio_T <= bound), "bound": bound,
+            "mae_ratio_per_species": [float(x) for x in ratio], "inert_exact": bool(np.all(ev["max_Y"][inert] == 0)),
+            "mae_ratio_T": float(ratio_T), "species_ok": [bool(x) for x in ok_species]}
+
 
 def trajectories(mech: Mechanism, mech_json: dict, n_init: int, n_steps: int, dt: float = 1e-6,
                  seed: int = synth.TRAIN_SEED, device="cuda"):
@@ -83,10 +125,12 @@ def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, 
     return losses
 
 
-def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6):
+def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6, mech_json: dict | None = None):
     """Per-species error of the network against the integrator on the same states
     (in-range cells only), and the error of a frozen composition (Y(t+dt) = Y(t))
-    for scale."""
+    for scale.  With mech_json, also the element conservation of both results:
+    the largest relative change over the cells of each element's moles per
+    unit mass (the frozen composition conserves them exactly)."""
     import torch
     Ti, Yi = T.clone(), Y.clone()
     st, _ = integrate(mech, Ti, p, Yi, dt)
@@ -102,7 +146,16 @@ def evaluate(dnn: Dnn, mech: Mechanism, T, p, Y, dt=1e-6):
     du_p = (bct(Yd) - bct(Y))[:, ok]
     var = du_t.var(dim=1)
     r2 = 1.0 - ((du_p - du_t) ** 2).mean(dim=1) / torch.where(var > 0, var, torch.ones_like(var))
+    extra = {}
+    if mech_json is not None:
+        A = torch.tensor(element_matrix(mech_json), device=T.device)
+        b0 = A @ Y[:, ok]
+        den = torch.clamp(b0.abs(), min=1e-300)
+        extra["element_imbalance_dnn"] = ((A @ (Yd[:, ok] - Y[:, ok])).abs() / den).max(dim=1).values.cpu().numpy()
+        extra["element_imbalance_integrator"] = \
+            ((A @ (Yi[:, ok] - Y[:, ok])).abs() / den).max(dim=1).values.cpu().numpy()
     return {
+        **extra,
         "r2_dF": r2.cpu().numpy(), "var_dF": var.cpu().numpy(),
         "n": int(T.numel()), "n_network": int(ok.sum()), "n_fallback": int(nfb),
         "mae_Y": err_Y.mean(dim=1).cpu().numpy(), "max_Y": err_Y.max(dim=1).values.cpu().numpy(),
@@ -174,7 +227,8 @@ def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22
     Te, Pe, Ye, n_oor = heldout(m, mech_json, dnn, n_eval, n_steps, oor_frac, seed)
     n_eval = Te.numel()
     # accuracy: network vs integrator on the same states
-    ev = evaluate(dnn, m, Te, Pe, Ye)
+    ev = evaluate(dnn, m, Te, Pe, Ye, mech_json=mech_json)
+    bound = within_bound(ev, inert_mask(mech_json))
     # throughput: network (incl. pre/post and fallback) and integrator, same cells
     Tw, Yw = Te.clone(), Ye.clone()
 
@@ -215,6 +269,13 @@ def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22
             "mae_T_K": ev["mae_T"], "max_T_K": ev["max_T"],
             "r2_dF_mean_reacting": float(np.mean(r2)) if r2.size else None,
             "frozen_composition_mae_Y": [float(x) for x in ev["frozen_mae_Y"]],
+            "frozen_composition_mae_T_K": ev["frozen_mae_T"],
+            "bound": bound,
+            "element_imbalance_max_rel": {
+                "dnn": [float(x) for x in ev["element_imbalance_dnn"]],
+                "integrator": [float(x) for x in ev["element_imbalance_integrator"]],
+                "frozen_composition": 0.0,
+                "elements": sorted({e for sp in mech_json["species"] for e in sp["composition"]})},
         },
         "integrator_substeps_per_cell": (acc + rej) / n_eval,
     }

@@ -39,9 +39,18 @@ def test_forward_matches_oracle(widths, rows):
     U = dnn.forward_raw(X).cpu().numpy()
     Uo, _ = mlp.forward(P, X.float().cpu().numpy(), emulate=True)
     scale = np.abs(Uo[:, :9]).max()
-    d = np.abs(U[:, :9] - Uo[:, :9])
-    assert d.max() <= 1e-2 * scale, (d.max(), scale)
-    assert d.mean() <= 1e-3 * scale
+    d = np.abs(U[:, :9] - Uo[:, :9]) / scale
+    # Same rounding points on both sides: the outputs differ only where an FP32
+    # accumulation-order difference flips a BF16 rounding of a hidden
+    # activation upstream (one BF16 ulp, 2^-8 relative, of one term of the
+    # next layer's sums).  Bounds: the largest difference, and the share of
+    # outputs touched by a flip at all (above the FP32 accumulation noise).
+    touched = float(np.mean(d > 1e-5))
+    print({"widths": widths, "rows": rows, "max": float(d.max()), "median": float(np.median(d)),
+           "touched": touched})
+    assert d.max() <= 1e-3, d.max()
+    assert np.median(d) <= 1e-5
+    assert touched <= 0.25
 
 
 @pytest.fixture(scope="module")
@@ -72,11 +81,30 @@ def test_train_step_gradients_match_oracle(data):
     du = ((np.maximum(Yn1.T, 0) ** 0.1) - (np.maximum(Yn0.T, 0) ** 0.1)) / 0.1
     tgt = np.zeros((n, 16))
     tgt[:, :9] = (du - norm["mean_out"][:9]) / norm["std_out"][:9]
-    lo, go, _ = mlp.loss_and_grads(mlp.unpack(params0, widths), x, tgt, 9, emulate=True)
+    lo, go, _, cache = mlp.loss_and_grads(mlp.unpack(params0, widths), x, tgt, 9, emulate=True,
+                                          return_cache=True)
     assert abs(loss - lo) <= 2e-3 * lo
-    for name, _ in mlp.layout(widths):
-        a, b = g[name], go[name]
-        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-12, name
+    # Element by element, each weight gradient against the scale of its own
+    # sum: dW_l[i, j] = sum_r dZ_l[r, i] H_{l-1}[r, j], S = sum_r |dZ_l| |H_{l-1}|.
+    # The two sides agree up to FP32 accumulation order and the BF16 rounding
+    # flips it causes upstream (each flip moves one term by 2^-8 of itself).
+    worst = {}
+    for l in (1, 2, 3, 4):
+        dZ, H = np.abs(cache[f"dZ{l}"]), np.abs(cache[f"H{l - 1}"])
+        SW = dZ.T @ H
+        Sb = dZ.sum(axis=0)
+        for name, S in ((f"W{l}", SW), (f"b{l}", Sb)):
+            err = np.abs(g[name] - go[name])
+            ok = err <= 2 ** -7 * S + 1e-9 * S.max()
+            worst[name] = float((err / (S + 1e-300)).max())
+            assert ok.all(), (name, worst[name], int((~ok).sum()))
+            # and relative to the gradient itself where it is not a cancellation
+            big = np.abs(go[name]) >= 0.1 * S
+            if big.any():
+                rel = err[big] / np.abs(go[name][big])
+                worst[name + "_rel"] = float(rel.max())
+                assert np.median(rel) <= 1e-3, (name, float(np.median(rel)))
+    print(worst)
 
 
 # small widths, and the full 1600-800-400 network (its layers take the
@@ -107,9 +135,11 @@ def test_infer_pipeline_and_fallback(data, widths):
             "mean_out": np.r_[nm["mean_out"], np.zeros(7)], "std_out": np.r_[nm["std_out"], np.ones(7)]}
     _, x = mlp.features(f["T"][net], f["p"][net], f["Y"][:, net], 0.1, norm, 9)
     U, _ = mlp.forward(mlp.unpack(dnn.params(), widths), x.astype(np.float32), emulate=True)
-    To, Yo = mlp.post(f["T"][net], f["p"][net], f["Y"][:, net], U, 0.1, norm, 9, o.nasa, o.W)
+    inert = mlp.inert_species(mech)
+    To, Yo = mlp.post(f["T"][net], f["p"][net], f["Y"][:, net], U, 0.1, norm, 9, o.nasa, o.W, inert=inert)
     Yg = Y.cpu().numpy()[:, net]
     assert np.allclose(Yg.sum(axis=0), 1.0, rtol=1e-13)
+    assert inert.sum() == 1 and np.array_equal(Yg[inert], f["Y"][inert][:, net])  # N2 untouched
     # same network, same rounding points: differences only where an FP32 / BF16
     # rounding decision flips between the two accumulation orders
     err = np.abs(Yg - Yo).max(axis=0) / (np.abs(Yo - f["Y"][:, net]).max() + 1e-300)
@@ -146,7 +176,8 @@ def test_post_resolves_small_changes(data):
     assert len(net) > 0.9 * len(sel)
     U = np.tile(w["b4"].astype(np.float32), (len(net), 1)).astype(np.float64)
     norm = {"mean_out": np.r_[nm["mean_out"], np.zeros(7)], "std_out": np.r_[nm["std_out"], np.ones(7)]}
-    To, Yo = mlp.post(Th[net], ph[net], Yh[:, net], U, 0.1, norm, 9, o.nasa, o.W)
+    To, Yo = mlp.post(Th[net], ph[net], Yh[:, net], U, 0.1, norm, 9, o.nasa, o.W,
+                      inert=mlp.inert_species(mech))
     Yg, Tg = Y.cpu().numpy()[:, net], T.cpu().numpy()[net]
     dY = np.abs(Yo - Yh[:, net])
     assert dY.max() > 0
@@ -177,3 +208,117 @@ def test_short_training_learns_the_map(data):
     assert ev["n_network"] > 0
     reacting = ev["var_dF"] > 0
     assert np.mean(ev["r2_dF"][reacting]) > 0.5, ev["r2_dF"]
+
+
+def test_adam_steps_match_oracle(data):
+    """Two training steps with lr > 0: the FP32 parameters and both moment
+    estimates after each step against the oracle's Adam (Kingma & Ba,
+    Algorithm 1, FP64) applied to the step's own gradient and the state the
+    GPU held before the step."""
+    mech, m, (T0, P, Y0, T1, Y1) = data
+    widths = (64, 32, 16)
+    dnn = df.Dnn(_opts(widths, batch=512), seed=4)
+    dnn.fit_norm(T0, P, Y0, Y1)
+    n, lr = 512, 3e-3
+    theta = dnn.params().astype(np.float64)
+    m1, m2, t = (a.astype(np.float64) if isinstance(a, np.ndarray) else a for a in dnn.adam_state())
+    assert t == 0 and not m1.any() and not m2.any()
+    for step in (1, 2):
+        sl = slice((step - 1) * n, step * n)
+        dnn.train_step(T0[sl].contiguous(), P[sl].contiguous(), Y0[:, sl].contiguous(), Y1[:, sl].contiguous(), lr)
+        g = dnn.grads().astype(np.float64)
+        th_o, m_o, v_o = mlp.adam_step(theta, m1, m2, g, step, lr)
+        theta = dnn.params().astype(np.float64)
+        a, b, t = dnn.adam_state()
+        m1, m2 = a.astype(np.float64), b.astype(np.float64)
+        assert t == step
+        assert np.all(np.abs(m1 - m_o) <= 1e-6 * np.abs(m_o) + 1e-30), np.max(np.abs(m1 - m_o) / (np.abs(m_o) + 1e-30))
+        assert np.all(np.abs(m2 - v_o) <= 1e-6 * np.abs(v_o) + 1e-38), np.max(np.abs(m2 - v_o) / (np.abs(v_o) + 1e-38))
+        # FP32 parameter: one rounding of theta (half an ulp) plus the FP32
+        # update's few roundings (relative 1e-6 of a step of size ~lr)
+        tol = 2.0 ** -23 * np.abs(th_o) + 1e-6 * lr
+        err = np.abs(theta - th_o)
+        assert np.all(err <= tol), (step, float(np.max(err / tol)))
+        assert np.max(np.abs(theta - th_o)) < 0.1 * lr
+
+
+def test_gradient_halves_sum_to_the_union_gradient(data):
+    """df_dnn_grad on two shards of a batch, each normalised by the whole batch,
+    sums to the gradient of one pass over the union (FP32 summation order
+    only: every row's output gradient is rounded to BF16 identically); then
+    df_dnn_adam_step on the summed buffer gives the parameters of
+    df_dnn_train_step on the union."""
+    mech, m, (T0, P, Y0, T1, Y1) = data
+    widths = (64, 32, 16)
+    n = 512
+    args = [a[..., :n].contiguous() for a in (T0, P, Y0, Y1)]
+    ref = df.Dnn(_opts(widths, batch=512), seed=9)
+    ref.fit_norm(T0, P, Y0, Y1)
+    p0 = ref.params()
+    lu = ref.grad(*args)
+    g_union = ref.grad_tensor().clone()
+    acc = torch.zeros_like(g_union)
+    ls = 0.0
+    for lo, hi in ((0, 200), (200, n)):
+        ls += ref.grad(*[a[..., lo:hi].contiguous() for a in args], n_total=n)
+        acc += ref.grad_tensor()
+    assert abs(ls - lu) <= 1e-5 * lu
+    scale = g_union.abs().max().item()
+    assert torch.max(torch.abs(acc - g_union)).item() <= 1e-5 * scale
+    # the split step on the summed gradient equals the fused step
+    ref.grad_tensor().copy_(acc)
+    ref.adam_step(1e-3)
+    p_split = ref.params()
+    fused = df.Dnn(_opts(widths, batch=512), seed=9)
+    fused.fit_norm(T0, P, Y0, Y1)
+    assert np.array_equal(fused.params(), p0)
+    fused.train_step(*args, lr=1e-3)
+    assert np.max(np.abs(p_split - fused.params())) <= 1e-6 * 1e-3 + 2 ** -22 * np.abs(p0).max()
+
+
+def _element_imbalance(mech, Y0, Y1):
+    """Largest relative change of the element mass per unit mass (moles of each
+    element per kg), over cells: |sum_k a_ek (Y1_k - Y0_k) / W_k| /
+    sum_k a_ek Y0_k / W_k."""
+    names = [s["name"] for s in mech["species"]]
+    elems = sorted({e for s in mech["species"] for e in s["composition"]})
+    A = np.array([[s["composition"].get(e, 0) / s["W"] for s in mech["species"]] for e in elems])
+    b0 = A @ Y0
+    return np.max(np.abs(A @ (Y1 - Y0)) / np.maximum(b0, 1e-300), axis=0), names
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """The full 11-1600-800-400-9 network trained for 20 s on integrator pairs
+    of the uneven-stiffness field (2^14 trajectories x 16 steps)."""
+    mech = synth.h2_air_mechanism()
+    m = df.Mechanism(mech)
+    Ts, p, Ys = surrogate.trajectories(m, mech, 1 << 14, 16)
+    T0, P0, Y0, T1, Y1 = surrogate.pairs(Ts, p, Ys)
+    del Ts, Ys
+    o = df.dnn_default_opts()
+    dnn = df.Dnn(o, seed=22)
+    dnn.fit_norm(T0, P0, Y0, Y1)
+    surrogate.train(dnn, T0, P0, Y0, Y1, epochs=10_000, batch=4096, time_budget=20.0)
+    return mech, m, dnn
+
+
+def test_dnn_error_within_the_stated_per_species_bound(trained):
+    """On 2^16 held-out trajectory states (no out-of-range cells): for every
+    species the network's mean absolute error in Y(t + dt) against the FP64
+    integrator is at most surrogate.ERROR_BOUND (10%) of the mean absolute
+    change the integrator makes; the inert species is exact; the mean error in
+    T is within the same fraction of the mean temperature change."""
+    mech, m, dnn = trained
+    Ts, p, Ys = surrogate.trajectories(m, mech, 1 << 12, 16, seed=4242)
+    T = torch.cat(Ts[1:]).contiguous()
+    Y = torch.cat(Ys[1:], dim=1).contiguous()
+    P = p.repeat(len(Ts) - 1).contiguous()
+    assert T.numel() >= 1 << 16
+    ev = surrogate.evaluate(dnn, m, T, P, Y, mech_json=mech)
+    print({k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in ev.items() if k in
+           ("mae_Y", "frozen_mae_Y", "max_Y", "mae_T", "frozen_mae_T", "n_fallback", "element_imbalance_dnn",
+            "element_imbalance_integrator")})
+    assert ev["n_network"] >= 0.95 * ev["n"]
+    check = surrogate.within_bound(ev, surrogate.inert_mask(mech))
+    assert check["ok"], check
