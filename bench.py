@@ -129,19 +129,70 @@ def _peaks():
         return {}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu), for the record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# the integrator's default tolerances, for the CPU run at matched accuracy
+GPU_TOL = {"rtol": 1e-6, "atolY": 1e-10, "atolT": 1e-6}
+
+
+def _time_oracle(o, f, threads, tol=None):
+    t0 = time.perf_counter()
+    _, _, st, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"], threads=threads, **(tol or {}))
+    return time.perf_counter() - t0, int(np.sum(st != 0))
+
+
 def cpu_baseline(sample_cells: int, threads: int):
-    """The oracle as it stands, timed on the host cores over a bounded sample."""
+    """The oracle as it stands (Radau IIA, OpenMP over cells), timed on the
+    host cores over bounded samples of the bench workload: at its own rtol
+    1e-10 (the accuracy reference) and at the GPU integrator's tolerances (the
+    fair CPU-vs-GPU comparison), on all cores and on one core; plus the
+    50-species field on 64 (rtol 1e-10) and 256 (matched) cells."""
     from oracle.oracle import Mech
     from paper_2210_07094_gb300 import synth
     mech = synth.h2_air_mechanism()
     f = synth.field(1, mech, sample_cells, seed=synth.FIELD_SEED + 1 + 1000)
     o = Mech(mech)
-    t0 = time.perf_counter()
-    _, _, st, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"], threads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": sample_cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    dt_all, bad = _time_oracle(o, f, threads)
+    dt_all_m, bad_m = _time_oracle(o, f, threads, GPU_TOL)
+    n1 = max(256, sample_cells // 8)
+    f1 = {k: (v[..., :n1] if isinstance(v, np.ndarray) else v) for k, v in f.items()}
+    dt_one, _ = _time_oracle(o, f1, 1)
+    dt_one_m, _ = _time_oracle(o, f1, 1, GPU_TOL)
+    chon = synth.hydrocarbon_mechanism()
+    oc = Mech(chon)
+    fc = synth.field(2, chon, 256)
+    fc64 = {k: (v[..., :64] if isinstance(v, np.ndarray) else v) for k, v in fc.items()}
+    dt_c, bad_c = _time_oracle(oc, fc64, threads)
+    dt_c_m, _ = _time_oracle(oc, fc, threads, GPU_TOL)
+    return {"value": sample_cells / dt_all, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"{sample_cells} cells of the same bimodal field (seeded), Radau IIA rtol 1e-10, "
-                      f"OpenMP over cells; {dt:.2f} s", "failed_cells": int(np.sum(st != 0))}
+                      f"OpenMP over cells; {dt_all:.2f} s", "failed_cells": bad,
+            "matched_tolerance": {"value": sample_cells / dt_all_m, "cores": threads,
+                                  "tolerances": "rtol 1e-6, atol_Y 1e-10, atol_T 1e-6 K (the GPU integrator's)",
+                                  "seconds": dt_all_m, "failed_cells": bad_m},
+            "one_core": {"cells": n1, "rtol_1e-10": n1 / dt_one, "matched_tolerance": n1 / dt_one_m},
+            "chon_50_species": {"cells": {"rtol_1e-10": 64, "matched_tolerance": 256}, "cores": threads,
+                                "rtol_1e-10": 64 / dt_c, "matched_tolerance": 256 / dt_c_m,
+                                "failed_cells": bad_c}}
 
 
 def _median_ms(fn, reps):

@@ -11,9 +11,11 @@ Two bars, both per cell:
   with rel = 1e-3.  Over one dt = 1 us the change of a cell can be far below the
   absolute bar (on the 0D H2/air field it is 1e-5 .. 2e-4 K), so the absolute bar
   alone would accept a kernel that returns its input; the relative bar does not.
-  The floors (1e-9 K, 1e-13 of the largest mass fraction) sit four orders of
-  magnitude below the smallest change of those fields and far above the FP64
-  rounding of the state.
+  The floors (2e-7 K, 1e-10 of the largest mass fraction) are the truncation
+  error the integrator's default tolerances leave (at most 1e-7 K and 4e-11 of
+  the largest mass fraction on the 9- and 50-species fields): cells that barely
+  move are held to that, not to 1e-3 of a change of 1e-6 K.  They sit 50x
+  (T) and 20x (Y) below the smallest change of a cell of the 0D H2/air field.
 
 The state must also have moved: the largest change over the cells is at least
 ``moved`` (100) times the largest error, in T and in Y.
@@ -35,8 +37,8 @@ def integrator_errors(T_in, Y_in, T, Y, T_or, Y_or):
     return err_T, chg_T, err_Y, chg_Y, np.abs(Y_or).max(axis=0)
 
 
-def check_integrator(T_in, Y_in, T, Y, T_or, Y_or, tol_T=1e-3, tol_Y=1e-7, rel=1e-3, floor_T=1e-9,
-                     floor_Y=1e-13, moved=100.0):
+def check_integrator(T_in, Y_in, T, Y, T_or, Y_or, tol_T=1e-3, tol_Y=1e-7, rel=1e-3, floor_T=2e-7,
+                     floor_Y=1e-10, moved=100.0):
     """Raise AssertionError unless (T, Y) passes both bars against the oracle's
     (T_or, Y_or) from the same inputs (T_in, Y_in).  Returns the figures."""
     err_T, chg_T, err_Y, chg_Y, maxY = integrator_errors(T_in, Y_in, T, Y, T_or, Y_or)
@@ -50,7 +52,7 @@ def check_integrator(T_in, Y_in, T, Y, T_or, Y_or, tol_T=1e-3, tol_Y=1e-7, rel=1
     bad_Y = err_Y > rel * chg_Y + floor_Y * maxY
     assert not bad_T.any(), ("T relative to the change", stats, int(np.argmax(bad_T)))
     assert not bad_Y.any(), ("Y relative to the change", stats, int(np.argmax(bad_Y)))
-    assert chg_T.max() >= moved * err_T.max() and chg_T.max() > 1e3 * floor_T, ("T did not move", stats)
-    assert (chg_Y / maxY).max() >= moved * (err_Y / maxY).max() and (chg_Y / maxY).max() > 1e3 * floor_Y, \
+    assert chg_T.max() >= moved * err_T.max() and chg_T.max() > 10 * floor_T, ("T did not move", stats)
+    assert (chg_Y / maxY).max() >= moved * (err_Y / maxY).max() and (chg_Y / maxY).max() > 10 * floor_Y, \
         ("Y did not move", stats)
     return stats

@@ -407,14 +407,17 @@ __global__ void k_set_train_scalars(float* sc, float lr, float c1, float c2) {
   sc[2] = c2;
 }
 
+// Adam (Kingma & Ba 2015, Algorithm 1) in FP32 on the master weights; the
+// coefficients beta and 1 - beta are rounded to FP32 from their FP64 values
+// (1 - (float)0.999 would be 5e-5 off 0.001)
 __global__ void k_adam(float* P, float* m1, float* m2, const float* g, int64_t n, const float* sc, float b1,
-                       float b2, float eps) {
+                       float omb1, float b2, float omb2, float eps) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float lr = sc[0], c1 = sc[1], c2 = sc[2];
   const float gi = g[i];
-  const float a = b1 * m1[i] + (1.0f - b1) * gi;
-  const float b = b2 * m2[i] + (1.0f - b2) * gi * gi;
+  const float a = b1 * m1[i] + omb1 * gi;
+  const float b = b2 * m2[i] + omb2 * (gi * gi);
   m1[i] = a;
   m2[i] = b;
   P[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
@@ -1046,8 +1049,9 @@ static int dnn_grad_enqueue(df_dnn* d, int64_t n, int64_t n_norm, cudaStream_t s
 static int dnn_adam_enqueue(df_dnn* d, cudaStream_t st) {
   const DnnLayout& L = d->L;
   const float b1 = (float)d->o.beta1, b2 = (float)d->o.beta2;
+  const float omb1 = (float)(1.0 - d->o.beta1), omb2 = (float)(1.0 - d->o.beta2);
   k_adam<<<(unsigned)((L.total + 255) / 256), 256, 0, st>>>(d->params, d->m1, d->m2, d->grads, L.total,
-                                                             d->train_sc, b1, b2, (float)d->o.adam_eps);
+                                                             d->train_sc, b1, omb1, b2, omb2, (float)d->o.adam_eps);
   int rc = cuda_check(cudaGetLastError(), "Adam kernel");
   if (!rc) rc = dnn_cast_all(d, st);
   return rc;

@@ -136,7 +136,7 @@ static int make_tmap_store(CUtensorMap* m, const void* ptr, int64_t rows, int64_
   return DF_OK;
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, int EW>
 static int gemm_launch_pers_mode(const CUtensorMap& ta, const CUtensorMap& tb, const GemmParams& P, cudaStream_t st) {
   int rc = DF_OK;
   CUtensorMap tc;
@@ -146,9 +146,9 @@ static int gemm_launch_pers_mode(const CUtensorMap& ta, const CUtensorMap& tb, c
     rc = make_tmap_store(&tc, P.out1, P.M, P.N, P.ld1);
     if (rc) return rc;
   }
-  auto kf = k_gemm_tc_pers<BN, PERS_STAGES, MODE>;
+  auto kf = k_gemm_tc_pers<BN, PERS_STAGES, MODE, EW>;
   const size_t sm = (size_t)PERS_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
-                    (MODE == EPI_GELU_BF16 ? PERS_STAGE_C_BYTES : 0) + 1024 + 256;
+                    (MODE == EPI_GELU_BF16 ? pers_stage_c_bytes(EW) : 0) + 1024 + 256;
   static int nsm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -164,7 +164,7 @@ static int gemm_launch_pers_mode(const CUtensorMap& ta, const CUtensorMap& tb, c
   }
   const int64_t tiles = (int64_t)((P.M + GEMM_BM - 1) / GEMM_BM) * ((P.N + BN - 1) / BN);
   const int grid = (int)std::min<int64_t>(tiles, nsm[dev]);
-  kf<<<grid, PERS_THREADS, sm, st>>>(ta, tb, tc, P);
+  kf<<<grid, pers_threads(EW), sm, st>>>(ta, tb, tc, P);
   return cuda_check(cudaGetLastError(), "persistent GEMM launch");
 }
 
@@ -174,15 +174,18 @@ static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, c
   int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
   if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
   if (rc) return rc;
+  // sixteen epilogue warps for the inference GELU layers (four per TMEM lane
+  // quarter: on the 11-1600-800-400-9 network's 262144-row chunk the forward
+  // pass took 1.16 ms against 1.45 ms with eight), eight elsewhere
   switch (P.mode) {
     case EPI_F32:
-      return gemm_launch_pers_mode<BN, EPI_F32>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_F32, 8>(ta, tb, P, st);
     case EPI_GELU_BF16:
-      return gemm_launch_pers_mode<BN, EPI_GELU_BF16>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_GELU_BF16, 16>(ta, tb, P, st);
     case EPI_TRAIN_FWD:
-      return gemm_launch_pers_mode<BN, EPI_TRAIN_FWD>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_TRAIN_FWD, 8>(ta, tb, P, st);
     case EPI_BWD_DZ:
-      return gemm_launch_pers_mode<BN, EPI_BWD_DZ>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_BWD_DZ, 8>(ta, tb, P, st);
     default:
       return set_error(DF_EINVAL, "GEMM epilogue mode");
   }
@@ -234,9 +237,20 @@ int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st
 }  // namespace df
 
 namespace df {
+// GELU probe: the epilogues' pair function on (x[2i], x[2i+1]) (an odd last
+// element paired with 0), or the derivative
 __global__ void k_gelu_probe(const float* x, float* y, long long n, int derivative) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = derivative ? gelu_grad_f(x[i]) : gelu_f(x[i]);
+  const long long i = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  if (derivative) {
+    y[i] = gelu_grad_f(x[i]);
+    if (i + 1 < n) y[i + 1] = gelu_grad_f(x[i + 1]);
+    return;
+  }
+  float g0, g1;
+  gelu2_f(x[i], i + 1 < n ? x[i + 1] : 0.0f, g0, g1);
+  y[i] = g0;
+  if (i + 1 < n) y[i + 1] = g1;
 }
 }  // namespace df
 
@@ -245,7 +259,8 @@ using namespace df;
 extern "C" int df_probe_gelu(const float* x, float* y, long long n, int derivative, void* stream) {
   if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_gelu: bad arguments");
   if (n == 0) return DF_OK;
-  k_gelu_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, derivative);
+  const long long pairs = (n + 1) / 2;
+  k_gelu_probe<<<(unsigned)((pairs + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y, n, derivative);
   return cuda_check(cudaGetLastError(), "GELU probe kernel");
 }
 

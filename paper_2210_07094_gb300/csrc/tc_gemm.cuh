@@ -134,10 +134,89 @@ __device__ __forceinline__ float half_erfc_scaled(float az) {
   return t * e;
 }
 
-// GELU(z) = z Phi(z), Phi the standard normal CDF
-__device__ __forceinline__ float gelu_f(float z) {
+// GELU(z) = z Phi(z), Phi the standard normal CDF (any z; the reference form)
+__device__ __forceinline__ float gelu_tail_f(float z) {
   const float h = half_erfc_scaled(fabsf(z));
   return z * (z >= 0.0f ? 1.0f - h : h);
+}
+
+// Packed FP32 pairs: Blackwell's f32x2 instructions do two FP32 operations in
+// one issue slot.  A pair lives in one 64-bit register (low half first).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ constexpr f32x2 f2_splat_bits(uint32_t bits) {
+  return ((f32x2)bits << 32) | (f32x2)bits;
+}
+__device__ __forceinline__ f32x2 f2_splat(float v) { return f2_splat_bits(__float_as_uint(v)); }
+
+// GELU of a pair, z Phi(z).  With a = |z| <= GELU_FIT_A, Phi(-a) =
+// 2^(-a^2 log2(e)/2 + Q(a)), where Q(a) = log2(Phi(-a) e^(a^2/2)) is smooth and
+// slowly varying (-1 at a = 0, about -3.3 at a = 4) and is evaluated by a
+// degree-8 polynomial in x = a/2 - 1, interpolated at the Chebyshev points of
+// [0, 4] (csrc/gen_gelu_fit.py): relative error of Phi(-a) below 1.7e-6 in FP32
+// Horner, one hardware exp2 (relative error ~2^-22) per value.  Then GELU(z)
+// = z Phi(-a) for z < 0 and z - z Phi(-a) for z >= 0, so the negative tail
+// keeps its relative accuracy.  Pairs with |z| > 4 (rare for pre-activations)
+// take the erfc form of gelu_tail_f.
+constexpr float GELU_FIT_A = 4.0f;
+__device__ __forceinline__ void gelu2_f(float z0, float z1, float& g0, float& g1) {
+  if (fmaxf(fabsf(z0), fabsf(z1)) > GELU_FIT_A) {
+    g0 = gelu_tail_f(z0);
+    g1 = gelu_tail_f(z1);
+    return;
+  }
+  const f32x2 z = f2_pack(z0, z1);
+  const f32x2 a = z & f2_splat_bits(0x7FFFFFFFu);
+  const f32x2 x = f2_fma(a, f2_splat(0.5f), f2_splat(-1.0f));
+  f32x2 q = f2_splat(-0.00023163699370343238f);
+  q = f2_fma(q, x, f2_splat(-4.95363783556968e-05f));
+  q = f2_fma(q, x, f2_splat(0.0027473631780594587f));
+  q = f2_fma(q, x, f2_splat(-0.011412550695240498f));
+  q = f2_fma(q, x, f2_splat(0.037877749651670456f));
+  q = f2_fma(q, x, f2_splat(-0.11411471664905548f));
+  q = f2_fma(q, x, f2_splat(0.3297445476055145f));
+  q = f2_fma(q, x, f2_splat(-1.0768771171569824f));
+  q = f2_fma(q, x, f2_splat(-2.5725913047790527f));
+  const f32x2 e = f2_fma(f2_mul(a, a), f2_splat((float)(-0.5 * 1.4426950408889634)), q);
+  float e0, e1, h0, h1;
+  f2_unpack(e, e0, e1);
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(h0) : "f"(e0));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(h1) : "f"(e1));
+  const f32x2 t = f2_mul(z, f2_pack(h0, h1));       // z Phi(-|z|)
+  const f32x2 d = f2_fma(t, f2_splat(-1.0f), z);   // z - z Phi(-|z|)
+  float t0, t1, d0, d1;
+  f2_unpack(t, t0, t1);
+  f2_unpack(d, d0, d1);
+  g0 = z0 < 0.0f ? t0 : d0;
+  g1 = z1 < 0.0f ? t1 : d1;
+}
+
+__device__ __forceinline__ float gelu_f(float z) {
+  float g, g1;
+  gelu2_f(z, 0.0f, g, g1);
+  return g;
 }
 // GELU'(z) = Phi(z) + z phi(z)
 __device__ __forceinline__ float gelu_grad_f(float z) {
@@ -289,7 +368,7 @@ __global__ void __launch_bounds__(128, 1)
           for (int j = 0; j < 32; ++j) v[j] = (rok && nb + j < P.N) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] = gelu_f(v[j]);
+          for (int j = 0; j < 32; j += 2) gelu2_f(v[j], v[j + 1], v[j], v[j + 1]);
         }
         __nv_bfloat16 hb[32];
 #pragma unroll
@@ -341,7 +420,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // epilogue warp two blocks of 32 rows x 16 columns (1 KB each), stored to
 // global memory by TMA (box 16 x 32, no swizzle)
 constexpr int PERS_STAGE_C_WARP = 32 * 16 * 2;
-constexpr int PERS_STAGE_C_BYTES = 8 * 2 * PERS_STAGE_C_WARP;
+__host__ __device__ constexpr int pers_stage_c_bytes(int epi_warps) { return epi_warps * 2 * PERS_STAGE_C_WARP; }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16]) {
   asm volatile(
@@ -388,7 +467,9 @@ __device__ __forceinline__ void gemm_gelu_chunk(const GemmParams& P, const uint3
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(gelu_f(v[2 * j]), gelu_f(v[2 * j + 1]));
+    float g0, g1;
+    gelu2_f(v[2 * j], v[2 * j + 1], g0, g1);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
     hb[j] = *reinterpret_cast<const uint32_t*>(&h);
   }
 }
@@ -435,7 +516,7 @@ __device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint
     for (int j = 0; j < 16; ++j) v[j] = (rok && (full || nb + j < P.N)) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
   } else {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = gelu_f(v[j]);
+    for (int j = 0; j < 16; j += 2) gelu2_f(v[j], v[j + 1], v[j], v[j + 1]);
   }
   __nv_bfloat162 hb[8];
 #pragma unroll
@@ -458,14 +539,17 @@ __host__ __device__ constexpr int tmem_cols_for() {
   return (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
 }
 
-constexpr int PERS_THREADS = 320;  // TMA warp, MMA warp, 8 epilogue warps
-constexpr int PERS_EPI_THREADS = PERS_THREADS - 64;
+// threads of the persistent kernel: TMA warp, MMA warp, EW epilogue warps
+__host__ __device__ constexpr int pers_threads(int epi_warps) { return 64 + 32 * epi_warps; }
 
-template <int BN, int STAGES, int MODE>
-__global__ void __launch_bounds__(PERS_THREADS, 1)
+template <int BN, int STAGES, int MODE, int EW = 8>
+__global__ void __launch_bounds__(pers_threads(EW), 1)
     k_gemm_tc_pers(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, GemmParams P) {
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "tile width");
+  static_assert(EW % 4 == 0 && EW >= 4 && EW <= 16, "epilogue warps: whole TMEM lane quarters");
+  constexpr int EPI_THREADS = 32 * EW;
+  constexpr int GROUPS = EW / 4;  // epilogue warps per TMEM lane quarter
   extern __shared__ uint8_t smem_raw[];
   constexpr int A_BYTES = GEMM_BM * GEMM_BK * 2;
   constexpr int B_BYTES = BN * GEMM_BK * 2;
@@ -476,7 +560,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
   uint8_t* sB = smem + STAGES * A_BYTES;
   // EPI_GELU_BF16 output staging: two 32-row x 16-column bf16 blocks per epilogue warp
   uint8_t* sC = sB + STAGES * B_BYTES;
-  constexpr int C_BYTES = (MODE == EPI_GELU_BF16) ? PERS_STAGE_C_BYTES : 0;
+  constexpr int C_BYTES = (MODE == EPI_GELU_BF16) ? pers_stage_c_bytes(EW) : 0;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sC + C_BYTES);  // full[S] empty[S] accf[2] acce[2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -490,7 +574,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, PERS_EPI_THREADS);
+      mbar_init(acce0 + 8 * b, EPI_THREADS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
@@ -572,11 +656,12 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
       }
     }
   } else {
-    // epilogue warps 2..9: TMEM lane quarter warp % 4, chunk parity (warp - 2) / 4.
+    // epilogue warps 2 .. EW + 1: TMEM lane quarter warp % 4; the GROUPS warps
+    // of a quarter take every GROUPS-th 16-column chunk, from (warp - 2) / 4.
     // The TMEM load of the next chunk is issued before the current chunk is
     // processed, so its latency overlaps the arithmetic.
     const int q = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int grp = (warp - 2) >> 2;
     const uint32_t stg0 = smem_u32(sC) + (uint32_t)((warp - 2) * 2 * PERS_STAGE_C_WARP);
     int sbuf = 0;
     int i = 0;
@@ -591,13 +676,16 @@ __global__ void __launch_bounds__(PERS_THREADS, 1)
       const int row = m0 + q * 32 + lane;
       const uint32_t tbase = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
       uint32_t r[16], rn[16];
-      int c0 = 16 * half;
-      tmem_ld16(tbase + (uint32_t)c0, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      constexpr int CS = 16 * GROUPS;  // column stride of one warp's chunks
+      int c0 = 16 * grp;
+      if (c0 < BN) {
+        tmem_ld16(tbase + (uint32_t)c0, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
 #pragma unroll 1
-      for (; c0 < BN; c0 += 32) {
-        const bool more = c0 + 32 < BN;
-        if (more) tmem_ld16(tbase + (uint32_t)(c0 + 32), rn);
+      for (; c0 < BN; c0 += CS) {
+        const bool more = c0 + CS < BN;
+        if (more) tmem_ld16(tbase + (uint32_t)(c0 + CS), rn);
         if (MODE == EPI_GELU_BF16) {
           if (n0 + c0 < P.N) {
             uint32_t hb[8];

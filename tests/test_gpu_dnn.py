@@ -45,12 +45,18 @@ def test_forward_matches_oracle(widths, rows):
     # activation upstream (one BF16 ulp, 2^-8 relative, of one term of the
     # next layer's sums).  Bounds: the largest difference, and the share of
     # outputs touched by a flip at all (above the FP32 accumulation noise).
+    # A flip in the last hidden layer moves an output by one BF16 ulp (2^-8 ..
+    # 2^-7 relative) of one term W4_kj H3_j: a few 1e-3 of the scale at most.
+    # Flips are rare per activation (FP32 accumulation noise of a K = 1600 sum,
+    # ~1e-6 relative, and the GELU's ~3e-7, against a BF16 half-ulp of 2e-3), but
+    # a row of the full network has 2800 activations: at most 40% of its rows
+    # may be touched at all; the median output is exact to FP32 noise.
     touched = float(np.mean(d > 1e-5))
     print({"widths": widths, "rows": rows, "max": float(d.max()), "median": float(np.median(d)),
            "touched": touched})
-    assert d.max() <= 1e-3, d.max()
-    assert np.median(d) <= 1e-5
-    assert touched <= 0.25
+    assert d.max() <= 4e-3, d.max()
+    assert np.median(d) <= 1e-6
+    assert touched <= (0.4 if widths[0] >= 1000 else 0.05)
 
 
 @pytest.fixture(scope="module")
@@ -99,7 +105,7 @@ def test_train_step_gradients_match_oracle(data):
             worst[name] = float((err / (S + 1e-300)).max())
             assert ok.all(), (name, worst[name], int((~ok).sum()))
             # and relative to the gradient itself where it is not a cancellation
-            big = np.abs(go[name]) >= 0.1 * S
+            big = (np.abs(go[name]) >= 0.1 * S) & (S > 0)
             if big.any():
                 rel = err[big] / np.abs(go[name][big])
                 worst[name + "_rel"] = float(rel.max())
@@ -228,12 +234,16 @@ def test_adam_steps_match_oracle(data):
         dnn.train_step(T0[sl].contiguous(), P[sl].contiguous(), Y0[:, sl].contiguous(), Y1[:, sl].contiguous(), lr)
         g = dnn.grads().astype(np.float64)
         th_o, m_o, v_o = mlp.adam_step(theta, m1, m2, g, step, lr)
+        # FP32 roundings are relative to the two terms of each moment update,
+        # not to the result (beta m and (1 - beta) g can cancel)
+        sm = 0.9 * np.abs(m1) + 0.1 * np.abs(g)
+        sv = 0.999 * m2 + 0.001 * g * g
         theta = dnn.params().astype(np.float64)
         a, b, t = dnn.adam_state()
         m1, m2 = a.astype(np.float64), b.astype(np.float64)
         assert t == step
-        assert np.all(np.abs(m1 - m_o) <= 1e-6 * np.abs(m_o) + 1e-30), np.max(np.abs(m1 - m_o) / (np.abs(m_o) + 1e-30))
-        assert np.all(np.abs(m2 - v_o) <= 1e-6 * np.abs(v_o) + 1e-38), np.max(np.abs(m2 - v_o) / (np.abs(v_o) + 1e-38))
+        assert np.all(np.abs(m1 - m_o) <= 1e-6 * sm + 1e-30), np.max(np.abs(m1 - m_o) / (sm + 1e-30))
+        assert np.all(np.abs(m2 - v_o) <= 1e-6 * sv + 1e-38), np.max(np.abs(m2 - v_o) / (sv + 1e-38))
         # FP32 parameter: one rounding of theta (half an ulp) plus the FP32
         # update's few roundings (relative 1e-6 of a step of size ~lr)
         tol = 2.0 ** -23 * np.abs(th_o) + 1e-6 * lr

@@ -39,9 +39,12 @@ def test_gelu_relative_error():
     assert np.all(rel <= bound), (rel.max(), x[~tiny][np.argmax(rel / bound)])
     assert np.all(np.abs(y[tiny]) <= 1e-35)
     # after the BF16 rounding the epilogue applies, almost every value is the
-    # correctly rounded one
+    # correctly rounded one (a flip needs the value within the FP32 error,
+    # ~3e-7 relative in the body, of a BF16 rounding boundary)
     b = lambda a: torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).float().numpy()  # noqa: E731
-    assert np.mean(b(y) != b(exact)) < 1e-3
+    flips = float(np.mean(b(y) != b(exact)))
+    print({"bf16_flip_rate": flips, "max_rel": float(rel.max())})
+    assert flips < 5e-4
 
 
 def test_gelu_derivative_error():
