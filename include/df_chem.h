@@ -236,16 +236,18 @@ int df_chem_adjoint_static(const df_mech* mech, int64_t ncells, const double* T0
                            double* g_lnA, int32_t* status, int32_t* nsub, df_stream_t stream);
 
 /* Advance every cell by nsteps consecutive steps of dt (the repeated CFD step
- * of the 0D ignition runs, Sec. 3.1) in one persistent launch, and report each
- * cell's ignition delay as the paper defines it (Sec. 3.1: from [dT/dt]_max).
+ * of the 0D ignition runs, Sec. 4.1) in one persistent launch, and report each
+ * cell's ignition delay as the paper defines it (Sec. 4.1: from [dT/dt]_max).
  * Same arguments and per-cell status as df_chem_integrate, plus:
  *   nsteps >= 1: the substep sequence stops at every multiple of dt (the
  *     step-size controller carries h across the boundaries); max_substeps in
  *     opts bounds the total over all steps;
  *   nsub [ncells] (may be NULL): accepted substeps over all steps;
  *   t_ign [ncells] (device, may be NULL): the time in [0, nsteps*dt) of the
- *     largest dT/dt among the states at which accepted substeps start (the
- *     integrator evaluates f there anyway); NaN for a failed cell.
+ *     largest dT/dt: the largest among the states at which accepted substeps
+ *     start (the integrator evaluates f there anyway), its time refined by the
+ *     vertex of the parabola through that sample and its two neighbours (the
+ *     sample's own time at either end of the run); NaN for a failed cell.
  * With nsteps = 1 the result equals df_chem_integrate's.  Errors: DF_EINVAL
  * (also nsteps < 1), DF_ECUDA.  Asynchronous on `stream`. */
 int df_chem_integrate_steps(const df_mech* mech, int64_t ncells, double* T, const double* p, double* Y,

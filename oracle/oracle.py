@@ -163,8 +163,8 @@ class Mech:
 
     def ignition(self, T, p, Y, dt, nsteps, grid=4, rtol=1e-10):
         """nsteps consecutive steps of dt (the repeated CFD step of the 0D
-        ignition runs, Sec. 3.1) from (T, p, Y); the ignition delay is the time
-        of [dT/dt]_max (Sec. 3.1), here over a grid of dt/grid.  Returns the
+        ignition runs, Sec. 4.1) from (T, p, Y); the ignition delay is the time
+        of [dT/dt]_max (Sec. 4.1), here over a grid of dt/grid.  Returns the
         final T, Y, the grid time of the largest dT/dt per cell and that rate."""
         T = np.array(T, dtype=np.float64)
         Y = np.array(Y, dtype=np.float64)

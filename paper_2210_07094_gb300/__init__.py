@@ -171,7 +171,7 @@ def integrate_steps(mech: Mechanism, T, p, Y, dt: float, nsteps: int, opts: Inte
                     status=None, nsub=None, t_ign=None, stream=None):
     """Advance every cell by nsteps consecutive steps of dt in place and return
     (status, nsub, t_ign): t_ign is the time of the largest dT/dt (the
-    ignition delay of Sec. 3.1) per cell."""
+    ignition delay of Sec. 4.1) per cell."""
     torch = _torch()
     n, pT, pp, pY = _cells(mech, T, p, Y)
     if status is None:

@@ -236,8 +236,9 @@ std::string jit_thread_source(const df_mech* m) {
   return o.str();
 }
 
-std::string jit_kernel_name(int N, int threads) {
-  return "df::k_integrate_thread<" + std::to_string(N) + ", false, " + std::to_string(threads) + ", df::GenEval>";
+std::string jit_kernel_name(int N, int threads, bool ign = false) {
+  return "df::k_integrate_thread<" + std::to_string(N) + ", false, " + std::to_string(threads) + ", df::GenEval" +
+         (ign ? ", true>" : ">");
 }
 
 namespace {
@@ -371,6 +372,7 @@ struct Module {
   std::string why;
   CUmodule mod = nullptr;
   std::map<int, CUfunction> fn;  // threads per block -> kernel
+  CUfunction fn_ign = nullptr;    // 32 threads, refining the ignition time (IntegArgs.t_ign)
   size_t compile_ms = 0;
   bool from_cache = false;
 };
@@ -379,6 +381,7 @@ std::mutex g_mu;
 std::map<std::pair<int, std::string>, Module> g_modules;
 
 constexpr int kThreads[] = {32, 64};
+constexpr int kIgnThreads = 32;  // the block size of the kernel that refines the ignition time
 
 // ---------------------------------------------------------------------------
 // on-disk cache of compiled modules: <dir>/<key>.cubin and <key>.names (the
@@ -475,6 +478,16 @@ bool finish_module(Module& r, const Driver& drv, const std::vector<char>& cubin,
     }
     r.fn[kThreads[i]] = f;
   }
+  {
+    const size_t i = sizeof(kThreads) / sizeof(kThreads[0]);
+    if (i >= lowered.size() || lowered[i].empty() ||
+        drv.get_function(&r.fn_ign, r.mod, lowered[i].c_str()) != CUDA_SUCCESS) {
+      r.why = "generated kernel (ignition time) not found in the module";
+      drv.unload(r.mod);
+      r.mod = nullptr;
+      return false;
+    }
+  }
   CUdeviceptr tab = 0;
   size_t tab_bytes = 0;
   if (lowered.back().empty() || drv.get_global(&tab, &tab_bytes, r.mod, lowered.back().c_str()) != CUDA_SUCCESS ||
@@ -497,7 +510,7 @@ bool finish_module(Module& r, const Driver& drv, const std::vector<char>& cubin,
 
 // Version of the cached entries (the cubin and its lowered-name list, and what
 // finish_module expects of them); raised whenever either changes.
-constexpr int kCacheFormat = 2;
+constexpr int kCacheFormat = 3;
 
 Module build_module(int dev, const df_mech* m, const std::string& src) {
   Module r;
@@ -521,6 +534,7 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
   const std::string arch = "--gpu-architecture=sm_" + std::to_string(major * 10 + minor) + "a";
   std::vector<std::string> names;
   for (int t : kThreads) names.push_back(jit_kernel_name(m->dims.N, t));
+  names.push_back(jit_kernel_name(m->dims.N, kIgnThreads, true));
   names.push_back("&df::c_tab");
   const std::string incopt = "-I" + inc;
   const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
@@ -615,8 +629,15 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
                                    : "generated kernel compiled in " + std::to_string(md->compile_ms) + " ms";
   }
   if (!md->ok) return DF_OK;
-  auto f = md->fn.find(threads);
-  if (f == md->fn.end()) return DF_OK;  // no generated kernel for this block size
+  CUfunction fk = nullptr;
+  if (a.t_ign) {  // the variant that refines the ignition time, in its block size
+    fk = md->fn_ign;
+    threads = kIgnThreads;
+  } else {
+    auto f = md->fn.find(threads);
+    if (f == md->fn.end()) return DF_OK;  // no generated kernel for this block size
+    fk = f->second;
+  }
   const Driver& drv = driver();
   const int N = m->dims.N;
   const int per_thread = (N + 1) * (N + 1) + 6 * (N + 1);  // J and the stage vectors
@@ -628,10 +649,10 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
     sm = sizeof(double) * (128 + (size_t)per_thread * threads);
   }
   if (sm > m->max_smem_optin) return DF_OK;
-  if (drv.set_attr(f->second, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)sm) != CUDA_SUCCESS)
+  if (drv.set_attr(fk, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)sm) != CUDA_SUCCESS)
     return set_error(DF_ECUDA, "generated integrator: shared-memory attribute");
   int occ = 0;
-  if (drv.occupancy(&occ, f->second, threads, sm) != CUDA_SUCCESS || occ < 1)
+  if (drv.occupancy(&occ, fk, threads, sm) != CUDA_SUCCESS || occ < 1)
     return set_error(DF_ECUDA, "generated integrator: occupancy query");
   const int per_sm = bps > 0 ? std::min(bps, occ) : occ;
   int64_t blocks = (int64_t)m->num_sms * per_sm;
@@ -640,7 +661,7 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
   int rc = cuda_check(cudaMemsetAsync(m->counters, 0, 4 * sizeof(unsigned long long), st), "reset work counter");
   if (rc) return rc;
   void* params[] = {&args};
-  if (drv.launch(f->second, (unsigned)blocks, 1, 1, (unsigned)threads, 1, 1, (unsigned)sm, (CUstream)st, params,
+  if (drv.launch(fk, (unsigned)blocks, 1, 1, (unsigned)threads, 1, 1, (unsigned)sm, (CUstream)st, params,
                  nullptr) != CUDA_SUCCESS)
     return set_error(DF_ECUDA, "generated integrator launch");
   *launched = true;

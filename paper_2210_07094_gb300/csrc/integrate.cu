@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
     double t = 0.0, h = fmin(a.h0, a.dt);
     double hacc = 0.0, erracc = 1.0;
     int nacc = 0, nrej = 0, istep = 0;
-    double fbest = -INFINITY, tbest = 0.0;
+    PeakTrack pk;
+    pk.reset();
     bool last_rej = false;
     while (!done) {
       bool last = false;
@@ -220,10 +221,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         erracc = fmax(1e-2, en);
         h *= fac;
         last_rej = false;
-        if (fT > fbest) {  // dT/dt at the start of an accepted substep
-          fbest = fT;
-          tbest = istep * a.dt + t0;
-        }
+        pk.add(istep * a.dt + t0, fT);  // dT/dt at the start of an accepted substep
         if (t >= a.dt) {
           if (++istep < a.nsteps) t = 0.0;  // next consecutive step of dt
           else done = true;
@@ -253,7 +251,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
       }
     }
     if (lane == 0) {
-      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? tbest : NAN;
+      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? pk.time() : NAN;
       a.status[cell] = status;
       if (a.nsub) a.nsub[cell] = nacc;
       tot_acc += nacc;
@@ -413,8 +411,10 @@ int integrate_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int thr
   if (sm > m->max_smem_optin)
     return set_error(DF_EUNSUPPORTED, "integrator shared memory exceeds the per-block limit");
   // block sizes with a compile-time stride (constant pressure); others take
-  // the run-time stride
-  auto kf = constv            ? k_integrate_thread<NS, true>
+  // the run-time stride; with t_ign the kernels that refine the ignition time
+  auto kf = a.t_ign ? (constv ? k_integrate_thread<NS, true, 0, BlobEval, true>
+                              : k_integrate_thread<NS, false, 0, BlobEval, true>)
+            : constv          ? k_integrate_thread<NS, true>
             : threads == 32  ? k_integrate_thread<NS, false, 32>
             : threads == 64  ? k_integrate_thread<NS, false, 64>
             : threads == 128 ? k_integrate_thread<NS, false, 128>

@@ -56,8 +56,10 @@ __host__ __device__ inline int blob_smem_doubles(const MechDims& d) { return (d.
 
 // BT > 0: the kernel is launched with exactly BT threads per block, the
 // stride of the per-thread shared-memory vectors is a compile-time constant.
-// EVAL: the evaluation policy of f and J (see BlobEval).
-template <int NS, bool CONSTV = false, int BT = 0, class EVAL = BlobEval>
+// EVAL: the evaluation policy of f and J (see BlobEval).  IGN: track the
+// largest dT/dt with the neighbouring samples that refine its time (a.t_ign);
+// without it only the time of the largest sample is kept (fewer registers).
+template <int NS, bool CONSTV = false, int BT = 0, class EVAL = BlobEval, bool IGN = false>
 __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   constexpr int n = NS + 1;
   extern __shared__ double smem[];
@@ -93,6 +95,8 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   int status = 0, nacc = 0, nrej = 0, istep = 0;
   double y[n];
   double t = 0.0, h = 0.0, fbest = -INFINITY, tbest = 0.0;
+  PeakTrack pk;
+  if (IGN) pk.reset();
   double prm = 0.0;  // pressure [dyn/cm^2], or the fixed density [g/cm^3] at constant volume
   StepState ss{0.0, 1.0};
   unsigned long long tot_acc = 0, tot_rej = 0;
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) a.Y[(int64_t)k * a.ncells + cell] = y[1 + k];
       }
-      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? tbest : NAN;
+      if (a.t_ign) a.t_ign[cell] = status == DF_CELL_OK ? (IGN ? pk.time() : tbest) : NAN;
       a.status[cell] = status;
       if (a.nsub) a.nsub[cell] = nacc;
       tot_acc += nacc;
@@ -146,6 +150,7 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
           nacc = nrej = istep = 0;
           fbest = -INFINITY;
           tbest = 0.0;
+          if (IGN) pk.reset();
           last_rej = false;
           status = ok ? DF_CELL_OK : DF_CELL_NONFINITE;
           done = !ok || !(a.dt > 0.0);
@@ -173,9 +178,13 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
                                                 &fT);
     const int nacc0 = nacc;
     step_control(tb, ok, en, last, a.dt, y, ys, t, h, nacc, nrej, last_rej, done, ss);
-    if (nacc > nacc0 && fT > fbest) {  // dT/dt at the start of an accepted substep
-      fbest = fT;
-      tbest = istep * a.dt + t0;
+    if (nacc > nacc0) {  // dT/dt at the start of an accepted substep
+      if (IGN) {
+        pk.add(istep * a.dt + t0, fT);
+      } else if (fT > fbest) {
+        fbest = fT;
+        tbest = istep * a.dt + t0;
+      }
     }
     if (done && ++istep < a.nsteps) {  // next consecutive step of dt
       done = false;

@@ -188,6 +188,51 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
   return ok && isfinite(en);
 }
 
+// Ignition delay (Sec. 4.1 defines it by [dT/dt]_max): the largest dT/dt
+// among the samples of one cell -- the states at which its accepted substeps
+// start, in time order, where the integrator evaluates f anyway -- with its
+// time refined by the vertex of the parabola through the largest sample and
+// its two neighbours, so the delay is resolved below the substep spacing
+// where the rate peak is smooth.  Without a neighbour on either side the time
+// of the largest sample stands.
+struct PeakTrack {
+  double tp, fp;  // the sample before the largest
+  double tb, fb;  // the largest
+  double tn, fn;  // the first sample after the largest
+  double tl, fl;  // the latest sample
+  int have;       // bit 0: a sample before the largest, bit 1: one after, bit 2: any sample
+  __host__ __device__ void reset() {
+    tp = fp = tn = fn = tl = fl = tb = 0.0;
+    fb = -INFINITY;
+    have = 0;
+  }
+  __host__ __device__ void add(double t, double f) {
+    if (f > fb) {
+      tp = tl;
+      fp = fl;
+      tb = t;
+      fb = f;
+      have = (have & 4) ? 5 : 4;
+    } else if (!(have & 2)) {
+      tn = t;
+      fn = f;
+      have |= 2;
+    }
+    tl = t;
+    fl = f;
+    have |= 4;
+  }
+  __host__ __device__ double time() const {
+    if ((have & 3) != 3) return tb;
+    const double a = tb - tp, b = tb - tn;    // a > 0 > b
+    const double fa = fb - fp, fc = fb - fn;  // both >= 0
+    const double den = a * fc - b * fa;
+    if (!(den > 0.0)) return tb;
+    const double tv = tb - 0.5 * (a * a * fc - b * b * fa) / den;
+    return fmin(fmax(tv, tp), tn);
+  }
+};
+
 // accept / reject and the next step size.  Elementary controller (safety 0.9,
 // growth limits [0.2, 6], down to 1e-4 before the first accepted step, no
 // growth right after a rejection) combined with Gustafsson's predictive

@@ -251,6 +251,41 @@ def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22
     ms_int = ev_time(run_int, reps)
     acc, rej = m.last_stats()
     r2 = ev["r2_dF"][ev["var_dF"] > 0]
+    # the same pass split into the cells the network takes and the fallback
+    # cells: how the time divides, and the bound the FP64 fallback sets on the
+    # speed-up (the integrator's time over its time on the fallback cells alone)
+    Tw.copy_(Te)
+    Yw.copy_(Ye)
+    _, used, _ = dnn.infer(m, Tw, Pe, Yw, 1e-6)
+    split = {}
+    for name, sel in (("network_cells_only", used == 0), ("fallback_cells_only", used != 0)):
+        idx = sel.nonzero().squeeze(1)
+        Ts, Ps, Ys = Te[idx].contiguous(), Pe[idx].contiguous(), Ye[:, idx].contiguous()
+        Tx, Yx = Ts.clone(), Ys.clone()
+
+        def run_d(e0, e1, Ts=Ts, Ps=Ps, Ys=Ys, Tx=Tx, Yx=Yx):
+            Tx.copy_(Ts)
+            Yx.copy_(Ys)
+            e0.record()
+            dnn.infer(m, Tx, Ps, Yx, 1e-6)
+            e1.record()
+
+        def run_i(e0, e1, Ts=Ts, Ps=Ps, Ys=Ys, Tx=Tx, Yx=Yx):
+            Tx.copy_(Ts)
+            Yx.copy_(Ys)
+            e0.record()
+            integrate(m, Tx, Ps, Yx, 1e-6)
+            e1.record()
+
+        ms_i = ev_time(run_i, reps)
+        split[name] = {"cells": int(idx.numel()), "ms_integrator": ms_i}
+        if name == "network_cells_only":
+            ms_d = ev_time(run_d, reps)
+            split[name].update({"ms_infer": ms_d, "infer_cells_per_s": idx.numel() / (ms_d * 1e-3),
+                                "speedup_vs_integrator": ms_i / ms_d})
+        else:
+            split[name].update({"share_of_integrator_time_on_all_cells": ms_i / ms_int,
+                                "speedup_bound_with_an_instant_network": ms_int / ms_i})
     return {
         "workload": f"train on {n_pairs} integrator pairs ({n_train_init} trajectories x {n_steps} steps of "
                     f"dt=1us); infer {n_eval} held-out trajectory states, {n_oor} moved outside the training "
@@ -278,4 +313,5 @@ def experiment(mech_json: dict, n_train_init=1 << 16, n_steps=32, n_eval=1 << 22
                 "elements": sorted({e for sp in mech_json["species"] for e in sp["composition"]})},
         },
         "integrator_substeps_per_cell": (acc + rej) / n_eval,
+        **split,
     }

@@ -363,6 +363,25 @@ def isomer_mechanism(kind: str = "elementary", A: float = 2.0e5, b: float = 0.0,
             "species": _iso_species(a7_b), "reactions": [rxn]}
 
 
+def autocatalytic_mechanism(A: float = 1.0e7, da6: float = -1.0, W: float = 30.0) -> dict:
+    """A + B -> 2 B (irreversible, b = 0, Ea = 0) with an inert D; A, B and D
+    have the same W and cp, and B's enthalpy sits da6 * R below A's.  At
+    constant pressure with W-bar fixed, dY_B/dt = r Y_A Y_B, r = A rho / W (a
+    logistic curve), and dT/dt is proportional to the same product: the rate
+    peaks where Y_A = Y_B.  With |da6| small the temperature (and rho) barely
+    moves, so the time of [dT/dt]_max is ln(Y_A0 / Y_B0) / (r (Y_A0 + Y_B0))."""
+    base = [3.5, 1e-3, -1e-7, 0.0, 0.0, -1000.0, 10.0]
+    nb = list(base)
+    nb[5] = base[5] + da6
+    sp = [{"name": "A", "composition": {"X": 2}, "W": W, "nasa7": base, "T_range": [300.0, 3000.0]},
+          {"name": "B", "composition": {"X": 2}, "W": W, "nasa7": nb, "T_range": [300.0, 3000.0]},
+          {"name": "D", "composition": {"Z": 1}, "W": W, "nasa7": list(base), "T_range": [300.0, 3000.0]}]
+    rxn = {"reactants": {"A": 1, "B": 1}, "products": {"B": 2}, "type": "elementary", "reversible": False,
+           "A": A, "b": 0.0, "Ea": 0.0, "equation": "A + B => 2 B"}
+    return {"name": "autocatalytic", "elements": ["X", "Z"], "units": {"A": "cm, mol, s", "Ea": "kJ/mol", "T": "K"},
+            "species": sp, "reactions": [rxn]}
+
+
 def zero_rate(mech: dict) -> dict:
     """Same species and reactions with every pre-exponential set to 0."""
     m = json.loads(json.dumps(mech))

@@ -1,5 +1,5 @@
 """Multi-step driver (df_chem_integrate_steps): nsteps consecutive steps of dt
-in one launch, and the ignition delay from [dT/dt]_max (Sec. 3.1), against
+in one launch, and the ignition delay from [dT/dt]_max (Sec. 4.1), against
 df_chem_integrate and the oracle."""
 import numpy as np
 import pytest
@@ -51,13 +51,16 @@ def test_ignition_window_against_oracle(h2):
     T, p, Y = _dev(T0, p0, Y0)
     st, ns, ti = df.integrate_steps(m, T, p, Y, dt, nsteps)
     assert int(st.abs().sum()) == 0
-    To, Yo, to, rate = o.ignition(T0, p0, Y0, dt, nsteps, grid=4)
+    To, Yo, to, rate = o.ignition(T0, p0, Y0, dt, nsteps, grid=16)
     Tg, Yg = T.cpu().numpy(), Y.cpu().numpy()
     assert np.max(np.abs(Tg - To)) <= 1e-3
     assert np.max(np.abs(Yg - Yo) / Yo.max(axis=0)) <= 1e-7
     tig = ti.cpu().numpy()
     assert np.all(to > 5 * dt)  # an interior maximum, not the initial state
-    assert np.all(np.abs(tig - to) <= 2 * dt), np.max(np.abs(tig - to))
+    # the oracle's grid resolves dt/16; the GPU's time is the vertex of the
+    # parabola through its largest substep-start sample and the neighbours
+    print({"max_abs_dt_ign_over_dt": float(np.max(np.abs(tig - to)) / dt)})
+    assert np.all(np.abs(tig - to) <= dt / 4), np.max(np.abs(tig - to))
     # the GPU's chosen time has (nearly) the oracle's largest rate
     for c in range(0, n, 6):
         Tc, Yc, _, _ = o.integrate(T0[c:c + 1], p0[c:c + 1], Y0[:, c:c + 1], float(tig[c])) \
@@ -79,3 +82,30 @@ def test_steps_match_repeated_calls_warp_path():
     assert torch.max(torch.abs(T - T2)).item() <= 1e-4
     assert torch.max(torch.abs(Y - Y2)).item() <= 1e-8
     assert bool(((ti >= 0) & (ti < 3 * f["dt"])).all())
+
+
+def test_ignition_time_of_the_logistic_closed_form():
+    """A + B -> 2 B (equal W and cp, small heat of reaction): the largest dT/dt
+    falls where Y_A = Y_B, at t* = ln(Y_A0 / Y_B0) / (r (Y_A0 + Y_B0)), r = A rho / W
+    (the oracle reaches it within half its grid, CPU test).  The GPU's refined
+    time lies within dt/20 of t*, far inside its substep spacing; the thread
+    path (the 3-species built kernel) and the warp path agree."""
+    mech = synth.autocatalytic_mechanism()
+    m = df.Mechanism(mech)
+    YA = np.array([0.5, 0.5, 0.3, 0.6] * 8)
+    YB = np.array([1e-3, 1e-4, 1e-3, 5e-3] * 8)
+    Y0 = np.vstack([YA, YB, 1.0 - YA - YB])
+    n = YA.size
+    rho = 10 * 101325.0 * 30.0 / (8.314462618e7 * 1000.0)
+    tstar = np.log(YA / YB) / (1e7 * rho / 30.0 * (YA + YB))
+    dt = 0.01
+    for path in (1, 2):
+        T, p, Y = _dev(np.full(n, 1000.0), np.full(n, 101325.0), Y0)
+        o = df.default_opts()
+        o.path = path
+        st, ns, ti = df.integrate_steps(m, T, p, Y, dt, 25, o)
+        assert int(st.abs().sum()) == 0
+        err = np.abs(ti.cpu().numpy() - tstar)
+        print({"path": path, "max_err_over_dt": float(err.max() / dt),
+               "substeps_per_step": float(ns.float().mean() / 25)})
+        assert np.all(err <= dt / 20), (path, err.max() / dt)

@@ -483,3 +483,24 @@ def test_parity_check_rejects_a_kernel_that_returns_its_input():
         check_integrator(f["T"], f["Y"], Tw, Yw, To, Yo)
     Tt, Yt, _, _ = o.integrate(f["T"], f["p"], f["Y"], f["dt"], rtol=1e-12, atolT=1e-12)
     check_integrator(f["T"], f["Y"], Tt, Yt, To, Yo)
+
+
+def test_ignition_time_of_the_logistic_closed_form():
+    """A + B -> 2 B with equal molar masses and heat capacities and a small heat
+    of reaction: dY_B/dt = r Y_A Y_B with r = A rho / W, a logistic curve whose
+    rate -- and dT/dt with it -- peaks when Y_A = Y_B, at
+    t* = ln(Y_A0 / Y_B0) / (r (Y_A0 + Y_B0)).  The oracle's time of the largest
+    dT/dt (Sec. 4.1's ignition delay) on a grid of dt/16 lies within half a grid
+    spacing of t*, plus the shift from the 0.1 K the mixture heats (rho moves by
+    1e-4)."""
+    mech = synth.autocatalytic_mechanism()
+    o = Mech(mech)
+    YA = np.array([0.5, 0.5, 0.3, 0.6])
+    YB = np.array([1e-3, 1e-4, 1e-3, 5e-3])
+    Y = np.vstack([YA, YB, 1.0 - YA - YB])
+    T0, p = np.full(4, 1000.0), np.full(4, 101325.0)
+    rho = 10 * 101325.0 * 30.0 / (8.314462618e7 * 1000.0)  # g/cm^3, cgs gas constant
+    tstar = np.log(YA / YB) / (1e7 * rho / 30.0 * (YA + YB))
+    dt, grid = 0.01, 16
+    _, _, tig, _ = o.ignition(T0, p, Y, dt, 25, grid=grid)
+    assert np.all(np.abs(tig - tstar) <= 0.5 * dt / grid + 1e-3 * tstar), (tig, tstar)
