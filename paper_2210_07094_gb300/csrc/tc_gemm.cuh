@@ -181,12 +181,8 @@ __device__ __forceinline__ f32x2 f2_splat(float v) { return f2_splat_bits(__floa
 // keeps its relative accuracy.  Pairs with |z| > 4 (rare for pre-activations)
 // take the erfc form of gelu_tail_f.
 constexpr float GELU_FIT_A = 4.0f;
-__device__ __forceinline__ void gelu2_f(float z0, float z1, float& g0, float& g1) {
-  if (fmaxf(fabsf(z0), fabsf(z1)) > GELU_FIT_A) {
-    g0 = gelu_tail_f(z0);
-    g1 = gelu_tail_f(z1);
-    return;
-  }
+// the fitted form, valid for |z0|, |z1| <= GELU_FIT_A
+__device__ __forceinline__ void gelu2_fit(float z0, float z1, float& g0, float& g1) {
   const f32x2 z = f2_pack(z0, z1);
   const f32x2 a = z & f2_splat_bits(0x7FFFFFFFu);
   const f32x2 x = f2_fma(a, f2_splat(0.5f), f2_splat(-1.0f));
@@ -211,6 +207,33 @@ __device__ __forceinline__ void gelu2_f(float z0, float z1, float& g0, float& g1
   f2_unpack(d, d0, d1);
   g0 = z0 < 0.0f ? t0 : d0;
   g1 = z1 < 0.0f ? t1 : d1;
+}
+
+__device__ __forceinline__ void gelu2_f(float z0, float z1, float& g0, float& g1) {
+  if (fmaxf(fabsf(z0), fabsf(z1)) > GELU_FIT_A) {
+    g0 = gelu_tail_f(z0);
+    g1 = gelu_tail_f(z1);
+    return;
+  }
+  gelu2_fit(z0, z1, g0, g1);
+}
+
+// GELU of 2P values in place.  One range test for the whole group, so the
+// common case (every |z| <= 4) is straight-line code in which the compiler
+// interleaves the P independent pairs; a group with a larger value takes the
+// per-pair test.
+template <int P>
+__device__ __forceinline__ void gelu_group(float (&v)[2 * P]) {
+  float amax = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2 * P; ++j) amax = fmaxf(amax, fabsf(v[j]));
+  if (amax <= GELU_FIT_A) {
+#pragma unroll
+    for (int j = 0; j < P; ++j) gelu2_fit(v[2 * j], v[2 * j + 1], v[2 * j], v[2 * j + 1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < P; ++j) gelu2_f(v[2 * j], v[2 * j + 1], v[2 * j], v[2 * j + 1]);
+  }
 }
 
 __device__ __forceinline__ float gelu_f(float z) {
@@ -367,8 +390,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = (rok && nb + j < P.N) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
         } else {
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) gelu2_f(v[j], v[j + 1], v[j], v[j + 1]);
+          gelu_group<16>(v);
         }
         __nv_bfloat16 hb[32];
 #pragma unroll
@@ -465,11 +487,10 @@ __device__ __forceinline__ void gemm_gelu_chunk(const GemmParams& P, const uint3
       for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
     }
   }
+  gelu_group<8>(v);
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    float g0, g1;
-    gelu2_f(v[2 * j], v[2 * j + 1], g0, g1);
-    const __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
     hb[j] = *reinterpret_cast<const uint32_t*>(&h);
   }
 }
@@ -515,8 +536,7 @@ __device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = (rok && (full || nb + j < P.N)) ? v[j] * gelu_grad_f(az[j]) : 0.0f;
   } else {
-#pragma unroll
-    for (int j = 0; j < 16; j += 2) gelu2_f(v[j], v[j + 1], v[j], v[j + 1]);
+    gelu_group<8>(v);
   }
   __nv_bfloat162 hb[8];
 #pragma unroll
