@@ -94,12 +94,16 @@ def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, 
           log=None):
     """Adam with a cosine learning-rate schedule over shuffled mini-batches.
     Each epoch the pairs are permuted once into batch-major blocks, so every
-    step hands the library contiguous views (no per-step gathers)."""
+    step hands the library contiguous views (no per-step gathers).  With a
+    time budget the schedule spans the steps that fit in it: the step rate is
+    measured over the first 200 steps and the cosine's length set from it, so
+    the learning rate has decayed to lr1 when the budget ends."""
     import torch
     n = T.numel()
     batch = min(batch, n)
     steps_per_epoch = max(1, n // batch)
     total = max(1, int(epochs * steps_per_epoch))
+    probe = 200 if time_budget is not None else -1
     g = torch.Generator(device=T.device).manual_seed(seed)
     losses = []
     t0 = time.time()
@@ -113,14 +117,18 @@ def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, 
             Ps = p[perm].view(steps_per_epoch, batch)
             Ys = Y[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
             Yns = Yn[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
-        lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * s / total))
+        if s == probe:  # steps that fit in the budget at the measured rate
+            torch.cuda.synchronize()
+            rate = s / max(time.time() - t0, 1e-9)
+            total = min(total, max(s + 1, int(rate * time_budget)))
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * min(s / total, 1.0)))
         want = (s % 50 == 0) or s == total - 1
         loss = dnn.train_step(Ts[k], Ps[k], Ys[k], Yns[k], lr, want_loss=want)
         if want:
             losses.append((s, loss))
             if log:
                 log(f"step {s}/{total} lr {lr:.2e} loss {loss:.4e}")
-        if time_budget is not None and time.time() - t0 > time_budget:
+        if s + 1 >= total or (time_budget is not None and time.time() - t0 > 1.1 * time_budget):
             break
     return losses
 
