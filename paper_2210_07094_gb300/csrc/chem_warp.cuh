@@ -51,6 +51,20 @@ __host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
   return w;
 }
 
+// 1/a in FP64 from an FP32 seed and two Newton-Raphson steps r <- r (2 - a r)
+// (the relative error squares at each step: 2^-22 -> 2^-44 -> rounding): four
+// FP64 operations where a correctly rounded division takes a longer sequence
+// on the narrow FP64 pipe.  For |a| inside the FP32 normal range (the warp
+// path's pivots, temperatures, densities, heat capacities and step sizes); a
+// zero or non-finite a gives a non-finite result.
+__device__ __forceinline__ double rcp_nr(double a) {
+  float r0f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)a));
+  const double r0 = (double)r0f;
+  const double r1 = r0 * fma(-a, r0, 2.0);
+  return r1 * fma(-a, r1, 2.0);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(WFULL, v, o);
@@ -74,7 +88,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   double* wdot = ws + L.wdot;
   const double T = y[0];
   const double lnT = log_tab(T);
-  const double invT = 1.0 / T;
+  const double invT = rcp_nr(T);
   // thermo and sum Y/W
   double sYW = 0.0;
   for (int k = lane; k < N; k += 32) {
@@ -89,7 +103,8 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     sYW += y[1 + k] * mv.sp[SP_REC * k + 1];
   }
   const double sumYW = warp_sum(sYW);
-  const double rho = CONSTV ? pc : pc * invT / (RU * sumYW);
+  const double Wbar = rcp_nr(sumYW);
+  const double rho = CONSTV ? pc : pc * invT * Wbar * (1.0 / RU);
   for (int k = lane; k < N; k += 32) C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
   __syncwarp();
   const double lnP0RT = LOG_PSTD_RU - lnT;
@@ -148,14 +163,13 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   __syncwarp();
   const double cpm = RU * warp_sum(cpp);
   const double Hw = RU * T * warp_sum(hwp);
-  const double invrho = 1.0 / rho;
-  const double invcp = 1.0 / cpm;
+  const double invrho = rcp_nr(rho);
+  const double invcp = rcp_nr(cpm);
   for (int k = lane; k < N; k += 32) f[1 + k] = mv.sp[SP_REC * k] * wdot[k] * invrho;
   const double fT = -Hw * invrho * invcp;
   if (lane == 0) f[0] = fT;
   if (WITH_J) {
     double* J = ws + L.J;
-    const double Wbar = 1.0 / sumYW;
     // concentration-space rows of this lane's species: one loop over the
     // concatenation of their reaction lists (as for the production rates)
     if (ka >= 0)
@@ -231,25 +245,30 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
 }
 
 // LU with partial pivoting of the n x n row-major matrix A (shared memory),
-// whole rows swapped, reciprocal pivots on the diagonal.  Returns false if a
-// pivot is zero or not finite.
+// whole rows swapped, reciprocal pivots on the diagonal, and the columns of U
+// above the diagonal divided by their pivot (U'_ik = U_ik / U_kk, for the
+// back substitution of warp_solve).  Returns false if a pivot is zero or not
+// finite.  The pivot search compares the magnitudes' bit patterns as 64-bit
+// integers (non-negative doubles order like their patterns), so it runs on
+// the integer pipe instead of the narrow FP64 one; a NaN sorts above every
+// finite value, is picked, and fails the finiteness test.
 __device__ bool warp_lu(double* A, int* piv, int n) {
   const int lane = threadIdx.x & 31;
   bool ok = true;
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
+    long long best = -1;
     int bi = k;
     for (int i = k + lane; i < n; i += 32) {
-      const double v = fabs(A[i * n + k]);
+      const long long v = __double_as_longlong(A[i * n + k]) & 0x7FFFFFFFFFFFFFFFLL;
       if (v > best) { best = v; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(WFULL, best, o);
+      const long long ob = __shfl_xor_sync(WFULL, best, o);
       const int oi = __shfl_xor_sync(WFULL, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    ok = ok && (best > 0.0) && (best < INFINITY);
+    ok = ok && (best > 0) && (best < 0x7FF0000000000000LL);
     if (lane == 0) piv[k] = bi;
     if (bi != k) {
       for (int j = lane; j < n; j += 32) {
@@ -259,9 +278,10 @@ __device__ bool warp_lu(double* A, int* piv, int n) {
       }
     }
     __syncwarp();
-    const double inv = 1.0 / A[k * n + k];
+    const double inv = rcp_nr(A[k * n + k]);
     __syncwarp();
     for (int i = k + 1 + lane; i < n; i += 32) A[i * n + k] *= inv;
+    for (int i = lane; i < k; i += 32) A[i * n + k] *= inv;  // U'_ik = U_ik / U_kk (row i < k is final)
     if (lane == 0) A[k * n + k] = inv;
     __syncwarp();
     // trailing update of the m x m block: its elements are dealt to the lanes
@@ -308,13 +328,16 @@ __device__ void warp_solve(const double* A, const int* piv, double* x, int n) {
     for (int i = k + 1 + lane; i < n; i += 32) x[i] -= A[i * n + k] * xk;
     __syncwarp();
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const double xk = x[k] * A[k * n + k];
+  // back substitution on b~ (x_k = b~_k / U_kk): b~_i -= U'_ik b~_k for i < k,
+  // with U' = U scaled by its column pivots, then one scaling pass
+  for (int k = n - 1; k > 0; --k) {
+    const double bk = x[k];
     __syncwarp();
-    if (lane == 0) x[k] = xk;
-    for (int i = lane; i < k; i += 32) x[i] -= A[i * n + k] * xk;
+    for (int i = lane; i < k; i += 32) x[i] -= A[i * n + k] * bk;
     __syncwarp();
   }
+  for (int i = lane; i < n; i += 32) x[i] *= A[i * n + i];
+  __syncwarp();
 }
 
 }  // namespace df

@@ -168,14 +168,14 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
           last = false;
         }
       }
-      const double hgi = 1.0 / (h * tb.gamma);
+      const double ih = rcp_nr(h);
+      const double hgi = rcp_nr(h * tb.gamma);
       for (int e = lane; e < n * n; e += 32) {
         const int i = e / n, j = e - i * n;
         J[e] = (i == j ? hgi : 0.0) - J[e];
       }
       __syncwarp();
       bool ok = warp_lu(J, piv, n);
-      const double ih = 1.0 / h;
       for (int s = 0; s < tb.s; ++s) {
         if (s > 0 && tb.newf[s]) {
           for (int i = lane; i < n; i += 32) {
@@ -205,21 +205,24 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         const double sc = (i == 0 ? a.atolT : a.atolY) + a.rtol * fmax(fabs(y[i]), fabs(yn));
         e2 += (e / sc) * (e / sc);
       }
-      double en = sqrt(warp_sum(e2) / n);
-      ok = ok && isfinite(en);
+      // WRMS error norm: the accept test in FP64 (sum <= n), the step-size
+      // factors of the controller (see step_control) in FP32 on the wide pipe
+      const double esum = warp_sum(e2);
+      ok = ok && isfinite(esum);
+      const float en = sqrtf((float)esum * (1.0f / (float)n));
       __syncwarp();
-      if (ok && en <= 1.0) {
+      if (ok && esum <= (double)n) {
         for (int i = lane; i < n; i += 32) y[i] = ys[i];
         t = last ? a.dt : t + h;
         ++nacc;
         // elementary + Gustafsson predictive controller (see step_control)
-        const double e = fmax(en, 1e-10);
-        double fac = 0.9 * pow(e, -1.0 / tb.elo);
-        if (nacc > 1) fac = fmin(fac, 0.9 * (h / hacc) * pow(e * e / erracc, -1.0 / tb.elo));
-        fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+        const float e = fmaxf(en, 1e-10f), ie = -1.0f / (float)tb.elo;
+        float fac = 0.9f * powf(e, ie);
+        if (nacc > 1) fac = fminf(fac, 0.9f * ((float)h / (float)hacc) * powf(e * e / (float)erracc, ie));
+        fac = fminf(last_rej ? 1.0f : 6.0f, fmaxf(0.2f, fac));
         hacc = h;
-        erracc = fmax(1e-2, en);
-        h *= fac;
+        erracc = fmax(1e-2, (double)en);
+        h *= (double)fac;
         last_rej = false;
         pk.add(istep * a.dt + t0, fT);  // dT/dt at the start of an accepted substep
         if (t >= a.dt) {
@@ -228,9 +231,9 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
         }
       } else {
         ++nrej;
-        const double fmin = nacc == 0 ? 1e-4 : 0.2;
-        const double fac = ok ? fmax(fmin, 0.9 * pow(en, -1.0 / tb.elo)) : 0.25;
-        h *= fac;
+        const float fmn = nacc == 0 ? 1e-4f : 0.2f;
+        const float fac = ok ? fmaxf(fmn, 0.9f * powf(en, -1.0f / (float)tb.elo)) : 0.25f;
+        h *= (double)fac;
         last_rej = true;
       }
       if (!done) {
