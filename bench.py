@@ -36,10 +36,24 @@ UNIT = "cell-steps/s"
 # DP thread-instruction counters (2*DFMA + DADD + DMUL = 4.3845e10) of one timed
 # launch on the 2^20-cell field (the kernel generated for the mechanism, in the
 # autotuned 32-thread shape) divided by the 2199716 attempts that launch
-# counted (profiles/integrator_thread9_h2air_bimodal.md).
+# counted.
 FLOP_PER_SUBSTEP = 19932
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
 TRAFFIC_PER_LAUNCH = 232478208 + 236807424
+# hash of the device sources that kernel is built from, when the two counters
+# above were taken; a different hash at run time marks them stale in the line
+COUNTERS_SOURCES = ("integrate_thread.cuh", "rosenbrock.cuh", "chem_thread.cuh", "dev_common.cuh", "fastexp.cuh",
+                    "fastlog.cuh", "fastlog_table.inc", "codegen.cu")
+COUNTERS_SOURCE_HASH = "unset"
+
+
+def counters_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in COUNTERS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2210_07094_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
 
 
 def _rank_info():
@@ -630,9 +644,11 @@ def main():
     fp64_peak = g.value
     if FLOP_PER_SUBSTEP:
         achieved = FLOP_PER_SUBSTEP * subs / (t_local / args.steps) / 1e12
+        fresh = counters_source_hash() == COUNTERS_SOURCE_HASH
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e3, "unit": "TFLOP/s",
                 "frac": achieved / (fp64_peak / 1e3),
-                "traffic": TRAFFIC_PER_LAUNCH if ncells == NCELLS else None,
+                "counters_current": fresh,
+                "traffic": TRAFFIC_PER_LAUNCH if (ncells == NCELLS and fresh) else None,
                 "traffic_note": "ncu DRAM bytes of one 2^20-cell launch; 2.6x the 180 MB of cell state read "
                                 "and written, from 8-byte accesses in hottest-first cell order (32-byte sectors); "
                                 "0.1% of HBM bandwidth over the launch",
