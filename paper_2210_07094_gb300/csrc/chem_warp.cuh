@@ -32,7 +32,6 @@ __host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
   WarpWS w;
   int o = 0;
   w.y = o; o += n;
-  w.ys = o; o += n;
   w.f = o; o += n;
   w.wdot = o; o += N;
   w.C = o; o += N;
@@ -46,7 +45,11 @@ __host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
   w.dM = o; o += M;
   w.J = o; o += n * n;
   w.K = o; o += 6 * n;
-  w.piv = o; o += n;  // int storage in double slots
+  // the stage state shares the last stage vector's slot: it is read (f(ys))
+  // before that stage vector is written, and the candidate state overwrites
+  // it element by element after each lane has read its own elements
+  w.ys = w.K + 5 * n;
+  w.piv = o; o += (n + 1) / 2;  // ints, two per double slot
   w.total = (o + 1) & ~1;
   return w;
 }

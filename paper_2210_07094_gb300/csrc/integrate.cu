@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
           e += tb.e[s] * K[s * n + i];
         }
         ys[i] = yn;
-        const double sc = (i == 0 ? a.atolT : a.atolY) + a.rtol * fmax(fabs(y[i]), fabs(yn));
-        e2 += (e / sc) * (e / sc);
+        const double r = e * rcp_nr((i == 0 ? a.atolT : a.atolY) + a.rtol * fmax(fabs(y[i]), fabs(yn)));
+        e2 += r * r;
       }
       // WRMS error norm: the accept test in FP64 (sum <= n), the step-size
       // factors of the controller (see step_control) in FP32 on the wide pipe
@@ -462,14 +462,23 @@ int warp_shape(const df_mech* m, const WarpWS& L, bool want_stage, int max_warps
   const size_t per_warp = sizeof(double) * (size_t)L.total;
   const size_t fixed = sizeof(double) * 128;
   const size_t blob = sizeof(double) * (size_t)blob_smem_doubles(m->dims);
+  // the mechanism staged in shared memory where that costs no warp; where
+  // leaving it in global memory (read through L1) fits one more warp per
+  // block, more warps win (they keep the narrow FP64 pipe busier)
+  int best_w = 0, best_st = 0;
   for (int st = want_stage ? 1 : 0; st >= 0; --st) {
     const size_t base = fixed + (st ? blob : 0);
     if (base + per_warp > m->max_smem_optin) continue;
-    int w = (int)((m->max_smem_optin - base) / per_warp);
-    w = std::min(w, max_warps);
-    *warps = w;
-    *stage = st;
-    *smem = base + per_warp * w;
+    const int w = std::min((int)((m->max_smem_optin - base) / per_warp), max_warps);
+    if (w > best_w) {
+      best_w = w;
+      best_st = st;
+    }
+  }
+  if (best_w > 0) {
+    *warps = best_w;
+    *stage = best_st;
+    *smem = fixed + (best_st ? blob : 0) + per_warp * best_w;
     return DF_OK;
   }
   return set_error(DF_EUNSUPPORTED, "warp-path workspace exceeds shared memory");
