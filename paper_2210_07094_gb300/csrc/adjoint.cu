@@ -29,6 +29,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "common.cuh"
 #include "rosenbrock.cuh"
@@ -66,15 +67,35 @@ struct AdjArgs {
   double* stages;
 };
 
-template <int NS>
+// Per-thread shared-memory doubles.  Without KEEP (the reverse sweep
+// recomputes each step): Dual C, wdot, gRT, hRT, cpR, sigma, v (14 NS) + W
+// (n^2) + K, Kbar (12 n) + theta (M) + u, ud (2 NS) + Rbar (n).  With KEEP (the
+// forward sweep stores each accepted step's stages and LU factors in the
+// workspace and the reverse sweep reads them there): the dual vectors, then a
+// region of max(n^2, 6n + M + 2NS) that holds Kbar, theta, u, ud in the
+// reverse sweep and W in the forward sweep, then Rbar; the forward sweep's K
+// sits in the derivative halves of the dual vectors, unused until the reverse
+// sweep (6n <= 7NS for NS >= 6).  Less shared memory per thread, more warps
+// per SM on the narrow FP64 pipe.
+template <int NS, bool KEEP = false>
 __host__ __device__ constexpr int adj_ws_doubles(int M) {
-  // Dual C, wdot, gRT, hRT, cpR, sigma, v (14 NS) + W (n^2) + K, Kbar (12 n)
-  // + theta (M) + u, ud (2 NS) + Rbar (n)
-  return 16 * NS + (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
+  return KEEP ? 14 * NS + ((NS + 1) * (NS + 1) > 6 * (NS + 1) + M + 2 * NS ? (NS + 1) * (NS + 1)
+                                                                         : 6 * (NS + 1) + M + 2 * NS) +
+                    (NS + 1)
+              : 16 * NS + (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
 }
 
-template <int NS>
+// read-only view of the stored stages in the workspace: element i at p[i * s],
+// s = ncells (64-bit offsets)
+struct GV {
+  const double* p;
+  int64_t s;
+  __device__ __forceinline__ double operator[](int i) const { return p[(int64_t)i * s]; }
+};
+
+template <int NS, bool KEEP = false>
 __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
+  static_assert(!KEEP || 6 * (NS + 1) <= 7 * NS, "KEEP: the forward K must fit the dual derivative halves");
   constexpr int n = NS + 1;
   extern __shared__ double smem[];
   const int tid = threadIdx.x, stride = blockDim.x;
@@ -102,13 +123,17 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       hRT{vb + 6 * NS * stride, 2 * stride}, cpR{vb + 8 * NS * stride, 2 * stride},
       sg{vb + 10 * NS * stride, 2 * stride}, vs{vb + 12 * NS * stride, 2 * stride};
   double* rest = base + (14 * NS) * stride + tid;
-  SV Wv{rest, stride};
-  SV Kv{rest + n * n * stride, stride};
-  SV Kb{rest + (n * n + 6 * n) * stride, stride};
-  SV th{rest + (n * n + 12 * n) * stride, stride};
-  SV uu{rest + (n * n + 12 * n + M) * stride, stride};
-  SV ud{rest + (n * n + 12 * n + M + NS) * stride, stride};
-  SV vv{rest + (n * n + 12 * n + M + 2 * NS) * stride, stride};
+  const int region = KEEP ? (n * n > 6 * n + M + 2 * NS ? n * n : 6 * n + M + 2 * NS) : n * n + 12 * n + M + 2 * NS;
+  SV Wv{rest, stride};  // the forward sweep's W (both layouts) and the recomputed one
+  SV Kv = KEEP ? SV{vb + 1, 2 * stride} : SV{rest + n * n * stride, stride};
+  const int kstride = KEEP ? 2 * stride : stride;  // stride of a stage vector inside Kv
+  double* kb0 = KEEP ? rest : rest + (n * n + 6 * n) * stride;
+  SV Kb{kb0, stride};
+  SV th{kb0 + 6 * n * stride, stride};
+  SV uu{kb0 + (6 * n + M) * stride, stride};
+  SV ud{kb0 + (6 * n + M + NS) * stride, stride};
+  SV vv{rest + region * stride, stride};
+  const int th_off = 14 * NS + (KEEP ? 6 * n : n * n + 12 * n);  // theta's offset (units of stride)
   const RosTab& tb = c_tab_adj;
   for (int j = 0; j < M; ++j) th[j] = 0.0;
 
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       for (int i = 0; i < n; ++i) yold[i] = y[i];
       int pv[n];
       const bool sok = ros_attempt<NS>(mv, tb, pc, y, h, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv,
-                                       stride, ynew, en, pv, nacc == 0 && nrej == 0, &last);
+                                       kstride, ynew, en, pv, nacc == 0 && nrej == 0, &last);
       const double hstep = h;  // the step actually taken (the first one may be cut)
       const int before = nacc;
       step_control(tb, sok, en, last, a.dt, y, ynew, t, h, nacc, nrej, last_rej, done, ss);
@@ -173,6 +198,9 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
           done = true;
         }
       }
+    }
+    if (KEEP) {  // the forward sweep's W overlaid theta, u, ud and Kbar
+      for (int j = 0; j < M; ++j) th[j] = 0.0;
     }
     double lam[n];
     if (status == DF_CELL_OK) {
@@ -216,15 +244,29 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
         for (int i = 0; i < n; ++i) yi[i] = slot[i];
         double hs = slot[n];
         int piv[n];
-        if (a.stages) {  // the forward sweep kept this step's stages and factors
+        // this step's stages and LU factors: read in place from the workspace
+        // (KEEP), copied from it, or recomputed
+        typedef typename std::conditional<KEEP, GV, SV>::type StageView;
+        StageView Wr, Kr;
+        if constexpr (KEEP) {
           const double* sp = a.stages + (int64_t)istep * (7 * n + n * n) * a.ncells + cell;
-          for (int i = 0; i < 6 * n; ++i) Kv[i] = sp[i * a.ncells];
-          for (int i = 0; i < n * n; ++i) Wv[i] = sp[(6 * n + i) * a.ncells];
+          Kr = GV{sp, a.ncells};
+          Wr = GV{sp + (int64_t)6 * n * a.ncells, a.ncells};
 #pragma unroll
-          for (int i = 0; i < n; ++i) piv[i] = (int)sp[(6 * n + n * n + i) * a.ncells];
+          for (int i = 0; i < n; ++i) piv[i] = (int)sp[(int64_t)(6 * n + n * n + i) * a.ncells];
         } else {
-          ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
-                          en, piv);
+          if (a.stages) {  // the forward sweep kept this step's stages and factors
+            const double* sp = a.stages + (int64_t)istep * (7 * n + n * n) * a.ncells + cell;
+            for (int i = 0; i < 6 * n; ++i) Kv[i] = sp[i * a.ncells];
+            for (int i = 0; i < n * n; ++i) Wv[i] = sp[(6 * n + i) * a.ncells];
+#pragma unroll
+            for (int i = 0; i < n; ++i) piv[i] = (int)sp[(6 * n + n * n + i) * a.ncells];
+          } else {
+            ros_attempt<NS>(mv, tb, pc, yi, hs, a.rtol, a.atolY, a.atolT, C, wd, gRT, hRT, cpR, Wv, Kv, stride, ynew,
+                            en, piv);
+          }
+          Kr = Kv;
+          Wr = Wv;
         }
         const double ih = 1.0 / hs;
         double yb[n];
@@ -242,14 +284,14 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
           for (int k = 0; k < n; ++k) {
             double acc = r[k];
 #pragma unroll
-            for (int j = 0; j < k; ++j) acc -= Wv[j * n + k] * r[j];
-            r[k] = acc * Wv[k * n + k];
+            for (int j = 0; j < k; ++j) acc -= Wr[j * n + k] * r[j];
+            r[k] = acc * Wr[k * n + k];
           }
 #pragma unroll
           for (int k = n - 1; k >= 0; --k) {
             double acc = r[k];
 #pragma unroll
-            for (int j = k + 1; j < n; ++j) acc -= Wv[j * n + k] * r[j];
+            for (int j = k + 1; j < n; ++j) acc -= Wr[j * n + k] * r[j];
             r[k] = acc;
           }
 #pragma unroll
@@ -273,7 +315,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
 #pragma unroll
           for (int i = 0; i < n; ++i) {
             double acc = yi[i];
-            for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kv[j * n + i];
+            for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kr[j * n + i];
             ysg[i] = acc;
           }
           {
@@ -290,7 +332,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
           {
             Dual yd[n], fd[n], bd[n];
 #pragma unroll
-            for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kv[s * n + i]);
+            for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kr[s * n + i]);
             ThetaHook hk{1, vv, 0.0, th, uu, ud};
             eval_vjp<NS, Dual>(mv, pc, yd, r, bd, fd, dC, dW, dG, dH, dCp, dS, dV, &hk);
 #pragma unroll
@@ -318,7 +360,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
   if (a.partial) {
     for (int j = tid; j < M; j += stride) {
       double acc = 0.0;
-      for (int q = 0; q < stride; ++q) acc += base[(size_t)(14 * NS + n * n + 12 * n + j) * stride + q];
+      for (int q = 0; q < stride; ++q) acc += base[(size_t)(th_off + j) * stride + q];
       a.partial[(int64_t)blockIdx.x * M + j] = acc;
     }
   }
@@ -373,17 +415,18 @@ bool adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool wit
   return true;
 }
 
-template <int NS>
-static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
+template <int NS, bool KEEP>
+static int adjoint_dispatch_layout(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
   const int threads = ADJ_THREADS;
-  size_t sm = sizeof(double) * (128 + ((m->dims.total + 1) & ~1) + (size_t)adj_ws_doubles<NS>(m->dims.M) * threads);
+  const size_t per = (size_t)adj_ws_doubles<NS, KEEP>(m->dims.M) * threads;
+  size_t sm = sizeof(double) * (128 + ((m->dims.total + 1) & ~1) + per);
   a.stage_blob = 1;
   if (sm > m->max_smem_optin) {
     a.stage_blob = 0;
-    sm = sizeof(double) * (128 + (size_t)adj_ws_doubles<NS>(m->dims.M) * threads);
+    sm = sizeof(double) * (128 + per);
   }
   if (sm > m->max_smem_optin) return set_error(DF_EUNSUPPORTED, "adjoint workspace exceeds shared memory");
-  auto kf = k_adjoint_thread<NS>;
+  auto kf = k_adjoint_thread<NS, KEEP>;
   int rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                       "set adjoint shared memory");
   if (rc) return rc;
@@ -396,6 +439,16 @@ static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double
     rc = cuda_check(cudaGetLastError(), "adjoint reduction launch");
   }
   return rc;
+}
+
+// the smaller layout when the stages are kept in the workspace and the
+// forward sweep's stage vectors fit the dual derivative halves
+template <int NS>
+static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
+  if constexpr (6 * (NS + 1) <= 7 * NS) {
+    if (a.stages) return adjoint_dispatch_layout<NS, true>(m, a, st, g_lnA);
+  }
+  return adjoint_dispatch_layout<NS, false>(m, a, st, g_lnA);
 }
 
 int launch_adjoint(const df_mech* m, int64_t ncells, const double* T0, const double* p, const double* Y0,
