@@ -156,10 +156,25 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     } else {
       o << "    RateOutT<double> ro;\n    rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, ro);\n";
     }
-    o
-      << "    if (ro.active) {\n      const double q = ro.q;\n";
-    for (int i = 0; i < nr; ++i) o << "      wdot[" << r[i] << "] -= q;\n";
-    for (int i = 0; i < np; ++i) o << "      wdot[" << p[i] << "] += q;\n";
+    // The species of the reaction with their net stoichiometric coefficient
+    // nu_k (products minus reactants): one update of wdot and of each Jacobian
+    // row per species, scaled by nu_k, instead of one per reactant or product
+    // entry (a species entered twice, or on both sides, is touched once or not
+    // at all).  The columns d q / d C_l likewise sum the entries of species l.
+    std::vector<int> spc;
+    std::vector<int> nu(N, 0);
+    for (int i = 0; i < nr; ++i) nu[r[i]] -= 1;
+    for (int i = 0; i < np; ++i) nu[p[i]] += 1;
+    for (int i = 0; i < nr; ++i)
+      if (std::find(spc.begin(), spc.end(), r[i]) == spc.end()) spc.push_back(r[i]);
+    for (int i = 0; i < np; ++i)
+      if (std::find(spc.begin(), spc.end(), p[i]) == spc.end()) spc.push_back(p[i]);
+    auto nu_times = [](int v, const std::string& x) {
+      return v == 1 ? "(" + x + ")" : v == -1 ? "-(" + x + ")" : std::to_string(v) + ".0 * (" + x + ")";
+    };
+    o << "    if (ro.active) {\n      const double q = ro.q;\n";
+    for (int k : spc)
+      if (nu[k] != 0) o << "      wdot[" << k << "] += " << nu_times(nu[k], "q") << ";\n";
     o << "      if (WITH_J) {\n"
       << "        const double dr0 = ro.fk * ro.cr[1] * ro.cr[2];\n"
       << "        const double dr1 = ro.fk * ro.cr[0] * ro.cr[2];\n"
@@ -168,15 +183,23 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
       << "        const double dp1 = -(ro.rk * ro.cp[0] * ro.cp[2]);\n"
       << "        const double dp2 = -(ro.rk * ro.cp[0] * ro.cp[1]);\n"
       << "        (void)dr1; (void)dr2; (void)dp1; (void)dp2;\n";
-    for (int a = 0; a < nr + np; ++a) {
-      const bool isr = a < nr;
-      const int row = 1 + (isr ? r[a] : p[a - nr]);
-      const char* sg = isr ? "-" : "";
-      o << "        Jv[" << row * n << "] += " << sg << "(ro.dqdT);\n";
-      for (int i = 0; i < nr; ++i) o << "        Jv[" << row * n + 1 + r[i] << "] += " << sg << "(dr" << i << ");\n";
-      for (int i = 0; i < np; ++i) o << "        Jv[" << row * n + 1 + p[i] << "] += " << sg << "(dp" << i << ");\n";
+    // d q / d C_l of each species of the reaction
+    for (int l : spc) {
+      std::string terms;
+      for (int i = 0; i < nr; ++i)
+        if (r[i] == l) terms += (terms.empty() ? "" : " + ") + std::string("dr") + std::to_string(i);
+      for (int i = 0; i < np; ++i)
+        if (p[i] == l) terms += (terms.empty() ? "" : " + ") + std::string("dp") + std::to_string(i);
+      o << "        const double dq" << l << " = " << terms << ";\n";
+    }
+    for (int k : spc) {
+      if (nu[k] == 0) continue;
+      const int row = 1 + k;
+      o << "        Jv[" << row * n << "] += " << nu_times(nu[k], "ro.dqdT") << ";\n";
+      for (int l : spc)
+        o << "        Jv[" << row * n + 1 + l << "] += " << nu_times(nu[k], "dq" + std::to_string(l)) << ";\n";
       if (type != 0) {
-        o << "        {\n          const double cM = " << sg << "(ro.dqdM);\n";
+        o << "        {\n          const double cM = " << nu_times(nu[k], "ro.dqdM") << ";\n";
         for (int l = 0; l < N; ++l)
           o << "          Jv[" << row * n + 1 + l << "] += cM * " << lit(eff(l)) << ";\n";
         o << "        }\n";
