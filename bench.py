@@ -376,6 +376,8 @@ def profile_case(args):
     second hidden layer of an inference chunk) after one warm-up launch.
     chon: one warp-per-cell integrator launch on 8192 cells of the 50-species
     field.
+    dnn-train: 23 training steps of the 11-1600-800-400-9 network on 4096-pair
+    batches (the first eager, the second captured, then graph replays).
     dnn-infer: two inference passes of an (untrained) network over the held-out
     states of the learned-surrogate workload (2^22 trajectory states, 2% of them
     moved 50-300 K outside the training T range, half below, half above).
@@ -447,6 +449,28 @@ def profile_case(args):
         print(json.dumps({"case": "chon", "cells": 8192, "ms": e0.elapsed_time(e1), "accepted": acc,
                           "rejected": rej, "failed": int((st != 0).sum())}))
         return 0
+    if args.profile_case == "dnn-train":
+        import paper_2210_07094_gb300 as df
+        from paper_2210_07094_gb300 import surrogate, synth
+        mech = synth.h2_air_mechanism()
+        m = df.Mechanism(mech)
+        Ts, p, Ys = surrogate.trajectories(m, mech, 1 << 12, 8)
+        T0, P0, Y0, T1, Y1 = surrogate.pairs(Ts, p, Ys)
+        dnn = df.Dnn(df.dnn_default_opts(), seed=1)
+        dnn.fit_norm(T0, P0, Y0, Y1)
+        B = 4096
+        args_b = [a[..., :B].contiguous() for a in (T0, P0, Y0, Y1)]
+        for _ in range(3):  # eager first step, graph capture, first replay
+            dnn.train_step(*args_b, lr=1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            dnn.train_step(*args_b, lr=1e-3, want_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "dnn-train", "batch": B, "steps": 20, "ms_per_step": e0.elapsed_time(e1) / 20}))
+        return 0
     if args.profile_case == "dnn-infer":
         import paper_2210_07094_gb300 as df
         from paper_2210_07094_gb300 import surrogate, synth
@@ -508,7 +532,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the adjoint and 50-species measurements")
     ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
-    ap.add_argument("--profile-case", default=None, choices=["gemm-l2", "dnn-infer", "chon", "h2", "fp64-chains"],
+    ap.add_argument("--profile-case", default=None,
+                    choices=["gemm-l2", "dnn-infer", "dnn-train", "chon", "h2", "fp64-chains"],
                     help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")
