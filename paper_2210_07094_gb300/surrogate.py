@@ -97,13 +97,16 @@ def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, 
     step hands the library contiguous views (no per-step gathers).  With a
     time budget the schedule spans the steps that fit in it: the step rate is
     measured over the first 200 steps and the cosine's length set from it, so
-    the learning rate has decayed to lr1 when the budget ends."""
+    the learning rate has decayed to lr1 when the budget ends.  The rate is
+    taken over steps 200-400, after the one-time set-up of the first steps
+    (the graph capture of the step)."""
     import torch
     n = T.numel()
     batch = min(batch, n)
     steps_per_epoch = max(1, n // batch)
     total = max(1, int(epochs * steps_per_epoch))
-    probe = 200 if time_budget is not None else -1
+    probe0, probe = (200, 400) if time_budget is not None else (-1, -1)
+    t_probe0 = None
     g = torch.Generator(device=T.device).manual_seed(seed)
     losses = []
     t0 = time.time()
@@ -117,10 +120,14 @@ def train(dnn: Dnn, T, p, Y, Yn, epochs: float, batch: int, lr0=1e-3, lr1=1e-5, 
             Ps = p[perm].view(steps_per_epoch, batch)
             Ys = Y[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
             Yns = Yn[:, perm].view(N, steps_per_epoch, batch).permute(1, 0, 2).contiguous()
+        if s == probe0:
+            torch.cuda.synchronize()
+            t_probe0 = time.time()
         if s == probe:  # steps that fit in the budget at the measured rate
             torch.cuda.synchronize()
-            rate = s / max(time.time() - t0, 1e-9)
-            total = min(total, max(s + 1, int(rate * time_budget)))
+            now = time.time()
+            rate = (probe - probe0) / max(now - t_probe0, 1e-9)
+            total = min(total, max(s + 1, s + int(rate * (time_budget - (now - t0)))))
         lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * min(s / total, 1.0)))
         want = (s % 50 == 0) or s == total - 1
         loss = dnn.train_step(Ts[k], Ps[k], Ys[k], Yns[k], lr, want_loss=want)
