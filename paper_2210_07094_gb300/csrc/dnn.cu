@@ -17,7 +17,7 @@
 namespace df {
 
 constexpr int DNN_IN = 16;   // padded feature count (2 + N <= 16)
-constexpr int DNN_OUT = 16;  // padded output count (N <= 16)
+constexpr int DNN_OUT = 16;  // padded output count (N <= 14: two inputs are T and p)
 
 struct DnnLayout {
   int w[3];
@@ -138,13 +138,25 @@ __global__ void k_dnn_init(float* P, DnnLayout L, int n_in, int n_out, uint64_t 
   }
 }
 
+// bf16 copies of W [out][in]: wb in the same layout and wtb = W^T [in][out],
+// through a 32 x 32 shared-memory tile so both writes coalesce
 __global__ void k_dnn_cast(const float* W, int out, int in, __nv_bfloat16* wb, __nv_bfloat16* wtb) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)out * in) return;
-  const int r = (int)(i / in), c = (int)(i % in);
-  const __nv_bfloat16 b = __float2bfloat16_rn(W[i]);
-  wb[i] = b;
-  wtb[(int64_t)c * out + r] = b;
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j, c = c0 + tx;
+    if (r < out && c < in) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(W[(int64_t)r * in + c]);
+      wb[(int64_t)r * in + c] = b;
+      tile[j][tx] = b;
+    }
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int c = c0 + j, r = r0 + tx;
+    if (r < out && c < in) wtb[(int64_t)c * out + r] = tile[tx][j];
+  }
 }
 
 // Box-Cox transform in FP64: F(Y) = (max(Y, 0)^lambda - 1) / lambda
@@ -218,6 +230,50 @@ __global__ void k_dnn_features(FeatArgs a) {
       const double du = (yn - yl[k]) / a.lam;
       t[k] = (float)((du - mean_out[k]) / std_out[k]);
     }
+  }
+}
+
+// Training features, one thread per (row, feature): the same values as
+// k_dnn_features (F(Y) in FP64, rounded to FP32, z-scored in FP32, rounded to
+// BF16; the target's change of F(Y) in FP64), spread over 16 threads per row
+// so that a 4096-row batch occupies the SMs (a thread per row leaves the
+// FP64 log and exponential chains of nine species exposed).  Writes X [n][16],
+// XT [16][ldT] and tgt [n][16]; padding features and outputs are zero.
+__global__ void k_dnn_features_train(FeatArgs a) {
+  __shared__ double2 tab[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t >> 4;
+  const int k = (int)(t & 15);
+  if (i >= a.n) return;
+  const int64_t c = a.c0 + i;
+  const float* mean_in = a.norm;
+  const float* std_in = a.norm + DNN_IN;
+  const float* mean_out = a.norm + 4 * DNN_IN;
+  const float* std_out = a.norm + 4 * DNN_IN + DNN_OUT;
+  float xk = 0.0f, tk = 0.0f;
+  if (k == 0) {
+    xk = ((float)a.T[c] - mean_in[0]) / std_in[0];
+  } else if (k == 1) {
+    xk = ((float)a.p[c] - mean_in[1]) / std_in[1];
+  } else if (k < 2 + a.N) {
+    const int sp = k - 2;
+    const double yl = ylam(a.Y[(int64_t)sp * a.ncells + c], a.lam, tab);
+    const float f = (float)((yl - 1.0) / a.lam);
+    xk = (f - mean_in[k]) / std_in[k];
+    const double yn = ylam(a.Ynext[(int64_t)sp * a.ncells + c], a.lam, tab);
+    const double du = (yn - yl) / a.lam;
+    tk = (float)((du - mean_out[sp]) / std_out[sp]);
+  }
+  const __nv_bfloat16 xb = __float2bfloat16_rn(xk);
+  a.X[i * DNN_IN + k] = xb;
+  a.XT[(int64_t)k * a.ldT + i] = xb;
+  // outputs: species sp at column sp (the target row is [16])
+  if (a.tgt) {
+    float* trow = a.tgt + i * DNN_OUT;
+    if (k >= 2 && k < 2 + a.N) trow[k - 2] = tk;
+    if (k >= a.N) trow[k] = 0.0f;  // columns N .. 15 are padding
   }
 }
 
@@ -383,20 +439,24 @@ __global__ void k_sum_partials(const double* part, int n, double* out) {
   }
 }
 
-// bias gradient: db[r] = sum over the first ncol columns of the bf16 row r (fixed order)
+// bias gradient: db[r] = sum over the first ncol columns of the bf16 row r, in
+// a fixed order (each thread a strided partial, then a tree): FP32 sums, whose
+// error (~(ncol / blockDim + log2 blockDim) ulp of the sum of |terms|) sits far
+// below the BF16 rounding of the terms; FP64 on the narrow pipe cost more than
+// the GEMMs of the step
 __global__ void k_dnn_rowsum(const __nv_bfloat16* A, int64_t ld, int rows, int64_t ncol, float* db) {
   const int r = blockIdx.x;
   if (r >= rows) return;
-  __shared__ double red[256];
-  double acc = 0.0;
-  for (int64_t c = threadIdx.x; c < ncol; c += blockDim.x) acc += (double)__bfloat162float(A[(int64_t)r * ld + c]);
+  __shared__ float red[256];
+  float acc = 0.0f;
+  for (int64_t c = threadIdx.x; c < ncol; c += blockDim.x) acc += __bfloat162float(A[(int64_t)r * ld + c]);
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[r] = (float)red[0];
+  if (threadIdx.x == 0) db[r] = red[0];
 }
 
 // sc = {lr, 1 - beta1^t, 1 - beta2^t} of this step (device memory, so a
@@ -657,9 +717,8 @@ static int dev_alloc(void** p, size_t bytes) {
 static int dnn_cast_all(df_dnn* d, cudaStream_t st) {
   for (int l = 0; l < 4; ++l) {
     const int out = d->L.out(l), in = d->L.in(l);
-    const int64_t n = (int64_t)out * in;
-    k_dnn_cast<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d->params + d->L.off[2 * l], out, in, d->wb[l],
-                                                           d->wtb[l]);
+    const dim3 grid((unsigned)((in + 31) / 32), (unsigned)((out + 31) / 32));
+    k_dnn_cast<<<grid, dim3(32, 8), 0, st>>>(d->params + d->L.off[2 * l], out, in, d->wb[l], d->wtb[l]);
   }
   return cuda_check(cudaGetLastError(), "weight cast");
 }
@@ -1004,7 +1063,7 @@ static int dnn_grad_enqueue(df_dnn* d, int64_t n, int64_t n_norm, cudaStream_t s
   fa.XT = d->XT;
   fa.ldT = B;
   fa.tgt = d->tgt;
-  k_dnn_features<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(fa);
+  k_dnn_features_train<<<(unsigned)((16 * n + 255) / 256), 256, 0, st>>>(fa);
   if (M > n) k_dnn_zero_rows<<<1, 8, 0, st>>>(d->X, d->XT, B, n, M);
   float* P = d->params;
   float* G = d->grads;

@@ -33,11 +33,14 @@ def test_generated_source_has_one_block_per_reaction(tmp_path):
     blocks = re.findall(r"// reaction (\d+)\n", src)
     assert [int(b) for b in blocks] == list(range(len(mech["reactions"])))
     names = [s["name"] for s in mech["species"]]
-    # every species a reaction changes appears as a literal production-rate index
+    # every species a reaction changes (net stoichiometric coefficient nonzero)
+    # appears as a literal production-rate index; one it leaves unchanged
+    # (O in O2 + H + O <=> O + HO2) does not
     for j, r in enumerate(mech["reactions"]):
-        body = src.split(f"// reaction {j}\n")[1].split("// reaction")[0]
-        for k in list(r["reactants"]) + list(r["products"]):
-            assert f"wdot[{names.index(k)}]" in body, (j, k)
+        body = src.split(f"// reaction {j}\n")[1].split("// reaction")[0].split("double Hw")[0]
+        for k in set(r["reactants"]) | set(r["products"]):
+            net = r["products"].get(k, 0) - r["reactants"].get(k, 0)
+            assert (f"wdot[{names.index(k)}]" in body) == (net != 0), (j, k, net)
 
 
 def test_generated_source_rejects_a_bad_file(tmp_path):
