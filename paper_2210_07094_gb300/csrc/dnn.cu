@@ -233,48 +233,48 @@ __global__ void k_dnn_features(FeatArgs a) {
   }
 }
 
-// Training features, one thread per (row, feature): the same values as
+// Training features, one thread per (row, species): the same values as
 // k_dnn_features (F(Y) in FP64, rounded to FP32, z-scored in FP32, rounded to
-// BF16; the target's change of F(Y) in FP64), spread over 16 threads per row
-// so that a 4096-row batch occupies the SMs (a thread per row leaves the
-// FP64 log and exponential chains of nine species exposed).  Writes X [n][16],
-// XT [16][ldT] and tgt [n][16]; padding features and outputs are zero.
+// BF16; the target's change of F(Y) in FP64), with the FP64 transforms of a
+// row spread over N threads so that a 4096-row batch occupies the SMs and no
+// lane of the narrow FP64 pipe idles (a thread per row left the log and
+// exponential chains of all species exposed).  The thread of species s also
+// writes the row's columns s, s + N, ... of the 16 - N inputs that are not
+// species (T, p, zero padding) and of the 16 - N zero target columns.
+// Writes X [n][16], XT [16][ldT] and tgt [n][16].
 __global__ void k_dnn_features_train(FeatArgs a) {
   __shared__ double2 tab[64];
   for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
   __syncthreads();
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t >> 4;
-  const int k = (int)(t & 15);
+  const int64_t i = t / a.N;
+  const int sp = (int)(t - i * a.N);
   if (i >= a.n) return;
   const int64_t c = a.c0 + i;
   const float* mean_in = a.norm;
   const float* std_in = a.norm + DNN_IN;
   const float* mean_out = a.norm + 4 * DNN_IN;
   const float* std_out = a.norm + 4 * DNN_IN + DNN_OUT;
-  float xk = 0.0f, tk = 0.0f;
-  if (k == 0) {
-    xk = ((float)a.T[c] - mean_in[0]) / std_in[0];
-  } else if (k == 1) {
-    xk = ((float)a.p[c] - mean_in[1]) / std_in[1];
-  } else if (k < 2 + a.N) {
-    const int sp = k - 2;
-    const double yl = ylam(a.Y[(int64_t)sp * a.ncells + c], a.lam, tab);
-    const float f = (float)((yl - 1.0) / a.lam);
-    xk = (f - mean_in[k]) / std_in[k];
-    const double yn = ylam(a.Ynext[(int64_t)sp * a.ncells + c], a.lam, tab);
-    const double du = (yn - yl) / a.lam;
-    tk = (float)((du - mean_out[sp]) / std_out[sp]);
+  const double yl = ylam(a.Y[(int64_t)sp * a.ncells + c], a.lam, tab);
+  const float f = (float)((yl - 1.0) / a.lam);
+  const __nv_bfloat16 xs = __float2bfloat16_rn((f - mean_in[2 + sp]) / std_in[2 + sp]);
+  a.X[i * DNN_IN + 2 + sp] = xs;
+  a.XT[(int64_t)(2 + sp) * a.ldT + i] = xs;
+  const double yn = ylam(a.Ynext[(int64_t)sp * a.ncells + c], a.lam, tab);
+  const double du = (yn - yl) / a.lam;
+  float* trow = a.tgt + i * DNN_OUT;
+  trow[sp] = (float)((du - mean_out[sp]) / std_out[sp]);
+  // inputs other than species: 0 -> T, 1 -> p, then the padding 2 + N .. 15
+  for (int e = sp; e < DNN_IN - a.N; e += a.N) {
+    const int k = e < 2 ? e : e + a.N;
+    float xk = 0.0f;
+    if (k == 0) xk = ((float)a.T[c] - mean_in[0]) / std_in[0];
+    if (k == 1) xk = ((float)a.p[c] - mean_in[1]) / std_in[1];
+    const __nv_bfloat16 xb = __float2bfloat16_rn(xk);
+    a.X[i * DNN_IN + k] = xb;
+    a.XT[(int64_t)k * a.ldT + i] = xb;
   }
-  const __nv_bfloat16 xb = __float2bfloat16_rn(xk);
-  a.X[i * DNN_IN + k] = xb;
-  a.XT[(int64_t)k * a.ldT + i] = xb;
-  // outputs: species sp at column sp (the target row is [16])
-  if (a.tgt) {
-    float* trow = a.tgt + i * DNN_OUT;
-    if (k >= 2 && k < 2 + a.N) trow[k - 2] = tk;
-    if (k >= a.N) trow[k] = 0.0f;  // columns N .. 15 are padding
-  }
+  for (int e = a.N + sp; e < DNN_OUT; e += a.N) trow[e] = 0.0f;
 }
 
 // Training-range test on the raw variables: the Box-Cox transform is monotonic,
@@ -402,9 +402,12 @@ __global__ void k_dnn_zero_rows(__nv_bfloat16* X, __nv_bfloat16* XT, int64_t ldT
 // mean when n_norm = n; a shard's share of the mean over n_norm rows
 // otherwise); dU = dloss/dU as bf16 [rows][16] and its transpose [16][ldT];
 // per-block partial sums of the squared errors
+// rows per block of the loss kernel (a 4096-row batch spreads over 64 SMs)
+constexpr int LOSS_ROWS = 64;
+
 __global__ void k_dnn_loss(const float* U, const float* tgt, int64_t n, int64_t n_norm, int64_t nrows, int N,
                            __nv_bfloat16* dU, __nv_bfloat16* dUT, int64_t ldT, double* part) {
-  __shared__ double red[256];
+  __shared__ double red[LOSS_ROWS];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (i < nrows) {
@@ -431,12 +434,15 @@ __global__ void k_dnn_loss(const float* U, const float* tgt, int64_t n, int64_t 
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// out = sum of the n partials in a fixed order (lane-strided sums, then a
+// fixed shuffle tree; one warp)
 __global__ void k_sum_partials(const double* part, int n, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    out[0] = s;
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[0] = s;
 }
 
 // bias gradient: db[r] = sum over the first ncol columns of the bf16 row r, in
@@ -766,7 +772,7 @@ static int dnn_train_buffers(df_dnn* d) {
   rc = rc ? rc : dev_alloc((void**)&d->tgt, B * DNN_OUT * 4);
   rc = rc ? rc : dev_alloc((void**)&d->dU, B * DNN_OUT * 2);
   rc = rc ? rc : dev_alloc((void**)&d->dUT, B * DNN_OUT * 2);
-  rc = rc ? rc : dev_alloc((void**)&d->loss_part, ((B + 255) / 256 + 1) * 8);
+  rc = rc ? rc : dev_alloc((void**)&d->loss_part, ((B + LOSS_ROWS - 1) / LOSS_ROWS + 1) * 8);
   rc = rc ? rc : dev_alloc((void**)&d->bT, B * 8);
   rc = rc ? rc : dev_alloc((void**)&d->bp, B * 8);
   rc = rc ? rc : dev_alloc((void**)&d->bY, B * d->o.n_species * 8);
@@ -1063,7 +1069,7 @@ static int dnn_grad_enqueue(df_dnn* d, int64_t n, int64_t n_norm, cudaStream_t s
   fa.XT = d->XT;
   fa.ldT = B;
   fa.tgt = d->tgt;
-  k_dnn_features_train<<<(unsigned)((16 * n + 255) / 256), 256, 0, st>>>(fa);
+  k_dnn_features_train<<<(unsigned)(((int64_t)N * n + 255) / 256), 256, 0, st>>>(fa);
   if (M > n) k_dnn_zero_rows<<<1, 8, 0, st>>>(d->X, d->XT, B, n, M);
   float* P = d->params;
   float* G = d->grads;
@@ -1078,8 +1084,8 @@ static int dnn_grad_enqueue(df_dnn* d, int64_t n, int64_t n_norm, cudaStream_t s
     rc = gemm(d, d->H[2], 0, d->wb[3], 0, (int)M, DNN_OUT, L.w[2], EPI_F32, P + L.off[7], d->U, DNN_OUT, nullptr, 0,
               nullptr, 0, nullptr, 0, st);
   if (rc) return rc;
-  const int nbl = (int)((M + 255) / 256);
-  k_dnn_loss<<<nbl, 256, 0, st>>>(d->U, d->tgt, n, n_norm, M, N, d->dU, d->dUT, B, d->loss_part);
+  const int nbl = (int)((M + LOSS_ROWS - 1) / LOSS_ROWS);
+  k_dnn_loss<<<nbl, LOSS_ROWS, 0, st>>>(d->U, d->tgt, n, n_norm, M, N, d->dU, d->dUT, B, d->loss_part);
   k_sum_partials<<<1, 32, 0, st>>>(d->loss_part, nbl, d->loss_part + nbl);
   // backward: layer 4
   rc = gemm(d, d->dUT, (int)B, d->HT[2], (int)B, DNN_OUT, L.w[2], (int)M, EPI_F32, nullptr, G + L.off[6], L.w[2],
@@ -1148,7 +1154,7 @@ static int dnn_set_step_scalars(df_dnn* d, float lr, cudaStream_t st) {
 static int train_step_loss(df_dnn* d, int64_t n, int64_t n_norm, int rc, float* loss_out, cudaStream_t st) {
   if (!rc && loss_out) {
     const int64_t M = (n + 7) / 8 * 8;
-    const int nbl = (int)((M + 255) / 256);
+    const int nbl = (int)((M + LOSS_ROWS - 1) / LOSS_ROWS);
     double l = 0.0;
     rc = cuda_check(cudaMemcpyAsync(&l, d->loss_part + nbl, 8, cudaMemcpyDeviceToHost, st), "read loss");
     if (!rc) rc = check_err_flag(d, st);

@@ -53,11 +53,18 @@ static int make_tmap(CUtensorMap* m, const void* ptr, int64_t rows, int64_t K, i
   return DF_OK;
 }
 
-constexpr int GEMM_STAGES = 3;
+// ring depth of the one-tile-per-CTA kernel: six stages (192 KB) for the
+// 128-wide tile, whose main users are the weight gradients (K = the batch,
+// 4096: a three-stage ring left the loads' latency exposed), three for the
+// 64- and 256-wide tiles (the 64-wide output layer keeps three CTAs per SM)
+template <int BN>
+constexpr int gemm_stages() {
+  return BN == 128 ? 6 : 3;
+}
 
 template <int BN>
 static size_t gemm_smem() {
-  return (size_t)GEMM_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
+  return (size_t)gemm_stages<BN>() * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) + 1024 + 256;
 }
 
 // out0[r][c] = sum_z ws[z][r][c] (+ bias[c]), z in order
@@ -77,7 +84,7 @@ static int gemm_launch_bn(const void* A, const void* B, const GemmParams& P, cud
   int rc = make_tmap(&ta, A, P.M, P.K, P.ldA, GEMM_BM);
   if (!rc) rc = make_tmap(&tb, B, P.N, P.K, P.ldB, BN);
   if (rc) return rc;
-  auto kf = k_gemm_tc<BN, GEMM_STAGES>;
+  auto kf = k_gemm_tc<BN, gemm_stages<BN>()>;
   const size_t sm = gemm_smem<BN>();
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -148,7 +155,7 @@ static int gemm_launch_pers_mode(const CUtensorMap& ta, const CUtensorMap& tb, c
   }
   auto kf = k_gemm_tc_pers<BN, PERS_STAGES, MODE, EW>;
   const size_t sm = (size_t)PERS_STAGES * (GEMM_BM * GEMM_BK * 2 + BN * GEMM_BK * 2) +
-                    (MODE == EPI_GELU_BF16 ? pers_stage_c_bytes(EW) : 0) + 1024 + 256;
+                    pers_epi_bytes(MODE, EW) + 1024 + 256;
   static int nsm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -195,13 +202,20 @@ static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, c
 // tile, so a tile costs about (BN + 128) column-units; minimise
 // ceil(N / BN) * (BN + 128) (measured on 262144 x 800 x 1600: 128 / 160 / 208 /
 // 256 wide took 0.714 / 0.573 / 0.534 / 0.617 ms, which this cost ranks
-// alike), ties to the wider tile
-static int pick_bn(int N) {
+// alike), ties to the wider tile.  With fewer than 128 row tiles (M < 16384: the training batches) the
+// last wave's balance matters as much: the cost is then the number of waves
+// of tiles over the SMs times (BN + 128) (4096 x 1600: 208 wide, two waves, in
+// place of 256 wide, two waves of which the second is half empty; 4096 x 400:
+// 128 wide, one wave of 128 tiles, in place of 64 tiles 208 wide)
+static int pick_bn(int N, int M, int nsm) {
   const int cand[4] = {256, 208, 160, 128};
+  const int64_t nM = (M + GEMM_BM - 1) / GEMM_BM;
+  const bool few = nM < 128 && nsm > 0;
   int best = 128;
   int64_t best_cost = INT64_MAX;
   for (int c : cand) {
-    const int64_t cost = (int64_t)((N + c - 1) / c) * (c + 128);
+    const int64_t nN = (N + c - 1) / c;
+    const int64_t cost = (few ? (nM * nN + nsm - 1) / nsm : nN) * (c + 128);
     if (cost < best_cost) {
       best_cost = cost;
       best = c;
@@ -213,7 +227,15 @@ static int pick_bn(int N) {
 int gemm_bf16(const void* A, const void* B, const GemmParams& P, cudaStream_t st, int bn) {
   if (P.M < 1 || P.N < 1 || P.K < 1 || (P.N % 8) != 0)
     return set_error(DF_EINVAL, "GEMM sizes: M, N, K >= 1 and N a multiple of 8");
-  if (bn == 0) bn = P.N <= 64 ? 64 : (P.M >= 1024 ? -pick_bn(P.N) : 128);
+  if (bn == 0) {
+    static int nsm[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !nsm[dev] &&
+        cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm[dev] = 0;
+    const int sms = (dev >= 0 && dev < 64) ? nsm[dev] : 0;
+    bn = P.N <= 64 ? 64 : (P.M >= 1024 ? -pick_bn(P.N, P.M, sms) : 128);
+  }
   switch (bn) {
     case -128:
       return gemm_launch_pers<128>(A, B, P, st);

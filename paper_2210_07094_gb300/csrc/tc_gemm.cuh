@@ -443,6 +443,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // global memory by TMA (box 16 x 32, no swizzle)
 constexpr int PERS_STAGE_C_WARP = 32 * 16 * 2;
 __host__ __device__ constexpr int pers_stage_c_bytes(int epi_warps) { return epi_warps * 2 * PERS_STAGE_C_WARP; }
+// staging of the training epilogues (EPI_TRAIN_FWD, EPI_BWD_DZ): per epilogue
+// warp one block of 32 rows x 16 FP32 columns at a row stride of 20 floats
+// (80 bytes: the 16-byte accesses of eight consecutive lanes, one row each or
+// two to four lanes per row, fall on distinct bank groups)
+constexpr int PERS_STAGE_T_LD = 20;
+constexpr int PERS_STAGE_T_WARP = 32 * PERS_STAGE_T_LD * 4;
+__host__ __device__ constexpr int pers_epi_bytes(int mode, int epi_warps) {
+  return mode == EPI_GELU_BF16 ? pers_stage_c_bytes(epi_warps)
+         : (mode == EPI_TRAIN_FWD || mode == EPI_BWD_DZ) ? epi_warps * PERS_STAGE_T_WARP
+                                                         : 0;
+}
 
 __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16]) {
   asm volatile(
@@ -554,6 +565,145 @@ __device__ __forceinline__ void gemm_epilogue_16(const GemmParams& P, const uint
   }
 }
 
+// The training epilogues of the persistent kernel for one 16-column chunk of
+// the warp's 32 rows (rows row0 .. row0 + 31, lane l owning row row0 + l in
+// TMEM).  Row-major global data moves through the warp's staging block, so a
+// warp instruction reads or writes 64-byte (FP32) or 32-byte (BF16) row
+// segments of eight or sixteen rows instead of one 16-byte piece of each of 32
+// rows: the pre-activation read of EPI_BWD_DZ, the FP32 Z and the BF16 H / dZ
+// writes.  The transposed BF16 output is written per lane as before (lanes on
+// consecutive rows: each store instruction covers 64 contiguous bytes).  Same
+// values and rounding as gemm_epilogue_16.
+// EPI_BWD_DZ: the lane's share of a chunk's pre-activation block (rows
+// row0 + 8 it + lane / 4, columns nb + 4 (lane % 4) .. + 3; zero outside the
+// matrix), loaded one chunk ahead so the global-load latency overlaps the
+// previous chunk's arithmetic (the first chunk of a tile: before the wait for
+// the tile's accumulator)
+__device__ __forceinline__ void bwd_load_aux(const GemmParams& P, int row0, int lane, int nb, float4 (&z)[4]) {
+  const int r4 = lane >> 2, c4 = 4 * (lane & 3);
+  const bool full = nb + 16 <= P.N;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int gr = row0 + 8 * it + r4;
+    z[it] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (gr < P.M && nb < P.N) {
+      const float* src = P.aux + (size_t)gr * P.lda + nb + c4;
+      if (full && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        z[it] = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        float t[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) t[e] = (nb + c4 + e < P.N) ? __ldg(src + e) : 0.0f;
+        z[it] = make_float4(t[0], t[1], t[2], t[3]);
+      }
+    }
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void gemm_epilogue_16_staged(const GemmParams& P, const uint32_t (&r)[16], int row0,
+                                                        int lane, int nb, float* stg, const float4 (&za)[4]) {
+  static_assert(MODE == EPI_TRAIN_FWD || MODE == EPI_BWD_DZ, "training epilogues only");
+  if (nb >= P.N) return;
+  const int row = row0 + lane;
+  const bool rok = row < P.M;
+  const bool full = nb + 16 <= P.N;
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  if (P.bias) {
+    if (full && (reinterpret_cast<uintptr_t>(P.bias + nb) & 15) == 0) {
+      const float4* b4 = reinterpret_cast<const float4*>(P.bias + nb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 b = __ldg(b4 + q);
+        v[4 * q] += b.x;
+        v[4 * q + 1] += b.y;
+        v[4 * q + 2] += b.z;
+        v[4 * q + 3] += b.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] += (nb + j < P.N) ? __ldg(P.bias + nb + j) : 0.0f;
+    }
+  }
+  float* mine = stg + lane * PERS_STAGE_T_LD;
+  // lane's place in a row-segment pass: FP32 rows take four lanes (eight rows
+  // per pass), BF16 rows two (sixteen rows per pass)
+  const int r4 = lane >> 2, c4 = 4 * (lane & 3);
+  const int r2 = lane >> 1, h2 = lane & 1;
+  __syncwarp();  // the previous chunk's reads of the block are done
+  if (MODE == EPI_BWD_DZ) {
+#pragma unroll
+    for (int it = 0; it < 4; ++it) *reinterpret_cast<float4*>(stg + (8 * it + r4) * PERS_STAGE_T_LD + c4) = za[it];
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 z = *reinterpret_cast<const float4*>(mine + 4 * q);
+      const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = 4 * q + e;
+        v[j] = (rok && (full || nb + j < P.N)) ? v[j] * gelu_grad_f(zz[e]) : 0.0f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      *reinterpret_cast<float4*>(mine + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int rr = 8 * it + r4, gr = row0 + rr;
+      if (gr < P.M) {
+        const float4 z = *reinterpret_cast<const float4*>(stg + rr * PERS_STAGE_T_LD + c4);
+        float* dst = P.out0 + (size_t)gr * P.ld0 + nb + c4;
+        if (full) {
+          *reinterpret_cast<float4*>(dst) = z;
+        } else {
+          const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (nb + c4 + e < P.N) dst[e] = zz[e];
+        }
+      }
+    }
+    gelu_group<8>(v);
+  }
+  __nv_bfloat162 hb[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) hb[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+  if (P.out1) {
+    __syncwarp();  // the FP32 reads of the block are done
+    uint4* m4 = reinterpret_cast<uint4*>(mine);
+    m4[0] = *reinterpret_cast<const uint4*>(hb);
+    m4[1] = *reinterpret_cast<const uint4*>(hb + 4);
+    __syncwarp();
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int rr = 16 * it + r2, gr = row0 + rr;
+      if (gr < P.M) {
+        const uint4 val = reinterpret_cast<const uint4*>(stg + rr * PERS_STAGE_T_LD)[h2];
+        __nv_bfloat16* dst = P.out1 + (size_t)gr * P.ld1 + nb + 8 * h2;
+        if (full) {
+          *reinterpret_cast<uint4*>(dst) = val;
+        } else {
+          const __nv_bfloat16* e8 = reinterpret_cast<const __nv_bfloat16*>(&val);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (nb + 8 * h2 + e < P.N) dst[e] = e8[e];
+        }
+      }
+    }
+  }
+  if (P.out2 && rok) {
+    const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(hb);
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if (full || nb + j < P.N) P.out2[(size_t)(nb + j) * P.ld2 + row] = h[j];
+  }
+}
+
 template <int BN>
 __host__ __device__ constexpr int tmem_cols_for() {
   return (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
@@ -580,7 +730,7 @@ __global__ void __launch_bounds__(pers_threads(EW), 1)
   uint8_t* sB = smem + STAGES * A_BYTES;
   // EPI_GELU_BF16 output staging: two 32-row x 16-column bf16 blocks per epilogue warp
   uint8_t* sC = sB + STAGES * B_BYTES;
-  constexpr int C_BYTES = (MODE == EPI_GELU_BF16) ? pers_stage_c_bytes(EW) : 0;
+  constexpr int C_BYTES = pers_epi_bytes(MODE, EW);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sC + C_BYTES);  // full[S] empty[S] accf[2] acce[2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -685,14 +835,16 @@ __global__ void __launch_bounds__(pers_threads(EW), 1)
     const uint32_t stg0 = smem_u32(sC) + (uint32_t)((warp - 2) * 2 * PERS_STAGE_C_WARP);
     int sbuf = 0;
     int i = 0;
+    float4 za[4];  // EPI_BWD_DZ: the next chunk's pre-activation block
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
       const int b = i & 1, u = i >> 1;
+      const int m0 = (t / nN) * GEMM_BM, n0 = (t % nN) * BN;
+      if (MODE == EPI_BWD_DZ && 16 * grp < BN) bwd_load_aux(P, m0 + q * 32, lane, n0 + 16 * grp, za);
       if (!mbar_wait(accf0 + 8 * b, u & 1)) {
         timed_out = true;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int m0 = (t / nN) * GEMM_BM, n0 = (t % nN) * BN;
       const int row = m0 + q * 32 + lane;
       const uint32_t tbase = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN);
       uint32_t r[16], rn[16];
@@ -724,6 +876,14 @@ __global__ void __launch_bounds__(pers_threads(EW), 1)
             }
             sbuf ^= 1;
           }
+        } else if (MODE == EPI_TRAIN_FWD || MODE == EPI_BWD_DZ) {
+          float* stg = reinterpret_cast<float*>(sC + (warp - 2) * PERS_STAGE_T_WARP);
+          float4 zc[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) zc[e] = za[e];
+          if (MODE == EPI_BWD_DZ && more) bwd_load_aux(P, m0 + q * 32, lane, n0 + c0 + CS, za);
+          gemm_epilogue_16_staged<(MODE == EPI_BWD_DZ) ? EPI_BWD_DZ : EPI_TRAIN_FWD>(P, r, m0 + q * 32, lane,
+                                                                                   n0 + c0, stg, zc);
         } else {
           gemm_epilogue_16<MODE>(P, r, row, n0 + c0);
         }

@@ -67,12 +67,15 @@ def data():
     return mech, m, surrogate.pairs(Ts, p, Ys)
 
 
-def test_train_step_gradients_match_oracle(data):
+# 512 rows and widths up to 64: the one-tile-per-CTA kernels; 1500 rows and
+# widths 200 / 136 / 72: the persistent kernel's training epilogues (several
+# row tiles per CTA, a ragged last row tile and a last 8-column chunk per layer)
+@pytest.mark.parametrize("widths,n", [((64, 32, 16), 512), ((200, 136, 72), 1500)])
+def test_train_step_gradients_match_oracle(data, widths, n):
     mech, m, (T0, P, Y0, T1, Y1) = data
-    widths = (64, 32, 16)
-    dnn = df.Dnn(_opts(widths, batch=512), seed=3)
+    assert T0.shape[0] >= n
+    dnn = df.Dnn(_opts(widths, batch=n), seed=3)
     dnn.fit_norm(T0, P, Y0, Y1)
-    n = 512
     params0 = dnn.params()
     loss = dnn.train_step(T0[:n].contiguous(), P[:n].contiguous(), Y0[:, :n].contiguous(),
                           Y1[:, :n].contiguous(), lr=0.0)
