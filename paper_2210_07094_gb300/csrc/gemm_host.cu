@@ -183,16 +183,19 @@ static int gemm_launch_pers(const void* A, const void* B, const GemmParams& P, c
   if (rc) return rc;
   // sixteen epilogue warps for the inference GELU layers (four per TMEM lane
   // quarter: on the 11-1600-800-400-9 network's 262144-row chunk the forward
-  // pass took 1.16 ms against 1.45 ms with eight), eight elsewhere
+  // pass took 1.16 ms against 1.45 ms with eight), twelve for the training
+  // epilogues (their registers allow three warps per quarter: on 4096-row
+  // batches the epilogue's latency, not the MMAs, sets the time), eight for
+  // plain FP32 output
   switch (P.mode) {
     case EPI_F32:
       return gemm_launch_pers_mode<BN, EPI_F32, 8>(ta, tb, P, st);
     case EPI_GELU_BF16:
       return gemm_launch_pers_mode<BN, EPI_GELU_BF16, 16>(ta, tb, P, st);
     case EPI_TRAIN_FWD:
-      return gemm_launch_pers_mode<BN, EPI_TRAIN_FWD, 8>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_TRAIN_FWD, 12>(ta, tb, P, st);
     case EPI_BWD_DZ:
-      return gemm_launch_pers_mode<BN, EPI_BWD_DZ, 8>(ta, tb, P, st);
+      return gemm_launch_pers_mode<BN, EPI_BWD_DZ, 12>(ta, tb, P, st);
     default:
       return set_error(DF_EINVAL, "GEMM epilogue mode");
   }
