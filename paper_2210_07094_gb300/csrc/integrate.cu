@@ -339,20 +339,54 @@ __global__ void k_order_scatter(const double* T, int64_t n, unsigned* offs, int3
   if (c < n) order[atomicAdd(&offs[t_bin(T[c])], 1u)] = (int32_t)c;
 }
 
-static int build_order(df_mech* m, const double* T, int64_t ncells, cudaStream_t st, int32_t** out) {
-  if (m->order_cap < ncells) {
+// the same order for a list of cells whose length is on the device (at most
+// cap entries): list entries are cell indices, the order holds cell indices
+__global__ void k_order_hist_list(const double* T, const int32_t* list, const unsigned long long* count, int64_t cap,
+                                  unsigned* hist) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long n = *count;
+  if (i < cap && (unsigned long long)i < n) atomicAdd(&hist[t_bin(T[list[i]])], 1u);
+}
+
+__global__ void k_order_scatter_list(const double* T, const int32_t* list, const unsigned long long* count,
+                                     int64_t cap, unsigned* offs, int32_t* order) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long n = *count;
+  if (i < cap && (unsigned long long)i < n) {
+    const int32_t c = list[i];
+    order[atomicAdd(&offs[t_bin(T[c])], 1u)] = c;
+  }
+}
+
+static int ensure_order_buffers(df_mech* m, int64_t n) {
+  if (m->order_cap < n) {
     if (m->order) cudaFree(m->order);
     m->order = nullptr;
     m->order_cap = 0;
-    int rc = cuda_check(cudaMalloc(&m->order, sizeof(int32_t) * ncells), "cudaMalloc order");
+    int rc = cuda_check(cudaMalloc(&m->order, sizeof(int32_t) * n), "cudaMalloc order");
     if (rc) return rc;
-    m->order_cap = ncells;
+    m->order_cap = n;
   }
-  if (!m->bins) {
-    int rc = cuda_check(cudaMalloc(&m->bins, sizeof(unsigned) * ORDER_BINS), "cudaMalloc bins");
-    if (rc) return rc;
-  }
-  int rc = cuda_check(cudaMemsetAsync(m->bins, 0, sizeof(unsigned) * ORDER_BINS, st), "clear bins");
+  if (!m->bins) return cuda_check(cudaMalloc(&m->bins, sizeof(unsigned) * ORDER_BINS), "cudaMalloc bins");
+  return DF_OK;
+}
+
+static int build_order_list(df_mech* m, const double* T, const int32_t* list, const unsigned long long* count,
+                            int64_t cap, cudaStream_t st, int32_t** out) {
+  int rc = ensure_order_buffers(m, cap);
+  if (!rc) rc = cuda_check(cudaMemsetAsync(m->bins, 0, sizeof(unsigned) * ORDER_BINS, st), "clear bins");
+  if (rc) return rc;
+  const unsigned blocks = (unsigned)((cap + 255) / 256);
+  k_order_hist_list<<<blocks, 256, 0, st>>>(T, list, count, cap, m->bins);
+  k_order_scan<<<1, 1024, 0, st>>>(m->bins);
+  k_order_scatter_list<<<blocks, 256, 0, st>>>(T, list, count, cap, m->bins, m->order);
+  *out = m->order;
+  return cuda_check(cudaGetLastError(), "list order kernels");
+}
+
+static int build_order(df_mech* m, const double* T, int64_t ncells, cudaStream_t st, int32_t** out) {
+  int rc = ensure_order_buffers(m, ncells);
+  if (!rc) rc = cuda_check(cudaMemsetAsync(m->bins, 0, sizeof(unsigned) * ORDER_BINS, st), "clear bins");
   if (rc) return rc;
   const unsigned blocks = (unsigned)((ncells + 255) / 256);
   k_order_hist<<<blocks, 256, 0, st>>>(T, ncells, m->bins);
@@ -601,6 +635,13 @@ int launch_integrate_list(df_mech* m, int64_t ncells, double* T, const double* p
   if (!order && o.order_by_T && nwork == ncells && ncells > 1) {
     int32_t* ord = nullptr;
     rc = build_order(m, T, ncells, st, &ord);
+    if (rc) return rc;
+    order = ord;
+  } else if (order && nwork_dev && o.order_by_T && nwork > 1) {
+    // a cell list counted on the device (the surrogate's fallback cells):
+    // hottest first as well, so its stiffest cells do not start last
+    int32_t* ord = nullptr;
+    rc = build_order_list(m, T, order, nwork_dev, nwork, st, &ord);
     if (rc) return rc;
     order = ord;
   }
