@@ -117,9 +117,21 @@ struct RxIn {
   S Mc;            // [M] (third body, falloff)
 };
 
+// Third-body efficiencies as a sum of all concentrations plus sparse
+// corrections: [M] = ctot + sum over the species l whose efficiency is not 1 of
+// (eps_l - 1) C_l.  off[s] .. off[s + 1] index the (l, low word, high word)
+// triples of efficiency slot s in ent (the correction eps_l - 1 as the two
+// 32-bit halves of a double).
+struct SparseEff {
+  const int* off;
+  const int* ent;
+  double ctot;
+};
+
 template <int NS, bool WITH_J, class S, class Vec>
 __device__ __forceinline__ void rate_gather(const MechView& mv, const double* r, int Nrt, const Vec& C,
-                                            const Vec& gRT, const Vec& hRT, RxIn<S>& g) {
+                                            const Vec& gRT, const Vec& hRT, RxIn<S>& g,
+                                            const SparseEff* se = nullptr) {
   const int N = NS > 0 ? NS : Nrt;
   g.lnA = r[0];
   g.beta = r[1];
@@ -146,11 +158,20 @@ __device__ __forceinline__ void rate_gather(const MechView& mv, const double* r,
   g.sh = sh;
   g.Mc = S(0.0);
   if ((mt.flags & 3) != 0) {
-    const double* ef = mv.eff + N * g.sl.eff;
-    S Mc(0.0);
+    if (se) {
+      S Mc(se->ctot);
+      for (int t = se->off[g.sl.eff]; t < se->off[g.sl.eff + 1]; ++t) {
+        const int* e = se->ent + 3 * t;
+        Mc += __hiloint2double(e[2], e[1]) * C[e[0]];
+      }
+      g.Mc = Mc;
+    } else {
+      const double* ef = mv.eff + N * g.sl.eff;
+      S Mc(0.0);
 #pragma unroll
-    for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
-    g.Mc = Mc;
+      for (int l = 0; l < N; ++l) Mc += ef[l] * C[l];
+      g.Mc = Mc;
+    }
   }
 }
 
@@ -253,9 +274,9 @@ __device__ __forceinline__ void rate_compute(const MechView& mv, const RxIn<S>& 
 template <int NS, bool WITH_J, class S, class Vec>
 __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, int Nrt, S T, S lnT, S invT,
                                          S lnP0RT, const Vec& C, const Vec& gRT, const Vec& hRT,
-                                         RateOutT<S>& o) {
+                                         RateOutT<S>& o, const SparseEff* se = nullptr) {
   RxIn<S> g;
-  rate_gather<NS, WITH_J>(mv, r, Nrt, C, gRT, hRT, g);
+  rate_gather<NS, WITH_J>(mv, r, Nrt, C, gRT, hRT, g, se);
   rate_compute<NS, WITH_J>(mv, g, T, lnT, invT, lnP0RT, o);
 }
 

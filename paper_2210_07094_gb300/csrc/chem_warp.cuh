@@ -68,6 +68,17 @@ __device__ __forceinline__ double rcp_nr(double a) {
   return r1 * fma(-a, r1, 2.0);
 }
 
+// a small nonzero integer (a stoichiometric coefficient, |v| < 2^20) as a
+// double, assembled with integer operations so that it takes no slot of the
+// narrow FP64 pipe
+__device__ __forceinline__ double int_to_double_small(int v) {
+  const unsigned a = (unsigned)(v < 0 ? -v : v);
+  const int lz = __clz(a);                                     // a >= 1: the leading one at bit 31 - lz
+  const unsigned mant = ((a << lz) << 1) >> 12;                // the 20 bits below the leading one
+  const unsigned hi = ((unsigned)(v < 0) << 31) | ((unsigned)(1023 + 31 - lz) << 20) | mant;
+  return __hiloint2double((int)hi, 0);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(WFULL, v, o);
@@ -108,13 +119,22 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   const double sumYW = warp_sum(sYW);
   const double Wbar = rcp_nr(sumYW);
   const double rho = CONSTV ? pc : pc * invT * Wbar * (1.0 / RU);
-  for (int k = lane; k < N; k += 32) C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
+  double cs = 0.0;
+  for (int k = lane; k < N; k += 32) {
+    const double ck = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
+    C[k] = ck;
+    cs += ck;
+  }
+  // third-body [M] = sum_l C_l + the sparse corrections (eps_l - 1) C_l; the
+  // table follows the species lists and the lane assignment in csr
+  const int* effs = csr + N + 1 + 2 * csr[N] + 64;
+  const SparseEff se{effs + 1, effs + 2 + effs[0], warp_sum(cs)};
   __syncwarp();
   const double lnP0RT = LOG_PSTD_RU - lnT;
   // reactions: one lane per reaction
   for (int j = lane; j < mv.M; j += 32) {
     RateOut ro;
-    rate_one<0, WITH_J>(mv, mv.rx + RX_REC * j, N, T, lnT, invT, lnP0RT, C, gRT, hRT, ro);
+    rate_one<0, WITH_J>(mv, mv.rx + RX_REC * j, N, T, lnT, invT, lnP0RT, C, gRT, hRT, ro, &se);
     if (ro.active) {
       ws[L.q + j] = ro.q;
       if (WITH_J) {
@@ -148,7 +168,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     for (int t = 0; t < la + lb; ++t) {
       const bool first = t < la;
       const int e = first ? ba + t : bb + (t - la);
-      const double c = csr[N + 2 + 2 * e] * ws[L.q + csr[N + 1 + 2 * e]];
+      const double c = int_to_double_small(csr[N + 2 + 2 * e]) * ws[L.q + csr[N + 1 + 2 * e]];
       if (first) wa += c;
       else wb += c;
     }
@@ -179,13 +199,17 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       for (int c = 0; c < n; ++c) J[(1 + ka) * n + c] = 0.0;
     if (kb >= 0)
       for (int c = 0; c < n; ++c) J[(1 + kb) * n + c] = 0.0;
+    // collider columns d q_j / d[M] eps_l: the unit part summed per row (sMa,
+    // sMb; added to every species column in the conversion below), the
+    // corrections eps_l - 1 entered where the efficiency is not 1
+    double sMa = 0.0, sMb = 0.0;
     for (int t = 0; t < la + lb; ++t) {
       const bool first = t < la;
       const int e = first ? ba + t : bb + (t - la);
       double* row = J + (1 + (first ? ka : kb)) * n;
       {
         const int j = csr[N + 1 + 2 * e];
-        const double nu = (double)csr[N + 2 + 2 * e];
+        const double nu = int_to_double_small(csr[N + 2 + 2 * e]);
         const double* r = mv.rx + RX_REC * j;
         const RxMeta mt = load_meta(r);
         const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;
@@ -201,8 +225,13 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
         if (np > 2) row[1 + mt.prod[2]] -= nu * rk * d0 * d1;
         if ((mt.flags & 3) != 0) {
           const double cM = nu * ws[L.dM + j];
-          const double* ef = mv.eff + N * load_slots(r).eff;
-          for (int l = 0; l < N; ++l) row[1 + l] += cM * ef[l];
+          if (first) sMa += cM;
+          else sMb += cM;
+          const int sl = load_slots(r).eff;
+          for (int u = se.off[sl]; u < se.off[sl + 1]; ++u) {
+            const int* q = se.ent + 3 * u;
+            row[1 + q[0]] += cM * __hiloint2double(q[2], q[1]);
+          }
         }
       }
     }
@@ -212,15 +241,17 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       if (k < 0) continue;
       double* row = J + (1 + k) * n;
       const double Wk = mv.sp[SP_REC * k];
+      const double sM = tk == 0 ? sMa : sMb;  // the row's unit collider part
       if (CONSTV) {  // C does not move with T or the mean molar mass
-        for (int i = 0; i < N; ++i) row[1 + i] = Wk * row[1 + i] * mv.sp[SP_REC * i + 1];
+        const double b = Wk * sM;
+        for (int i = 0; i < N; ++i) row[1 + i] = fma(Wk, row[1 + i], b) * mv.sp[SP_REC * i + 1];
         row[0] = Wk * invrho * row[0];
         continue;
       }
-      double s = 0.0;
+      double s = sM * se.ctot;
       for (int l = 0; l < N; ++l) s += row[1 + l] * C[l];
       const double wk = wdot[k];
-      const double a = Wk * Wbar * invrho * (wk - s);
+      const double a = Wk * Wbar * invrho * (wk - s) + Wk * sM;
       for (int i = 0; i < N; ++i) row[1 + i] = (Wk * row[1 + i] + a) * mv.sp[SP_REC * i + 1];
       row[0] = Wk * invrho * (row[0] + (wk - s) * invT);
     }

@@ -327,6 +327,28 @@ int parse_mechanism(const char* path, df_mech* m) {
     load[best] += ck.first;
   }
   m->csr_host.insert(m->csr_host.end(), asg.begin(), asg.end());
+  // Sparse third-body efficiencies for the warp path: [n_eff], offsets
+  // [n_eff + 1] (in triples), then per slot the (species, low word, high word)
+  // triples of eps_l - 1 for every species whose efficiency is not 1.
+  m->csr_host.push_back(n_eff);
+  const size_t off0 = m->csr_host.size();
+  m->csr_host.resize(off0 + n_eff + 1, 0);
+  int ntrip = 0;
+  for (int sl = 0; sl < n_eff; ++sl) {
+    m->csr_host[off0 + sl] = ntrip;
+    for (int l = 0; l < N; ++l) {
+      const double e = eff[(size_t)sl * N + l];
+      if (e == 1.0) continue;
+      const double dlt = e - 1.0;
+      unsigned long long bits;
+      memcpy(&bits, &dlt, 8);
+      m->csr_host.push_back(l);
+      m->csr_host.push_back((int)(unsigned)(bits & 0xffffffffull));
+      m->csr_host.push_back((int)(unsigned)(bits >> 32));
+      ++ntrip;
+    }
+  }
+  m->csr_host[off0 + n_eff] = ntrip;
   return DF_OK;
 }
 
