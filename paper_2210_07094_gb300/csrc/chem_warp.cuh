@@ -257,18 +257,22 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     }
     __syncwarp();
     // temperature row
+    // hw_k = (h_k/RT - EV) / W_k, once per species (into the g/RT slots, which
+    // the rates no longer need), for the column sums below
     double dcp = 0.0, cpf = 0.0;
     for (int k = lane; k < N; k += 32) {
       const double* a = mv.sp + SP_REC * k + 2;
       const double iW = mv.sp[SP_REC * k + 1];
       dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
       cpf += (cpR[k] - EV) * iW * f[1 + k];
+      gRT[k] = (hRT[k] - EV) * iW;
     }
     dcp = RU * warp_sum(dcp);
     cpf = RU * warp_sum(cpf);
+    __syncwarp();
     for (int jc = lane; jc < n; jc += 32) {
       double acc = 0.0;
-      for (int k = 0; k < N; ++k) acc += (hRT[k] - EV) * mv.sp[SP_REC * k + 1] * J[(1 + k) * n + jc];
+      for (int k = 0; k < N; ++k) acc += gRT[k] * J[(1 + k) * n + jc];
       acc *= RU * T;
       if (jc == 0) J[0] = -invcp * (acc + cpf) - fT * dcp * invcp;
       else J[jc] = -invcp * acc - fT * RU * (cpR[jc - 1] - EV) * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
