@@ -164,14 +164,19 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   const int bb = kb >= 0 ? csr[kb] : 0, lb = kb >= 0 ? csr[kb + 1] - bb : 0;
   double cpp = 0.0, hwp = 0.0;
   {
-    double wa = 0.0, wb = 0.0;
+    // one running sum, one multiply-add per entry: the first list's sum is
+    // set aside where the second list starts
+    double acc = 0.0, wa = 0.0, wb = 0.0;
     for (int t = 0; t < la + lb; ++t) {
-      const bool first = t < la;
-      const int e = first ? ba + t : bb + (t - la);
-      const double c = int_to_double_small(csr[N + 2 + 2 * e]) * ws[L.q + csr[N + 1 + 2 * e]];
-      if (first) wa += c;
-      else wb += c;
+      if (t == la) {
+        wa = acc;
+        acc = 0.0;
+      }
+      const int e = t < la ? ba + t : bb + (t - la);
+      acc = fma(int_to_double_small(csr[N + 2 + 2 * e]), ws[L.q + csr[N + 1 + 2 * e]], acc);
     }
+    if (lb > 0) wb = acc;
+    else wa = acc;
     if (ka >= 0) {
       wdot[ka] = wa;
       cpp += y[1 + ka] * (cpR[ka] - EV) * mv.sp[SP_REC * ka + 1];
