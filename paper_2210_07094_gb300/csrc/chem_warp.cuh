@@ -54,20 +54,6 @@ __host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
   return w;
 }
 
-// 1/a in FP64 from an FP32 seed and two Newton-Raphson steps r <- r (2 - a r)
-// (the relative error squares at each step: 2^-22 -> 2^-44 -> rounding): four
-// FP64 operations where a correctly rounded division takes a longer sequence
-// on the narrow FP64 pipe.  For |a| inside the FP32 normal range (the warp
-// path's pivots, temperatures, densities, heat capacities and step sizes); a
-// zero or non-finite a gives a non-finite result.
-__device__ __forceinline__ double rcp_nr(double a) {
-  float r0f;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)a));
-  const double r0 = (double)r0f;
-  const double r1 = r0 * fma(-a, r0, 2.0);
-  return r1 * fma(-a, r1, 2.0);
-}
-
 // a small nonzero integer (a stoichiometric coefficient, |v| < 2^20) as a
 // double, assembled with integer operations so that it takes no slot of the
 // narrow FP64 pipe

@@ -94,4 +94,21 @@ inline MechDims mech_dims(int N, int M, int n_eff, int n_troe) {
   return d;
 }
 
+#ifdef __CUDACC__
+// 1/a in FP64 from an FP32 seed and two Newton-Raphson steps r <- r (2 - a r)
+// (the relative error squares at each step: 2^-22 -> 2^-44 -> rounding): four
+// FP64 operations where a correctly rounded division takes a longer sequence
+// on the narrow FP64 pipe.  For |a| inside the FP32 normal range (pivots,
+// temperatures, densities, heat capacities, step sizes and error scales of the
+// integrators); a zero or non-finite a gives a non-finite result.
+__device__ __forceinline__ double rcp_nr(double a) {
+  float r0f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"((float)a));
+  const double r0 = (double)r0f;
+  const double r1 = r0 * fma(-a, r0, 2.0);
+  return r1 * fma(-a, r1, 2.0);
+}
+
+#endif
+
 }  // namespace df

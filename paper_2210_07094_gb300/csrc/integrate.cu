@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256, 1) k_integrate_warp(IntegArgs a, const in
       const double hgi = rcp_nr(h * tb.gamma);
       for (int e = lane; e < n * n; e += 32) {
         const int i = e / n, j = e - i * n;
-        J[e] = (i == j ? hgi : 0.0) - J[e];
+        J[e] = i == j ? hgi - J[e] : -J[e];
       }
       __syncwarp();
       bool ok = warp_lu(J, piv, n);

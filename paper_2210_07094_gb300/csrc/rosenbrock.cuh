@@ -100,9 +100,9 @@ constexpr double FIRST_STEP_THETA = 0.5;
 
 template <int n>
 __device__ __forceinline__ double first_step_limit(const double (&y)[n], const double (&f)[n]) {
-  double r = fabs(f[0]) / fabs(y[0]);
+  double r = fabs(f[0]) * rcp_nr(fabs(y[0]));
 #pragma unroll
-  for (int i = 1; i < n; ++i) r = fmax(r, fabs(f[i]) / fmax(fabs(y[i]), 1e-6));
+  for (int i = 1; i < n; ++i) r = fmax(r, fabs(f[i]) * rcp_nr(fmax(fabs(y[i]), 1e-6)));
   return r > 0.0 ? FIRST_STEP_THETA / r : INFINITY;
 }
 
@@ -140,16 +140,16 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
       if (last) *last = false;
     }
   }
-  const double hgi = 1.0 / (h * tb.gamma);
+  const double hgi = rcp_nr(h * tb.gamma);
 #pragma unroll
   for (int i = 0; i < n; ++i) {
 #pragma unroll
-    for (int j = 0; j < n; ++j) Jv[i * n + j] = (i == j ? hgi : 0.0) - Jv[i * n + j];
+    for (int j = 0; j < n; ++j) Jv[i * n + j] = i == j ? hgi - Jv[i * n + j] : -Jv[i * n + j];
   }
   int piv_l[n];
   int* piv = piv_out ? piv_out : piv_l;
   bool ok = lu_factor<n, ST>(Jv, piv);
-  const double ih = 1.0 / h;
+  const double ih = rcp_nr(h);
   for (int s = 0; s < tb.s; ++s) {
     if (s > 0 && tb.newf[s]) {
 #pragma unroll
@@ -181,10 +181,10 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
     }
     ynew[i] = yn;
     const double sc = (i == 0 ? atolT : atolY) + rtol * fmax(fabs(y[i]), fabs(yn));
-    const double r = e / sc;
+    const double r = e * rcp_nr(sc);
     e2 += r * r;
   }
-  en = sqrt(e2 / n);
+  en = sqrt(e2 * (1.0 / n));
   return ok && isfinite(en);
 }
 
@@ -248,28 +248,31 @@ template <int n>
 __device__ __forceinline__ void step_control(const RosTab& tb, bool ok, double en, bool last, double dt,
                                              double (&y)[n], const double (&ynew)[n], double& t, double& h,
                                              int& nacc, int& nrej, bool& last_rej, bool& done, StepState& ss) {
-  const double ie = -1.0 / tb.elo;
+  // the accept test in FP64, the step-size factors in FP32 (a heuristic's
+  // factors need no more; FP32 powf runs on the wide pipes, FP64 pow on the
+  // narrow one)
+  const float ie = -1.0f / (float)tb.elo;
   if (ok && en <= 1.0) {
 #pragma unroll
     for (int i = 0; i < n; ++i) y[i] = ynew[i];
     t = last ? dt : t + h;
     ++nacc;
-    const double e = fmax(en, 1e-10);
-    double fac = 0.9 * pow(e, ie);
-    if (nacc > 1) fac = fmin(fac, 0.9 * (h / ss.hacc) * pow(e * e / ss.erracc, ie));
-    fac = fmin(last_rej ? 1.0 : 6.0, fmax(0.2, fac));
+    const float e = fmaxf((float)en, 1e-10f);
+    float fac = 0.9f * powf(e, ie);
+    if (nacc > 1) fac = fminf(fac, 0.9f * ((float)h / (float)ss.hacc) * powf(e * e / (float)ss.erracc, ie));
+    fac = fminf(last_rej ? 1.0f : 6.0f, fmaxf(0.2f, fac));
     ss.hacc = h;
     ss.erracc = fmax(1e-2, en);
-    h *= fac;
+    h *= (double)fac;
     last_rej = false;
     if (t >= dt) done = true;
   } else {
     ++nrej;
     // before the first accepted step the trial step (= dt) may be orders of
     // magnitude too long for a stiff cell: let the error estimate cut it deeply
-    const double fmin = nacc == 0 ? 1e-4 : 0.2;
-    const double fac = ok ? fmax(fmin, 0.9 * pow(en, ie)) : 0.25;
-    h *= fac;
+    const float fmn = nacc == 0 ? 1e-4f : 0.2f;
+    const float fac = ok ? fmaxf(fmn, 0.9f * powf((float)en, ie)) : 0.25f;
+    h *= (double)fac;
     last_rej = true;
   }
 }
