@@ -623,14 +623,18 @@ __device__ __forceinline__ bool lu_factor(SVT<double, ST> A, int* piv) {
   bool ok = true;
 #pragma unroll 1
   for (int k = 0; k < n; ++k) {
+    // pivot search on the magnitudes' bit patterns as 64-bit integers
+    // (non-negative doubles order like their patterns): integer compares
+    // instead of FP64 ones on the narrow pipe; a NaN sorts above every finite
+    // value, is picked, and fails the finiteness test
     int p = k;
-    double best = fabs(A[k * n + k]);
+    long long best = __double_as_longlong(A[k * n + k]) & 0x7FFFFFFFFFFFFFFFLL;
     for (int i = k + 1; i < n; ++i) {
-      const double v = fabs(A[i * n + k]);
+      const long long v = __double_as_longlong(A[i * n + k]) & 0x7FFFFFFFFFFFFFFFLL;
       if (v > best) { best = v; p = i; }
     }
     piv[k] = p;
-    ok = ok && (best > 0.0) && (best < INFINITY);
+    ok = ok && (best > 0) && (best < 0x7FF0000000000000LL);
     if (p != k) {
 #pragma unroll
       for (int j = 0; j < n; ++j) {
