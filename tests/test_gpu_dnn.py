@@ -160,6 +160,54 @@ def test_infer_pipeline_and_fallback(data, widths):
         assert abs(h1 - h0) <= 1e-9 * 1.5e3 * f["T"][cc]
 
 
+def test_infer_full_size_sampled(data):
+    """The inference pass at the size the bench times: 2^22 cells in the
+    default 262144-row chunks through the 11-1600-800-400-9 network, 2% of
+    them above the training T range.  Sampled network cells against the oracle
+    pipeline (features, BF16-rounded MLP, post stage) and sampled fallback
+    cells against a direct integration of the same cells (bitwise)."""
+    mech, m, (T0, P, Y0, T1, Y1) = data
+    dnn = df.Dnn(df.dnn_default_opts(), seed=13)
+    dnn.fit_norm(T0, P, Y0, Y1)
+    o = Mech(mech)
+    n = 1 << 22
+    f = synth.field(1, mech, n, seed=2024)
+    f["T"] = np.clip(f["T"], T0.min().item() + 1, T0.max().item() - 1)
+    rng = np.random.default_rng(5)
+    out = np.sort(rng.choice(n, n // 50, replace=False))
+    f["T"][out] = rng.uniform(T0.max().item() + 50.0, T0.max().item() + 300.0, out.size)
+    T, p, Y = (torch.tensor(f[k], device=DEV) for k in ("T", "p", "Y"))
+    nfb, used, status = dnn.infer(m, T, p, Y, f["dt"])
+    used = used.cpu().numpy()
+    # the moved cells and any other cell with a feature outside the training range
+    fbl = np.nonzero(used)[0]
+    assert nfb == fbl.size and np.all(used[out] == 1)
+    assert int(status.abs().sum()) == 0
+    Tg, Yg = T.cpu().numpy(), Y.cpu().numpy()
+    # about 300 sampled fallback cells: a direct integration, bitwise
+    fb = fbl[:: max(1, fbl.size // 300)]
+    Ti, pi, Yi = (torch.tensor(np.ascontiguousarray(f[k][..., fb]), device=DEV) for k in ("T", "p", "Y"))
+    df.integrate(m, Ti, pi, Yi, f["dt"])
+    assert np.array_equal(Tg[fb], Ti.cpu().numpy()) and np.array_equal(Yg[:, fb], Yi.cpu().numpy())
+    # sampled network cells, spread over every chunk
+    net = np.arange(0, n, 9973)
+    net = net[used[net] == 0]
+    assert net.size > 300
+    nm = dnn.norm()
+    norm = {"mean_in": np.r_[nm["mean_in"], np.zeros(5)], "std_in": np.r_[nm["std_in"], np.ones(5)],
+            "mean_out": np.r_[nm["mean_out"], np.zeros(7)], "std_out": np.r_[nm["std_out"], np.ones(7)]}
+    _, x = mlp.features(f["T"][net], f["p"][net], f["Y"][:, net], 0.1, norm, 9)
+    U, _ = mlp.forward(mlp.unpack(dnn.params(), (1600, 800, 400)), x.astype(np.float32), emulate=True)
+    inert = mlp.inert_species(mech)
+    To, Yo = mlp.post(f["T"][net], f["p"][net], f["Y"][:, net], U, 0.1, norm, 9, o.nasa, o.W, inert=inert)
+    assert np.allclose(Yg[:, net].sum(axis=0), 1.0, rtol=1e-13)
+    assert np.array_equal(Yg[inert][:, net], f["Y"][inert][:, net])
+    err = np.abs(Yg[:, net] - Yo).max(axis=0) / (np.abs(Yo - f["Y"][:, net]).max() + 1e-300)
+    print({"cells": n, "fallback": int(nfb), "sampled": len(net), "median": float(np.median(err)),
+           "max": float(err.max())})
+    assert np.median(err) <= 1e-4 and np.quantile(err, 0.99) <= 3e-3 and err.max() <= 3e-2
+
+
 def test_post_resolves_small_changes(data):
     """Stage 3 on changes far below FP32 resolution of Y itself: with the output
     layer's weights zeroed the network returns its bias, so every cell gets the
