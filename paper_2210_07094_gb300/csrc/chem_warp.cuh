@@ -24,34 +24,51 @@ struct PV {
 
 // per-warp workspace layout (offsets in doubles)
 struct WarpWS {
-  int y, ys, f, wdot, C, gRT, hRT, cpR, q, fk, rk, dT, dM, J, K, piv, total;
+  int y, ys, f, wdot, C, gRT, hRT, q, fk, rk, dT, dM, J, K, piv, total;
 };
 
-__host__ __device__ inline WarpWS warp_ws_layout(int N, int M) {
+// Seven cells of the 50-species mechanism fit an SM where six did with one
+// slot per quantity: the production rates share the g/RT slots (the rates
+// read g/RT before the per-species sums write the production rates, and the
+// temperature row reuses the slots after the last read of the production
+// rates); d q / d[M] has one slot per third-body reaction; d q / dT lives in
+// the stage vectors while the Jacobian is built (no stage vector is live
+// then) where they have room; cp/R is recomputed where it is needed.
+__host__ __device__ inline WarpWS warp_ws_layout(int N, int M, int n_eff) {
   const int n = N + 1;
   WarpWS w;
   int o = 0;
   w.y = o; o += n;
   w.f = o; o += n;
-  w.wdot = o; o += N;
   w.C = o; o += N;
   w.gRT = o; o += N;
+  w.wdot = w.gRT;
   w.hRT = o; o += N;
-  w.cpR = o; o += N;
   w.q = o; o += M;
   w.fk = o; o += M;
   w.rk = o; o += M;
-  w.dT = o; o += M;
-  w.dM = o; o += M;
+  w.dM = o; o += n_eff > 0 ? n_eff : 1;
   w.J = o; o += n * n;
   w.K = o; o += 6 * n;
   // the stage state shares the last stage vector's slot: it is read (f(ys))
   // before that stage vector is written, and the candidate state overwrites
   // it element by element after each lane has read its own elements
   w.ys = w.K + 5 * n;
+  if (M <= 6 * n) {
+    w.dT = w.K;
+  } else {
+    w.dT = o;
+    o += M;
+  }
   w.piv = o; o += (n + 1) / 2;  // ints, two per double slot
   w.total = (o + 1) & ~1;
   return w;
+}
+
+// cp/R of species k at T (NASA-7)
+__device__ __forceinline__ double cp_species(const MechView& mv, int k, double T) {
+  const double* a = mv.sp + SP_REC * k + 2;
+  return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
 }
 
 // a small nonzero integer (a stoichiometric coefficient, |v| < 2^20) as a
@@ -84,8 +101,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   const double* y = ws + yoff;
   double* f = ws + L.f;
   PV C{ws + L.C}, gRT{ws + L.gRT}, hRT{ws + L.hRT};
-  double* cpR = ws + L.cpR;
-  double* wdot = ws + L.wdot;
+  double* wdot = ws + L.wdot;  // the g/RT slots, once the rates have read them
   const double T = y[0];
   const double lnT = log_tab(T);
   const double invT = rcp_nr(T);
@@ -93,7 +109,6 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
   double sYW = 0.0;
   for (int k = lane; k < N; k += 32) {
     const double* a = mv.sp + SP_REC * k + 2;
-    cpR[k] = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
     const double* ah = mv.sp + SP_REC * k + SP_H;  // a2/2 .. a5/5
     const double* as = mv.sp + SP_REC * k + SP_S;  // a3/2 .. a5/4
     const double hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;
@@ -127,7 +142,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
         ws[L.fk + j] = ro.fk;
         ws[L.rk + j] = ro.rk;
         ws[L.dT + j] = ro.dqdT;
-        ws[L.dM + j] = ro.dqdM;
+        if ((ro.mt.flags & 3) != 0) ws[L.dM + ro.sl.eff] = ro.dqdM;
       }
     } else {
       ws[L.q + j] = 0.0;
@@ -135,7 +150,8 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
         ws[L.fk + j] = 0.0;
         ws[L.rk + j] = 0.0;
         ws[L.dT + j] = 0.0;
-        ws[L.dM + j] = 0.0;
+        const double* r = mv.rx + RX_REC * j;
+        if ((load_meta(r).flags & 3) != 0) ws[L.dM + load_slots(r).eff] = 0.0;
       }
     }
   }
@@ -165,12 +181,12 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
     else wa = acc;
     if (ka >= 0) {
       wdot[ka] = wa;
-      cpp += y[1 + ka] * (cpR[ka] - EV) * mv.sp[SP_REC * ka + 1];
+      cpp += y[1 + ka] * (cp_species(mv, ka, T) - EV) * mv.sp[SP_REC * ka + 1];
       hwp += (hRT[ka] - EV) * wa;
     }
     if (kb >= 0) {
       wdot[kb] = wb;
-      cpp += y[1 + kb] * (cpR[kb] - EV) * mv.sp[SP_REC * kb + 1];
+      cpp += y[1 + kb] * (cp_species(mv, kb, T) - EV) * mv.sp[SP_REC * kb + 1];
       hwp += (hRT[kb] - EV) * wb;
     }
   }
@@ -215,10 +231,10 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
         if (np > 1) row[1 + mt.prod[1]] -= nu * rk * d0 * d2;
         if (np > 2) row[1 + mt.prod[2]] -= nu * rk * d0 * d1;
         if ((mt.flags & 3) != 0) {
-          const double cM = nu * ws[L.dM + j];
+          const int sl = load_slots(r).eff;
+          const double cM = nu * ws[L.dM + sl];
           if (first) sMa += cM;
           else sMb += cM;
-          const int sl = load_slots(r).eff;
           for (int u = se.off[sl]; u < se.off[sl + 1]; ++u) {
             const int* q = se.ent + 3 * u;
             row[1 + q[0]] += cM * __hiloint2double(q[2], q[1]);
@@ -255,7 +271,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       const double* a = mv.sp + SP_REC * k + 2;
       const double iW = mv.sp[SP_REC * k + 1];
       dcp += y[1 + k] * (a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]))) * iW;
-      cpf += (cpR[k] - EV) * iW * f[1 + k];
+      cpf += (cp_species(mv, k, T) - EV) * iW * f[1 + k];
       gRT[k] = (hRT[k] - EV) * iW;
     }
     dcp = RU * warp_sum(dcp);
@@ -266,7 +282,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       for (int k = 0; k < N; ++k) acc += gRT[k] * J[(1 + k) * n + jc];
       acc *= RU * T;
       if (jc == 0) J[0] = -invcp * (acc + cpf) - fT * dcp * invcp;
-      else J[jc] = -invcp * acc - fT * RU * (cpR[jc - 1] - EV) * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
+      else J[jc] = -invcp * acc - fT * RU * (cp_species(mv, jc - 1, T) - EV) * mv.sp[SP_REC * (jc - 1) + 1] * invcp;
     }
   }
   __syncwarp();

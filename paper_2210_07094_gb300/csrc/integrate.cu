@@ -520,7 +520,7 @@ int warp_shape(const df_mech* m, const WarpWS& L, bool want_stage, int max_warps
 
 int eval_warp_dispatch(const df_mech* m, int64_t ncells, const double* T, const double* p, const double* Y,
                        double* dydt, double* qdot, double* J, cudaStream_t st) {
-  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M);
+  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M, m->dims.n_eff);
   int warps, stage;
   size_t sm;
   int rc = warp_shape(m, L, false, 4, &warps, &stage, &sm);
@@ -540,7 +540,7 @@ int eval_warp_dispatch(const df_mech* m, int64_t ncells, const double* T, const 
 }
 
 int integrate_warp_dispatch(df_mech* m, const IntegArgs& a0, cudaStream_t st, int threads, bool constv) {
-  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M);
+  const WarpWS L = warp_ws_layout(m->dims.N, m->dims.M, m->dims.n_eff);
   int warps, stage;
   size_t sm;
   const int max_warps = threads > 0 ? threads / 32 : 8;
