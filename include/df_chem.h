@@ -196,8 +196,10 @@ int df_chem_integrate(const df_mech* mech, int64_t ncells, double* T, const doub
  *                of accepted steps; a cell with more than max_steps accepted
  *                steps gets DF_CELL_MAXSTEPS and a zero gradient
  *  workspace     device memory owned by the caller: at least the compact size
- *                8 * (ncells*max_steps*(N+2) + ceil(ncells/32)*M) + 256
- *                bytes; df_chem_adjoint_workspace_size() returns the size with
+ *                8 * (ncells*max_steps*(N+2) + ceil(ncells/16)*M) + 256
+ *                bytes (the ln A partial sums take ceil(ncells/B)*M doubles,
+ *                B the 16 to 32 cells of one block, which the library picks
+ *                from the device's shared memory); df_chem_adjoint_workspace_size() returns the size with
  *                the stored stages, 8 * ncells*max_steps*(7n + n^2) bytes more
  *                (n = N + 1).  On return its first ncells*max_steps*(N+2)
  *                doubles hold the checkpoints [cell][step][T, Y_1..Y_N, h] of
@@ -223,8 +225,8 @@ int df_chem_adjoint(const df_mech* mech, int64_t ncells, const double* T0, const
  * ln A partial sums) lives in one fixed 4 MiB device array inside the library,
  * held by every GPU that loads it until the process exits; nothing is
  * allocated.  Requests that need more (ncells * max_steps * (N + 2) doubles of
- * checkpoints plus ceil(ncells / 32) * M doubles of partials, in total more than
- * 4 MiB) return DF_EWORKSPACE with the size in the error detail.  The first
+ * checkpoints plus at most ceil(ncells / 16) * M doubles of partials, in total
+ * more than 4 MiB) return DF_EWORKSPACE with the size in the error detail.  The first
  * call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls share the one array: calls whose kernels

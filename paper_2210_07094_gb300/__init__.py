@@ -209,7 +209,7 @@ def adjoint(mech: Mechanism, T0, p, Y0, dt: float, gT1=None, gY1=None, gQ1=None,
                "df_chem_adjoint_workspace_size")
     if not store_stages:
         N, M = mech.n_species, mech.n_reactions
-        size = C.c_size_t(8 * (n * int(max_steps) * (N + 2) + (n + 31) // 32 * M) + 256)
+        size = C.c_size_t(8 * (n * int(max_steps) * (N + 2) + (n + 15) // 16 * M) + 256)
     ws = torch.empty(size.value, dtype=torch.uint8, device=dev)
     out = {
         "gT0": torch.empty(n, dtype=torch.float64, device=dev),

@@ -65,25 +65,27 @@ struct AdjArgs {
   // (n^2) and row pivots (n), kept by the forward sweep so that the reverse
   // sweep need not recompute the step; null: the reverse sweep recomputes it
   double* stages;
+  int hook_cp;  // 8 NS: the Dual cpR vector's offset (doubles, units of the block size)
 };
 
 // Per-thread shared-memory doubles.  Without KEEP (the reverse sweep
 // recomputes each step): Dual C, wdot, gRT, hRT, cpR, sigma, v (14 NS) + W
-// (n^2) + K, Kbar (12 n) + theta (M) + u, ud (2 NS) + Rbar (n).  With KEEP (the
-// forward sweep stores each accepted step's stages and LU factors in the
-// workspace and the reverse sweep reads them there): the dual vectors, then a
-// region of max(n^2, 6n + M + 2NS) that holds Kbar, theta, u, ud in the
-// reverse sweep and W in the forward sweep, then Rbar; the forward sweep's K
-// sits in the derivative halves of the dual vectors, unused until the reverse
-// sweep (6n <= 7NS for NS >= 6).  Less shared memory per thread, more warps
-// per SM on the narrow FP64 pipe.
-template <int NS, bool KEEP = false>
-__host__ __device__ constexpr int adj_ws_doubles(int M) {
-  return KEEP ? 14 * NS + ((NS + 1) * (NS + 1) > 6 * (NS + 1) + M + 2 * NS ? (NS + 1) * (NS + 1)
-                                                                         : 6 * (NS + 1) + M + 2 * NS) +
-                    (NS + 1)
-              : 16 * NS + (NS + 1) * (NS + 1) + 13 * (NS + 1) + M;
+// (n^2) + K, Kbar (12 n) + theta (M).  With KEEP (the forward sweep stores each
+// accepted step's stages and LU factors in the workspace and the reverse sweep
+// reads them there): the dual vectors, then a region of max(n^2, 6n + M) that
+// holds Kbar and theta in the reverse sweep and W in the forward sweep; the
+// forward sweep's K sits in the derivative halves of the dual vectors, unused
+// until the reverse sweep (6n <= 7NS for NS >= 6).  In both, the ln A hook's
+// scratch u, ud shares the Dual cpR vector (eval_vjp writes cpR only after its
+// reaction loop, the one place that reads u), and its weights are the
+// cotangent eval_vjp is given.  Less shared memory per thread, more warps per
+// SM on the narrow FP64 pipe.
+__host__ __device__ constexpr int adj_layout_doubles(int NS, int M, bool keep) {
+  return keep ? 14 * NS + ((NS + 1) * (NS + 1) > 6 * (NS + 1) + M ? (NS + 1) * (NS + 1) : 6 * (NS + 1) + M)
+              : 14 * NS + (NS + 1) * (NS + 1) + 12 * (NS + 1) + M;
 }
+
+__host__ __device__ constexpr bool adj_keep_possible(int NS) { return 6 * (NS + 1) <= 7 * NS; }
 
 // read-only view of the stored stages in the workspace: element i at p[i * s],
 // s = ncells (64-bit offsets)
@@ -123,16 +125,18 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
       hRT{vb + 6 * NS * stride, 2 * stride}, cpR{vb + 8 * NS * stride, 2 * stride},
       sg{vb + 10 * NS * stride, 2 * stride}, vs{vb + 12 * NS * stride, 2 * stride};
   double* rest = base + (14 * NS) * stride + tid;
-  const int region = KEEP ? (n * n > 6 * n + M + 2 * NS ? n * n : 6 * n + M + 2 * NS) : n * n + 12 * n + M + 2 * NS;
   SV Wv{rest, stride};  // the forward sweep's W (both layouts) and the recomputed one
   SV Kv = KEEP ? SV{vb + 1, 2 * stride} : SV{rest + n * n * stride, stride};
   const int kstride = KEEP ? 2 * stride : stride;  // stride of a stage vector inside Kv
   double* kb0 = KEEP ? rest : rest + (n * n + 6 * n) * stride;
   SV Kb{kb0, stride};
   SV th{kb0 + 6 * n * stride, stride};
-  SV uu{kb0 + (6 * n + M) * stride, stride};
-  SV ud{kb0 + (6 * n + M + NS) * stride, stride};
-  SV vv{rest + region * stride, stride};
+  // the ln A hook's scratch: the Dual cpR vector (its value halves for the
+  // double evaluation), at an offset the launch passes in: where the compiler
+  // can see that the scratch and cpR coincide it schedules eval_vjp with
+  // several hundred bytes of register spills
+  SV uu{vb + a.hook_cp * stride, 2 * stride};
+  SVT<Dual> uD{reinterpret_cast<Dual*>(vb + a.hook_cp * stride), stride};
   const int th_off = 14 * NS + (KEEP ? 6 * n : n * n + 12 * n);  // theta's offset (units of stride)
   const RosTab& tb = c_tab_adj;
   for (int j = 0; j < M; ++j) th[j] = 0.0;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
         // f_T d(rho cp)/dy: one transposed product with e_T (which also adds the
         // ln A terms of Q through the hook) and the closed-form derivative of
         // rho cp = (p/T) A/B, A = sum_k Y_k cp_k/(R W_k), B = sum_k Y_k/W_k
-        ThetaHook hk{2, vv, gq, th, uu, ud};
+        ThetaHook hk{2, gq, th, uu, uD};
         double e0[n], b0[n], fq[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) e0[i] = i == 0 ? 1.0 : 0.0;
@@ -308,8 +312,6 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
           for (int j = 0; j < s; ++j)
 #pragma unroll
             for (int i = 0; i < n; ++i) Kb[j * n + i] += (tb.c[s][j] * ih) * r[i];
-#pragma unroll
-          for (int i = 0; i < n; ++i) vv[i] = r[i];
           // F_s = f(Y_s): Ybar_s = J(Y_s)^T Rbar, theta += (df/dlnA)(Y_s)^T Rbar
           double ysg[n], fs[n];
 #pragma unroll
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
             ysg[i] = acc;
           }
           {
-            ThetaHook hk{1, vv, 0.0, th, uu, ud};
+            ThetaHook hk{1, 0.0, th, uu, uD};
             double bj[n];
             eval_vjp<NS, double>(mv, pc, ysg, r, bj, fs, C, wd, gRT, hRT, cpR, sg, vs, &hk);
 #pragma unroll
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
             Dual yd[n], fd[n], bd[n];
 #pragma unroll
             for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kr[s * n + i]);
-            ThetaHook hk{1, vv, 0.0, th, uu, ud};
+            ThetaHook hk{1, 0.0, th, uu, uD};
             eval_vjp<NS, Dual>(mv, pc, yd, r, bd, fd, dC, dW, dG, dH, dCp, dS, dV, &hk);
 #pragma unroll
             for (int jc = 0; jc < n; ++jc) yb[jc] += bd[jc].d;
@@ -383,7 +385,20 @@ static int ensure_adj_table(int dev) {
   return rc;
 }
 
-static constexpr int ADJ_THREADS = 32;
+// Threads (cells) per block: as many, up to one warp, as let four blocks share
+// an SM.  Each of an SM's four sub-partitions has its own FP64 unit, and a
+// thread's workspace is too large for two warps per sub-partition, so a
+// fourth block keeps the fourth unit busy: four blocks of 31 threads do more
+// work than three of 32 (the 9-species layout: 226 doubles per thread).  Both
+// layouts use the count of the one with stored stages, so that their per-block
+// ln A partial sums group the cells alike and the gradients agree bitwise.
+static int adj_threads(const df_mech* m) {
+  const int NS = m->dims.N;
+  const long per = adj_layout_doubles(NS, m->dims.M, adj_keep_possible(NS));
+  const long budget = (long)m->smem_per_sm / 4 - (long)m->smem_reserved_per_block;  // bytes per block
+  const long t = (budget / (long)sizeof(double) - 128) / per;  // 128: the exp table
+  return t >= 16 && t < 32 ? (int)t : 32;
+}
 
 // Workspace: checkpoints [ncells][cap][n + 1], then the per-block ln A
 // partials, then (with_stages) the stored stages [cap][7n + n^2][ncells].
@@ -392,7 +407,8 @@ static constexpr int ADJ_THREADS = 32;
 static bool adj_compact_doubles(const df_mech* m, int64_t ncells, int cap, size_t* out) {
   if (ncells < 0 || cap < 1) return false;
   const size_t n = (size_t)m->dims.N + 1;
-  const size_t blocks = ((size_t)ncells + ADJ_THREADS - 1) / ADJ_THREADS;
+  const size_t threads = (size_t)adj_threads(m);
+  const size_t blocks = ((size_t)ncells + threads - 1) / threads;
   size_t ck = 0, part = 0;
   if (__builtin_mul_overflow((size_t)ncells, (size_t)cap, &ck) || __builtin_mul_overflow(ck, n + 1, &ck) ||
       __builtin_mul_overflow(blocks, (size_t)m->dims.M, &part) || __builtin_add_overflow(ck, part, out))
@@ -417,14 +433,18 @@ bool adjoint_workspace_bytes(const df_mech* m, int64_t ncells, int cap, bool wit
 
 template <int NS, bool KEEP>
 static int adjoint_dispatch_layout(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
-  const int threads = ADJ_THREADS;
-  const size_t per = (size_t)adj_ws_doubles<NS, KEEP>(m->dims.M) * threads;
-  size_t sm = sizeof(double) * (128 + ((m->dims.total + 1) & ~1) + per);
-  a.stage_blob = 1;
-  if (sm > m->max_smem_optin) {
-    a.stage_blob = 0;
-    sm = sizeof(double) * (128 + per);
-  }
+  const int threads = adj_threads(m);
+  const size_t per = (size_t)adj_layout_doubles(NS, m->dims.M, KEEP) * threads;
+  a.hook_cp = 8 * NS;
+  // the mechanism is staged in shared memory unless that leaves fewer blocks
+  // on an SM than reading it through L1
+  const size_t sm_staged = sizeof(double) * (128 + ((m->dims.total + 1) & ~1) + per);
+  const size_t sm_plain = sizeof(double) * (128 + per);
+  auto blocks_per_sm = [m](size_t b) {
+    return b > m->max_smem_optin ? (size_t)0 : m->smem_per_sm / (b + m->smem_reserved_per_block);
+  };
+  a.stage_blob = blocks_per_sm(sm_staged) >= blocks_per_sm(sm_plain) ? 1 : 0;
+  const size_t sm = a.stage_blob ? sm_staged : sm_plain;
   if (sm > m->max_smem_optin) return set_error(DF_EUNSUPPORTED, "adjoint workspace exceeds shared memory");
   auto kf = k_adjoint_thread<NS, KEEP>;
   int rc = cuda_check(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
@@ -445,7 +465,7 @@ static int adjoint_dispatch_layout(const df_mech* m, AdjArgs a, cudaStream_t st,
 // forward sweep's stage vectors fit the dual derivative halves
 template <int NS>
 static int adjoint_dispatch(const df_mech* m, AdjArgs a, cudaStream_t st, double* g_lnA) {
-  if constexpr (6 * (NS + 1) <= 7 * NS) {
+  if constexpr (adj_keep_possible(NS)) {
     if (a.stages) return adjoint_dispatch_layout<NS, true>(m, a, st, g_lnA);
   }
   return adjoint_dispatch_layout<NS, false>(m, a, st, g_lnA);

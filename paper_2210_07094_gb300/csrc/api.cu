@@ -97,6 +97,8 @@ int df_mech_load(const char* path, df_mech** out) {
   if (!rc) {
     m->num_sms = prop.multiProcessorCount;
     m->max_smem_optin = prop.sharedMemPerBlockOptin;
+    m->smem_per_sm = prop.sharedMemPerMultiprocessor;
+    m->smem_reserved_per_block = prop.reservedSharedMemPerBlock;
   }
   if (!rc) rc = cuda_check(cudaMalloc(&m->blob_dev, sizeof(double) * m->dims.total + 8), "cudaMalloc blob");
   if (!rc)

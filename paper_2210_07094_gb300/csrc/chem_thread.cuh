@@ -281,26 +281,27 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
 }
 
 // Optional accumulation of d/d ln A_j of a weighted sum of the right-hand side
-// (the discrete adjoint's parameter gradient).  Mode 1: weights v (adjoint
-// vector of dy/dt), i.e. th[j] += v . d f / d ln A_j = q_j sum_k nu_kj u_k with
-// u_k = (W_k v_{Y_k} - v_T H_k / cp) / rho.  Mode 2: heat release, th[j] +=
-// g * d qdot / d ln A_j with qdot = -0.1 sum_k H_k wdot_k [W/m^3].  With a Dual
-// scalar only the derivative part is accumulated.
+// (the discrete adjoint's parameter gradient), inside eval_vjp.  Mode 1: the
+// weights are eval_vjp's cotangent r of dy/dt, i.e. th[j] += r . d f / d ln A_j
+// = q_j sum_k nu_kj u_k with u_k = (W_k r_{Y_k} - r_T H_k / cp) / rho.  Mode 2:
+// heat release, th[j] += g * d qdot / d ln A_j with qdot = -0.1 sum_k H_k wdot_k
+// [W/m^3].  With a Dual scalar only the derivative part is accumulated.  The
+// scratch u may be the storage of eval_vjp's cpR vector: eval_vjp reads u only
+// in its reaction loop and writes cpR after it.
 struct ThetaHook {
-  int mode;   // 0: off
-  SV v;       // mode 1: adjoint vector (n entries)
-  double g;   // mode 2: weight
-  SV th;      // per-thread accumulator, M entries
-  SV u;       // per-thread scratch, N entries (value parts)
-  SV ud;      // per-thread scratch, N entries (derivative parts, Dual only)
+  int mode;        // 0: off
+  double g;        // mode 2: weight
+  SV th;           // per-thread accumulator, M entries
+  SV u;            // per-thread scratch, N entries (double evaluation)
+  SVT<Dual> uD;    // per-thread scratch, N entries (Dual evaluation)
 };
 
 __device__ __forceinline__ void th_add(const ThetaHook& h, int j, double x) { h.th[j] += x; }
 __device__ __forceinline__ void th_add(const ThetaHook& h, int j, const Dual& x) { h.th[j] += x.d; }
 __device__ __forceinline__ void u_store(const ThetaHook& h, int k, double x) { h.u[k] = x; }
-__device__ __forceinline__ void u_store(const ThetaHook& h, int k, const Dual& x) { h.u[k] = x.v; h.ud[k] = x.d; }
+__device__ __forceinline__ void u_store(const ThetaHook& h, int k, const Dual& x) { h.uD[k] = x; }
 __device__ __forceinline__ double u_load(const ThetaHook& h, int k, double) { return h.u[k]; }
-__device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) { return Dual(h.u[k], h.ud[k]); }
+__device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) { return h.uD[k]; }
 
 // Evaluate f = dy/dt for y = (T, Y) and, when WITH_J, the analytic Jacobian
 // J = df/dy (row-major in the strided view Jv, n x n with n = NS + 1).
@@ -314,8 +315,7 @@ __device__ __forceinline__ Dual u_load(const ThetaHook& h, int k, const Dual&) {
 template <int NS, bool WITH_J, class S = double, bool CONSTV = false, int ST = 0>
 __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, const S (&y)[NS + 1], S (&f)[NS + 1],
                                          SVT<S, ST> C, SVT<S, ST> wdot, SVT<S, ST> gRT, SVT<S, ST> hRT,
-                                         SVT<S, ST> cpR, SVT<S, ST> Jv,
-                                         const ThetaHook* hook = nullptr) {
+                                         SVT<S, ST> cpR, SVT<S, ST> Jv) {
   constexpr int n = NS + 1;
   constexpr double EV = CONSTV ? 1.0 : 0.0;  // U/(RT) = H/(RT) - 1, cv/R = cp/R - 1
   const S T = y[0];
@@ -345,16 +345,6 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
     C[k] = rho * y[1 + k] * mv.sp[SP_REC * k + 1];
     wdot[k] = S(0.0);
   }
-  if (hook && hook->mode) {
-#pragma unroll
-    for (int k = 0; k < NS; ++k) {
-      const S Hk = RU * T * (hRT[k] - EV);
-      S uk;
-      if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * hook->v[1 + k] - hook->v[0] * Hk * invcp) * invrho;
-      else uk = -0.1 * hook->g * Hk;
-      u_store(*hook, k, uk);
-    }
-  }
   if (WITH_J) {
 #pragma unroll
     for (int i = 0; i < n * n; ++i) Jv[i] = S(0.0);
@@ -373,14 +363,6 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
     wdot[mt.prod[0]] += q;
     if (np > 1) wdot[mt.prod[1]] += q;
     if (np > 2) wdot[mt.prod[2]] += q;
-    if (hook && hook->mode) {
-      S w = u_load(*hook, mt.prod[0], q) - u_load(*hook, mt.reac[0], q);
-      if (np > 1) w += u_load(*hook, mt.prod[1], q);
-      if (np > 2) w += u_load(*hook, mt.prod[2], q);
-      if (nr > 1) w -= u_load(*hook, mt.reac[1], q);
-      if (nr > 2) w -= u_load(*hook, mt.reac[2], q);
-      th_add(*hook, j, q * w);
-    }
     if (WITH_J) {
       // d q / d C of each reactant / product entry (product rule, no division)
       S dr[3], dp[3];
@@ -492,7 +474,8 @@ __device__ __forceinline__ S eval_thread(const MechView& mv, const double pc, co
 //   b_{Y_i} = (v_i + D Wbar / rho) / W_i + r_0 e_i
 // with e the temperature row's own terms (e_T = -(cpf + f_T dcp/dT) / cp,
 // e_i = -f_T cp_i / cp).  Also returns f = dy/dt (f may alias nothing) and, with
-// a hook, its ln A terms.  sig and v are N-entry scratch vectors.
+// a hook, its ln A terms.  sig and v are N-entry scratch vectors; cpR receives
+// cp_k/R after the reaction loop (the hook's u, ud may share its storage).
 template <int NS, class S = double>
 __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, const S (&y)[NS + 1],
                                          const double (&r)[NS + 1], S (&b)[NS + 1], S (&f)[NS + 1], SVT<S> C,
@@ -506,7 +489,6 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
   for (int k = 0; k < NS; ++k) {
     const double* a = mv.sp + SP_REC * k + 2;
     const S cpk = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-    cpR[k] = cpk;
     const double* ah = mv.sp + SP_REC * k + SP_H;  // a2/2 .. a5/5
     const double* as = mv.sp + SP_REC * k + SP_S;  // a3/2 .. a5/4
     const S hk = a[0] + T * (ah[0] + T * (ah[1] + T * (ah[2] + T * ah[3]))) + a[5] * invT;
@@ -533,7 +515,7 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
     for (int k = 0; k < NS; ++k) {
       const S Hk = RU * T * hRT[k];
       S uk;
-      if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * hook->v[1 + k] - hook->v[0] * Hk * invcp) * invrho;
+      if (hook->mode == 1) uk = (mv.sp[SP_REC * k] * r[1 + k] - r[0] * Hk * invcp) * invrho;
       else uk = -0.1 * hook->g * Hk;
       u_store(*hook, k, uk);
     }
@@ -581,6 +563,13 @@ __device__ __forceinline__ void eval_vjp(const MechView& mv, const double pc, co
 #pragma unroll
       for (int l = 0; l < NS; ++l) v[l] += wM * ef[l];
     }
+  }
+  // cp_k/R, recomputed (the same arithmetic as in the first loop) now that the
+  // hook's scratch is no longer read
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const double* a = mv.sp + SP_REC * k + 2;
+    cpR[k] = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
   }
   S Hw(0.0), sw(0.0), svc(0.0);
 #pragma unroll

@@ -36,6 +36,7 @@ struct df_mech {
   int64_t tuned_for_ncells = -1;
   int num_sms = 0;
   size_t max_smem_optin = 0;
+  size_t smem_per_sm = 0, smem_reserved_per_block = 0;
   // generated thread-path kernel (codegen.cu): 1 when the last thread-path
   // launch used it, and its state (compile time, or why it is unavailable)
   int jit_used = 0;
