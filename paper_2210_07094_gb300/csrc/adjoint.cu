@@ -320,7 +320,9 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
             for (int j = 0; j < s; ++j) acc += tb.a[s][j] * Kr[j * n + i];
             ysg[i] = acc;
           }
-          {
+          // the first stage is evaluated at the step's start, where the dual
+          // evaluation below is: its value part stands in for this product
+          if (s > 0) {
             ThetaHook hk{1, 0.0, th, uu, uD};
             double bj[n];
             eval_vjp<NS, double>(mv, pc, ysg, r, bj, fs, C, wd, gRT, hRT, cpR, sg, vs, &hk);
@@ -335,8 +337,12 @@ __global__ void __launch_bounds__(32, 1) k_adjoint_thread(AdjArgs a) {
             Dual yd[n], fd[n], bd[n];
 #pragma unroll
             for (int i = 0; i < n; ++i) yd[i] = Dual(yi[i], Kr[s * n + i]);
-            ThetaHook hk{1, 0.0, th, uu, uD};
+            ThetaHook hk{1, 0.0, th, uu, uD, s == 0 ? 1 : 0};
             eval_vjp<NS, Dual>(mv, pc, yd, r, bd, fd, dC, dW, dG, dH, dCp, dS, dV, &hk);
+            if (s == 0) {
+#pragma unroll
+              for (int jc = 0; jc < n; ++jc) yb[jc] += bd[jc].v;
+            }
 #pragma unroll
             for (int jc = 0; jc < n; ++jc) yb[jc] += bd[jc].d;
           }

@@ -285,7 +285,9 @@ __device__ __forceinline__ void rate_one(const MechView& mv, const double* r, in
 // weights are eval_vjp's cotangent r of dy/dt, i.e. th[j] += r . d f / d ln A_j
 // = q_j sum_k nu_kj u_k with u_k = (W_k r_{Y_k} - r_T H_k / cp) / rho.  Mode 2:
 // heat release, th[j] += g * d qdot / d ln A_j with qdot = -0.1 sum_k H_k wdot_k
-// [W/m^3].  With a Dual scalar only the derivative part is accumulated.  The
+// [W/m^3].  With a Dual scalar only the derivative part is accumulated, or,
+// with both set, the value part and then the derivative part (a Dual
+// evaluation that also stands in for the double one at the same point).  The
 // scratch u may be the storage of eval_vjp's cpR vector: eval_vjp reads u only
 // in its reaction loop and writes cpR after it.
 struct ThetaHook {
@@ -294,10 +296,14 @@ struct ThetaHook {
   SV th;           // per-thread accumulator, M entries
   SV u;            // per-thread scratch, N entries (double evaluation)
   SVT<Dual> uD;    // per-thread scratch, N entries (Dual evaluation)
+  int both = 0;    // Dual evaluation: accumulate the value part too
 };
 
 __device__ __forceinline__ void th_add(const ThetaHook& h, int j, double x) { h.th[j] += x; }
-__device__ __forceinline__ void th_add(const ThetaHook& h, int j, const Dual& x) { h.th[j] += x.d; }
+__device__ __forceinline__ void th_add(const ThetaHook& h, int j, const Dual& x) {
+  if (h.both) h.th[j] += x.v;
+  h.th[j] += x.d;
+}
 __device__ __forceinline__ void u_store(const ThetaHook& h, int k, double x) { h.u[k] = x; }
 __device__ __forceinline__ void u_store(const ThetaHook& h, int k, const Dual& x) { h.uD[k] = x; }
 __device__ __forceinline__ double u_load(const ThetaHook& h, int k, double) { return h.u[k]; }
