@@ -39,18 +39,26 @@ UNIT = "cell-steps/s"
 # counted.
 FLOP_PER_SUBSTEP = 18665
 # dram__bytes_read.sum + dram__bytes_write.sum of that launch (same kernel build)
-TRAFFIC_PER_LAUNCH = 233112576 + 237247232
+TRAFFIC_PER_LAUNCH = 232208384 + 235899648
 # hash of the device sources that kernel is built from, when the two counters
 # above were taken; a different hash at run time marks them stale in the line
 COUNTERS_SOURCES = ("integrate_thread.cuh", "rosenbrock.cuh", "chem_thread.cuh", "dev_common.cuh", "fastexp.cuh",
                     "fastlog.cuh", "fastlog_table.inc", "codegen.cu")
-COUNTERS_SOURCE_HASH = "4e6cc29f4ce7ada5"
+COUNTERS_SOURCE_HASH = "407c9aa43d9c9c3a"
+# the same for the 50-species one-warp-per-cell path: FP64 operations per
+# substep from ncu's DP thread-instruction counters of one launch on 8192 cells
+# of the 50-species field (2*DFMA + DADD + DMUL over its substeps), and the
+# hash of the sources of that kernel when they were taken
+FLOP_PER_SUBSTEP_50 = 359934
+COUNTERS50_SOURCES = ("integrate.cu", "chem_warp.cuh", "chem_thread.cuh", "dev_common.cuh", "fastexp.cuh",
+                      "fastlog.cuh", "fastlog_table.inc")
+COUNTERS50_SOURCE_HASH = "599741d0cdf79adf"
 
 
-def counters_source_hash() -> str:
+def counters_source_hash(names=COUNTERS_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in COUNTERS_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_2210_07094_gb300", "csrc", name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
@@ -306,10 +314,11 @@ def ignition_case(ncells: int = 65536, nsteps: int = 150, dt: float = 2e-3):
             "failed_cells": int((st != 0).sum())}
 
 
-def chon_case():
+def chon_case(fp64_peak_gflops=None):
     """The 50-species / 300-reaction mechanism on 262144 cells (T ~ U[800,2200]
     K, 1 atm): one warp per cell, launch shape from the autotuner on an
-    8192-cell sample, one timed launch."""
+    8192-cell sample, one timed launch; with the measured FP64 peak, the
+    launch's FP64 rate from the per-substep operation count."""
     import torch
     import paper_2210_07094_gb300 as df
     from paper_2210_07094_gb300 import synth
@@ -338,7 +347,15 @@ def chon_case():
             "cells": n, "ms": ms, "cell_steps_per_s": n / (ms * 1e-3),
             "substeps_per_cell": {"accepted": acc / n, "rejected": rej / n},
             "launch_shape": {"block_threads": best.block_threads, "order_by_T": best.order_by_T},
-            "failed_cells": int((st["s"] != 0).sum())}
+            "failed_cells": int((st["s"] != 0).sum()),
+            "fp64": _chon_fp64(acc + rej, ms, fp64_peak_gflops)}
+
+
+def _chon_fp64(attempts, ms, peak_gflops):
+    gflops = FLOP_PER_SUBSTEP_50 * attempts / (ms * 1e-3) / 1e9
+    return {"flop_per_substep": FLOP_PER_SUBSTEP_50, "achieved_gflops": gflops,
+            "frac_of_measured_peak": gflops / peak_gflops if peak_gflops else None,
+            "counters_current": counters_source_hash(COUNTERS50_SOURCES) == COUNTERS50_SOURCE_HASH}
 
 
 def run_reference(args):
@@ -705,7 +722,7 @@ def main():
     }
     if rank == 0 and not args.no_extra and ncells == NCELLS:
         line["adjoint"] = adjoint_case()
-        line["chon_50_species"] = chon_case()
+        line["chon_50_species"] = chon_case(fp64_peak)
         line["ignition_multistep"] = ignition_case()
     if rank == 0 and not args.no_dnn and ncells == NCELLS:
         # learned surrogate (BF16 tensor-core MLP) on the same GPU and cell distribution
