@@ -29,8 +29,11 @@ int df_probe_fp64_chains(int warps_per_sm, int chains, int iters, double* ns_per
 
 /* y[i] = exp(x[i]) for i < n by the library's own table-driven exponential
  * (the one the rate kernels use), so that its accuracy can be checked against
- * CUDA's exp.  x, y: device memory; asynchronous on `stream` (a cudaStream_t). */
-int df_probe_exp(const double* x, double* y, long long n, void* stream);
+ * CUDA's exp.  table_bits: 6 (the 64-entry table of the library's kernels) or
+ * 8 (the 256-entry table of the kernels generated for a loaded mechanism).
+ * x, y: device memory; asynchronous on `stream` (a cudaStream_t).  Returns 0,
+ * or DF_EINVAL for a negative n, a missing buffer or other table_bits. */
+int df_probe_exp(const double* x, double* y, long long n, int table_bits, void* stream);
 
 /* y[i] = ln(x[i]) by the library's own table-driven logarithm (the one the
  * rate kernels use for ln T and the Troe falloff), so that its accuracy can be

@@ -85,7 +85,7 @@ SIGNATURES = [
     ("df_get_last_error_detail", _i, [C.c_char_p, _sz]),
     ("df_probe_fp64_peak", _i, [_i, _p, _p]),
     ("df_probe_fp64_chains", _i, [_i, _i, _i, _p, _p]),
-    ("df_probe_exp", _i, [_p, _p, C.c_longlong, _p]),
+    ("df_probe_exp", _i, [_p, _p, C.c_longlong, _i, _p]),
     ("df_probe_gelu", _i, [_p, _p, C.c_longlong, _i, _p]),
     ("df_probe_log", _i, [_p, _p, C.c_longlong, _p]),
     ("df_probe_gemm_bf16", _i, [_p, _p, _p, _i, _i, _i, _i, _p, _p]),

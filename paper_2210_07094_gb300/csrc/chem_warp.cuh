@@ -71,16 +71,6 @@ __device__ __forceinline__ double cp_species(const MechView& mv, int k, double T
   return a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
 }
 
-// a small nonzero integer (a stoichiometric coefficient, |v| < 2^20) as a
-// double, assembled with integer operations so that it takes no slot of the
-// narrow FP64 pipe
-__device__ __forceinline__ double int_to_double_small(int v) {
-  const unsigned a = (unsigned)(v < 0 ? -v : v);
-  const int lz = __clz(a);                                     // a >= 1: the leading one at bit 31 - lz
-  const unsigned mant = ((a << lz) << 1) >> 12;                // the 20 bits below the leading one
-  const unsigned hi = ((unsigned)(v < 0) << 31) | ((unsigned)(1023 + 31 - lz) << 20) | mant;
-  return __hiloint2double((int)hi, 0);
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -175,7 +165,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
         acc = 0.0;
       }
       const int e = t < la ? ba + t : bb + (t - la);
-      acc = fma(int_to_double_small(csr[N + 2 + 2 * e]), ws[L.q + csr[N + 1 + 2 * e]], acc);
+      acc = fma(small_int_to_double(csr[N + 2 + 2 * e]), ws[L.q + csr[N + 1 + 2 * e]], acc);
     }
     if (lb > 0) wb = acc;
     else wa = acc;
@@ -216,7 +206,7 @@ __device__ double warp_eval(const MechView& mv, const int* csr, int N, double pc
       double* row = J + (1 + (first ? ka : kb)) * n;
       {
         const int j = csr[N + 1 + 2 * e];
-        const double nu = int_to_double_small(csr[N + 2 + 2 * e]);
+        const double nu = small_int_to_double(csr[N + 2 + 2 * e]);
         const double* r = mv.rx + RX_REC * j;
         const RxMeta mt = load_meta(r);
         const int nr = mt.nrnp & 15, np = mt.nrnp >> 4;

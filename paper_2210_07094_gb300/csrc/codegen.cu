@@ -112,6 +112,15 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "  const double invrho = 1.0 / rho;\n  const double invcp = 1.0 / cpm;\n";
   for (int k = 0; k < N; ++k)
     o << "  C[" << k << "] = rho * y[" << 1 + k << "] * " << lit(sp(k, 1)) << ";\n  wdot[" << k << "] = 0.0;\n";
+  // [M] = sum_l eps_l C_l of the third-body and falloff reactions as the sum of
+  // all concentrations (once) plus (eps_l - 1) C_l where eps_l is not 1 (exact
+  // literals: eps_l - 1 rounds to nothing for eps_l >= 1/2)
+  bool any_collider = false;
+  for (int j = 0; j < M; ++j) any_collider = any_collider || (meta_of(m, j).flags & 3) != 0;
+  if (any_collider) {
+    o << "  double ctot = C[0];\n";
+    for (int k = 1; k < N; ++k) o << "  ctot += C[" << k << "];\n";
+  }
   o
     << "  if (WITH_J) {\n#pragma unroll\n    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;\n  }\n"
     << "  const double lnP0RT = LOG_PSTD_RU - lnT;\n";
@@ -141,8 +150,9 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     o << "    g.sg = sg;\n    g.sh = sh;\n";
     auto eff = [&](int l) { return m->blob_host[m->dims.off_eff + N * sl.eff + l]; };
     if (type != 0) {
-      o << "    {\n      double Mc = 0.0;\n";
-      for (int l = 0; l < N; ++l) o << "      Mc += " << lit(eff(l)) << " * C[" << l << "];\n";
+      o << "    {\n      double Mc = ctot;\n";
+      for (int l = 0; l < N; ++l)
+        if (eff(l) != 1.0) o << "      Mc += " << lit(eff(l) - 1.0) << " * C[" << l << "];\n";
       o << "      g.Mc = Mc;\n    }\n";
     } else {
       o << "    g.Mc = 0.0;\n";
@@ -405,6 +415,9 @@ std::map<std::pair<int, std::string>, Module> g_modules;
 
 constexpr int kThreads[] = {32, 64};
 constexpr int kIgnThreads = 32;  // the block size of the kernel that refines the ignition time
+// the generated kernels' exp table: 256 entries (one FP64 operation fewer per
+// exponential than the library's 64; 4 KB of shared memory per block)
+constexpr int kGenExpTableBits = 8;
 
 // ---------------------------------------------------------------------------
 // on-disk cache of compiled modules: <dir>/<key>.cubin and <key>.names (the
@@ -472,7 +485,7 @@ uint64_t headers_hash(const std::string& inc) {
   std::call_once(once, [&] {
     uint64_t acc = 1469598103934665603ull;
     const char* files[] = {"integrate_thread.cuh", "rosenbrock.cuh", "chem_thread.cuh", "dev_common.cuh",
-                           "fastexp.cuh", "fastlog.cuh", "fastlog_table.inc", "dual.cuh"};
+                           "fastexp.cuh", "fastexp_table256.inc", "fastlog.cuh", "fastlog_table.inc", "dual.cuh"};
     for (const char* fn : files) {
       std::string d;
       read_file(inc + "/" + fn, &d);
@@ -560,8 +573,9 @@ Module build_module(int dev, const df_mech* m, const std::string& src) {
   names.push_back(jit_kernel_name(m->dims.N, kIgnThreads, true));
   names.push_back("&df::c_tab");
   const std::string incopt = "-I" + inc;
+  const std::string expopt = "-DDF_EXP_TABLE_BITS=" + std::to_string(kGenExpTableBits);
   const char* opts[] = {arch.c_str(), "-std=c++17", incopt.c_str(), "-default-device", "-lineinfo",
-                        "-diag-suppress=177"};
+                        "-diag-suppress=177", expopt.c_str()};
   // the on-disk cache: keyed by the generated source, the device headers, the
   // architecture, the NVRTC version, the compile options (the include path
   // left out: a moved tree keeps its entries) and the entry format
@@ -665,12 +679,16 @@ int jit_thread_launch(df_mech* m, int threads, int bps, const IntegArgs& a, cuda
   const int N = m->dims.N;
   const int per_thread = (N + 1) * (N + 1) + 6 * (N + 1);  // J and the stage vectors
   IntegArgs args = a;
-  args.stage_blob = 1;
-  size_t sm = sizeof(double) * (128 + (size_t)blob_smem_doubles(m->dims) + (size_t)per_thread * threads);
-  if (sm > m->max_smem_optin) {
-    args.stage_blob = 0;
-    sm = sizeof(double) * (128 + (size_t)per_thread * threads);
-  }
+  // the exp table (2 doubles per entry), the mechanism if staging it leaves as
+  // many blocks on an SM as reading it through L1, the per-thread workspace
+  const size_t tab = 2 * ((size_t)1 << kGenExpTableBits);
+  const size_t sm_staged = sizeof(double) * (tab + (size_t)blob_smem_doubles(m->dims) + (size_t)per_thread * threads);
+  const size_t sm_plain = sizeof(double) * (tab + (size_t)per_thread * threads);
+  auto blocks_per_sm = [m](size_t b) {
+    return b > m->max_smem_optin ? (size_t)0 : m->smem_per_sm / (b + m->smem_reserved_per_block);
+  };
+  args.stage_blob = blocks_per_sm(sm_staged) >= blocks_per_sm(sm_plain) ? 1 : 0;
+  const size_t sm = args.stage_blob ? sm_staged : sm_plain;
   if (sm > m->max_smem_optin) return DF_OK;
   if (drv.set_attr(fk, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)sm) != CUDA_SUCCESS)
     return set_error(DF_ECUDA, "generated integrator: shared-memory attribute");

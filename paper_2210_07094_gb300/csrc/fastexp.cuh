@@ -8,10 +8,22 @@
 // ln2/64 split into two doubles with fused multiply-adds.  The truncated Taylor
 // tail r^6/720 <= 3.5e-17 stays below one ulp.  |x| >= 700, inf and NaN go to
 // the library exp().  The kernels stage the table into shared memory (lanes
-// index it with different j).
+// index it with different j).  A variant with 256 entries 2^(j/256) (|r| <=
+// ln2/512, so exp(r) - 1 needs terms only up to r^4/24, the tail r^5/120 <=
+// 3.8e-17) saves one FP64 operation per exponential for 4 KB of shared memory
+// per block instead of 1 KB; a translation unit picks it by defining
+// DF_EXP_TABLE_BITS as 8 (the kernels generated for a loaded mechanism).
 #pragma once
 
+#ifndef DF_EXP_TABLE_BITS
+#define DF_EXP_TABLE_BITS 6
+#endif
+
 namespace df {
+
+constexpr int EXP_TAB_BITS = DF_EXP_TABLE_BITS;
+static_assert(EXP_TAB_BITS == 6 || EXP_TAB_BITS == 8, "exp table: 64 or 256 entries");
+constexpr int EXP_TAB_SIZE = 1 << EXP_TAB_BITS;
 
 static __device__ const double2 g_exp2_tab[64] = {
     {0x1.0000000000000p+0, 0x0.0p+0},
@@ -80,27 +92,59 @@ static __device__ const double2 g_exp2_tab[64] = {
     {0x1.fa7c1819e90d8p+0, 0x1.74853f3a5931ep-55},
 };
 
-// the reduction and polynomial of exp_tang for |x| < 700 (no range guard)
-__device__ __forceinline__ double exp_tang_core(double x, const double2* tab) {
+// (double)v for |v| < 2^20, assembled from the integer's sign, leading one and
+// the bits below it with integer operations, so that the conversion takes no
+// slot of the narrow FP64 pipe (exact: every such integer is a double)
+__device__ __forceinline__ double small_int_to_double(int v) {
+  const unsigned a = (unsigned)(v < 0 ? -v : v);
+  const int lz = __clz(a | 1u);                  // the leading one of a > 0 at bit 31 - lz
+  const unsigned mant = ((a << lz) << 1) >> 12;  // the (at most 19) bits below it, left-aligned
+  const unsigned hi = ((unsigned)(v < 0) << 31) | ((unsigned)(1023 + 31 - lz) << 20) | mant;
+  return __hiloint2double(a != 0u ? (int)hi : 0, 0);
+}
+
+// 2^(j/256) as double-doubles (gen_exptab.py, 60-digit evaluation)
+static __device__ const double2 g_exp2_tab256[256] = {
+#include "fastexp_table256.inc"
+};
+
+// the table the kernels of this translation unit stage into shared memory
+__device__ __forceinline__ const double2* exp_table_src() { return EXP_TAB_BITS == 8 ? g_exp2_tab256 : g_exp2_tab; }
+
+// the reduction and polynomial of exp_tang for |x| < 700 (no range guard), with
+// a table of 2^B entries
+template <int B>
+__device__ __forceinline__ double exp_tang_core_b(double x, const double2* tab) {
+  static_assert(B == 6 || B == 8, "exp table: 64 or 256 entries");
   const double SHIFT = 0x1.8p52;                 // 1.5 * 2^52: round-to-integer shifter
-  const double INV_L = 0x1.71547652b82fep+6;     // 64 / ln 2
-  const double L1 = 0x1.62e42fefa39efp-7;        // ln 2 / 64, leading part
-  const double L2 = 0x1.abc9e3b39803fp-62;       // ln 2 / 64, trailing part
+  // 2^B / ln 2, and ln 2 / 2^B in a leading and a trailing part
+  const double INV_L = B == 8 ? 0x1.71547652b82fep+8 : 0x1.71547652b82fep+6;
+  const double L1 = B == 8 ? 0x1.62e42fefa39efp-9 : 0x1.62e42fefa39efp-7;
+  const double L2 = B == 8 ? 0x1.abc9e3b39803fp-64 : 0x1.abc9e3b39803fp-62;
   const double t = fma(x, INV_L, SHIFT);
-  const int k = __double2loint(t);
-  const double kd = t - SHIFT;
+  const int k = __double2loint(t);               // t = SHIFT + k exactly; |k| < 2^18
+  const double kd = small_int_to_double(k);      // = t - SHIFT, without an FP64 subtraction
   double r = fma(-kd, L1, x);
   r = fma(-kd, L2, r);
-  const int j = k & 63;
-  const int m = k >> 6;
+  const int j = k & ((1 << B) - 1);
+  const int m = k >> B;
   const double r2 = r * r;
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(q, r, 1.0 / 6.0);
+  double q;
+  if (B == 8) {
+    q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+  } else {
+    q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    q = fma(q, r, 1.0 / 6.0);
+  }
   q = fma(q, r, 0.5);
   const double p = fma(q, r2, r);                // exp(r) - 1
   const double2 tj = tab[j];
-  const double s = tj.x + fma(tj.x, p, tj.y);    // 2^(j/64) * exp(r)
+  const double s = tj.x + fma(tj.x, p, tj.y);    // 2^(j/2^B) * exp(r)
   return __hiloint2double(__double2hiint(s) + (int)((unsigned)m << 20), __double2loint(s));
+}
+
+__device__ __forceinline__ double exp_tang_core(double x, const double2* tab) {
+  return exp_tang_core_b<EXP_TAB_BITS>(x, tab);
 }
 
 // exp of two arguments at once: both reductions and polynomials in one
@@ -117,12 +161,15 @@ __device__ __forceinline__ void exp_tang2(double x1, double x2, const double2* t
   }
 }
 
-__device__ __forceinline__ double exp_tang(double x, const double2* tab) {
+template <int B>
+__device__ __forceinline__ double exp_tang_b(double x, const double2* tab) {
   // |x| >= 700, inf and NaN, tested on the high word with integer operations
   // (0x4085E000 is the high word of 700.0; the low word of 700.0 is zero), so
   // the narrow FP64 pipe is not spent on the guard
   if ((__double2hiint(x) & 0x7fffffff) >= 0x4085E000) return exp(x);
-  return exp_tang_core(x, tab);
+  return exp_tang_core_b<B>(x, tab);
 }
+
+__device__ __forceinline__ double exp_tang(double x, const double2* tab) { return exp_tang_b<EXP_TAB_BITS>(x, tab); }
 
 }  // namespace df

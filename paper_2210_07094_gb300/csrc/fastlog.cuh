@@ -12,6 +12,7 @@
 // Troe quantities enter as addends).  Zero, negative, subnormal, inf and NaN
 // arguments go to the library log().  About 13 FP64 operations.
 #pragma once
+#include "fastexp.cuh"  // small_int_to_double
 
 namespace df {
 
@@ -42,7 +43,7 @@ __device__ __forceinline__ double log_tab(double x) {
   p = fma(p, t, 1.0 / 3.0);
   p = fma(p, t, -0.5);
   const double lp = fma(p, t * t, t);  // log1p(t)
-  const double md = (double)m;
+  const double md = small_int_to_double(m);  // exact, on the integer pipes
   return fma(md, LN2_HI, lh) + (fma(md, LN2_LO, ll) + lp);
 }
 

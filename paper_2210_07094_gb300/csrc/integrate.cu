@@ -403,7 +403,7 @@ namespace {
 
 template <int NS>
 size_t thread_smem_bytes(const MechDims& d, int threads, bool stage) {
-  return sizeof(double) * (128 + (stage ? blob_smem_doubles(d) : 0) + (size_t)thread_ws_doubles<NS>() * threads);
+  return sizeof(double) * (2 * EXP_TAB_SIZE + (stage ? blob_smem_doubles(d) : 0) + (size_t)thread_ws_doubles<NS>() * threads);
 }
 
 template <int NS>

@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   const int stride = BT > 0 ? BT : blockDim.x;
   const double* blob = a.blob;
   double2* etab = reinterpret_cast<double2*>(smem);
-  for (int i = tid; i < 64; i += stride) etab[i] = g_exp2_tab[i];
-  int boff = 128;
+  for (int i = tid; i < EXP_TAB_SIZE; i += stride) etab[i] = exp_table_src()[i];
+  int boff = 2 * EXP_TAB_SIZE;
   if (a.stage_blob) {
     for (int i = tid; i < a.d.total; i += stride) smem[boff + i] = a.blob[i];
     blob = smem + boff;

@@ -35,12 +35,14 @@ __global__ void k_fma_chains(double* out, int iters, double a, double b) {
   out[tid] = s;
 }
 
+template <int B>
 __global__ void k_exp_probe(const double* x, double* y, long long n) {
-  __shared__ double2 tab[64];
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) tab[i] = g_exp2_tab[i];
+  __shared__ double2 tab[1 << B];
+  const double2* src = B == 8 ? g_exp2_tab256 : g_exp2_tab;
+  for (int i = threadIdx.x; i < (1 << B); i += blockDim.x) tab[i] = src[i];
   __syncthreads();
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) y[i] = exp_tang(x[i], tab);
+  if (i < n) y[i] = exp_tang_b<B>(x[i], tab);
 }
 
 __global__ void k_log_probe(const double* x, double* y, long long n) {
@@ -59,11 +61,14 @@ extern "C" int df_probe_log(const double* x, double* y, long long n, void* strea
   return cuda_check(cudaGetLastError(), "log probe kernel");
 }
 
-extern "C" int df_probe_exp(const double* x, double* y, long long n, void* stream) {
-  if (n < 0 || (n > 0 && (!x || !y))) return set_error(DF_EINVAL, "df_probe_exp: bad arguments");
+extern "C" int df_probe_exp(const double* x, double* y, long long n, int table_bits, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y)) || (table_bits != 6 && table_bits != 8))
+    return set_error(DF_EINVAL, "df_probe_exp: bad arguments");
   if (n == 0) return DF_OK;
   const int threads = 256;
-  k_exp_probe<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(x, y, n);
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (table_bits == 8) k_exp_probe<8><<<blocks, threads, 0, (cudaStream_t)stream>>>(x, y, n);
+  else k_exp_probe<6><<<blocks, threads, 0, (cudaStream_t)stream>>>(x, y, n);
   return cuda_check(cudaGetLastError(), "exp probe kernel");
 }
 

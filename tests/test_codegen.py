@@ -123,9 +123,11 @@ def test_generated_literals_are_the_mechanism_numbers(tmp_path):
         assert beta == [r["b"]]
         assert ear == [pytest.approx(r["Ea"] * 1e3 / R, rel=1e-15)]
         if r["type"] != "elementary":
+            # [M] = sum of all C plus (eps_l - 1) C_l for every eps_l != 1
+            assert "double Mc = ctot;" in blk
             mc = [_lits(ln)[0] for ln in blk.splitlines() if "Mc +=" in ln]
             eff = [r.get("efficiencies", {}).get(nm, 1.0) for nm in names]
-            assert mc == eff
+            assert mc == [e - 1.0 for e in eff if e != 1.0]
         if r["type"] == "falloff-troe":
             trp = _lits([ln for ln in blk.splitlines() if "trp[" in ln][0])
             lo, tr = r["low"], r["troe"]
