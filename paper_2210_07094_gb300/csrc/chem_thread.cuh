@@ -196,7 +196,10 @@ __device__ __forceinline__ void rate_compute(const MechView& mv, const RxIn<S>& 
   const S Pb = g.cp[0] * g.cp[1] * g.cp[2];
   const S sg = g.sg, sh = g.sh;
   const int dnu = np - nr;
-  const S lnKcinv = sg - (double)dnu * lnP0RT;  // ln(1/K_c)
+  // ln(1/K_c); a reaction that keeps its mole count has no pressure term (no
+  // operation where the counts are known at compile time, as in the kernels
+  // generated for a mechanism; the same value either way)
+  const S lnKcinv = dnu == 0 ? sg : sg - (double)dnu * lnP0RT;
   S kf, kr, mult(1.0), dqdM(0.0), dlnk(0.0);
   const RxSlots sl = g.sl;
   o.sl = sl;

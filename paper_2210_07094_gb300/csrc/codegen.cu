@@ -202,16 +202,26 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
         if (p[i] == l) terms += (terms.empty() ? "" : " + ") + std::string("dp") + std::to_string(i);
       o << "        const double dq" << l << " = " << terms << ";\n";
     }
+    // the concentration-space entries d wdot_k / d C_l enter row k scaled by
+    // W_k / W_l (a literal), the column scaling of the conversion to mass
+    // fractions below, so that the conversion adds only its rank-one part
+    auto wk_over_wl = [&](int k, int l) { return sp(k, 0) * sp(l, 1); };  // W_k * (1 / W_l)
     for (int k : spc) {
       if (nu[k] == 0) continue;
       const int row = 1 + k;
       o << "        Jv[" << row * n << "] += " << nu_times(nu[k], "ro.dqdT") << ";\n";
-      for (int l : spc)
-        o << "        Jv[" << row * n + 1 + l << "] += " << nu_times(nu[k], "dq" + std::to_string(l)) << ";\n";
+      for (int l : spc) {
+        if (l == k)
+          o << "        Jv[" << row * n + 1 + l << "] += " << nu_times(nu[k], "dq" + std::to_string(l)) << ";\n";
+        else
+          o << "        Jv[" << row * n + 1 + l << "] += " << lit(nu[k] * wk_over_wl(k, l)) << " * dq" << l << ";\n";
+      }
       if (type != 0) {
         o << "        {\n          const double cM = " << nu_times(nu[k], "ro.dqdM") << ";\n";
-        for (int l = 0; l < N; ++l)
-          o << "          Jv[" << row * n + 1 + l << "] += cM * " << lit(eff(l)) << ";\n";
+        for (int l = 0; l < N; ++l) {
+          const double c = l == k ? eff(l) : eff(l) * wk_over_wl(k, l);
+          o << "          Jv[" << row * n + 1 + l << "] += cM * " << lit(c) << ";\n";
+        }
         o << "        }\n";
       }
     }
@@ -225,13 +235,17 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "  f[0] = -(Hw * invrho * invcp);\n"
     << "  if (WITH_J) {\n"
     << "    const double Wbar = 1.0 / sumYW;\n"
+    // row k holds S'_kl = (W_k / W_l) dwdot_k/dC_l; with s_k = sum_l S_kl C_l =
+    // (1 / W_k) sum_l S'_kl rho Y_l and a_k = W_k Wbar (wdot_k - s_k) / rho:
+    // dY_k/dY_l = S'_kl + a_k / W_l
+    << "    double rY[NS];\n#pragma unroll\n    for (int l = 0; l < NS; ++l) rY[l] = rho * y[1 + l];\n"
     << "#pragma unroll 1\n"
     << "    for (int k = 0; k < NS; ++k) {\n"
     << "      const int row = (1 + k) * n;\n      const double Wk = mv.sp[SP_REC * k];\n"
-    << "      double s = 0.0;\n#pragma unroll\n      for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * C[l];\n"
+    << "      double s = 0.0;\n#pragma unroll\n      for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * rY[l];\n"
+    << "      s = s * mv.sp[SP_REC * k + 1];\n"
     << "      const double wk = wdot[k];\n      const double a = Wk * Wbar * invrho * (wk - s);\n"
-    << "#pragma unroll\n      for (int i = 0; i < NS; ++i) {\n        const double iWi = mv.sp[SP_REC * i + 1];\n"
-    << "        Jv[row + 1 + i] = (Wk * Jv[row + 1 + i] + a) * iWi;\n      }\n"
+    << "#pragma unroll\n      for (int i = 0; i < NS; ++i) Jv[row + 1 + i] = fma(a, mv.sp[SP_REC * i + 1], Jv[row + 1 + i]);\n"
     << "      Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);\n    }\n"
     << "    double dcp = 0.0, cpf = 0.0;\n";
   for (int k = 0; k < N; ++k) {
@@ -241,8 +255,12 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
   }
   o
     << "    dcp = dcp * RU;\n    cpf = cpf * RU;\n"
+    // the temperature row's species weights (h_k/RT) / W_k, once
+    << "    double hw[NS];\n";
+  for (int k = 0; k < N; ++k) o << "    hw[" << k << "] = hRT[" << k << "] * " << lit(sp(k, 1)) << ";\n";
+  o
     << "#pragma unroll 1\n    for (int jc = 0; jc < n; ++jc) {\n      double acc = 0.0;\n"
-    << "#pragma unroll\n      for (int k = 0; k < NS; ++k) acc += hRT[k] * mv.sp[SP_REC * k + 1] * Jv[(1 + k) * n + jc];\n"
+    << "#pragma unroll\n      for (int k = 0; k < NS; ++k) acc += hw[k] * Jv[(1 + k) * n + jc];\n"
     << "      acc = acc * (RU * T);\n"
     << "      if (jc == 0) {\n        Jv[0] = -(invcp * (acc + cpf)) - f[0] * dcp * invcp;\n      } else {\n"
     << "        const double iWj = mv.sp[SP_REC * (jc - 1) + 1];\n        const double cpj = RU * cpR[jc - 1] * iWj;\n"
