@@ -386,6 +386,7 @@ static int ensure_adj_table(int dev) {
   if (dev < 0 || dev >= 64) return DF_OK;
   if (g_adj_ready[dev]) return DF_OK;
   RosTab t = make_rodas4();
+  if (!t.stiff_acc) return set_error(DF_EUNSUPPORTED, "RODAS4 table not stiffly accurate");  // ros_attempt relies on it
   int rc = cuda_check(cudaMemcpyToSymbol(c_tab_adj, &t, sizeof(t)), "upload RODAS4 table");
   if (!rc) g_adj_ready[dev] = true;
   return rc;

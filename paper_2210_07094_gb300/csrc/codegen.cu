@@ -87,11 +87,14 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "], double (&f)[" << n << "], SVT<double, ST> Jv) {\n"
     << "  constexpr int NS = " << N << ";\n  constexpr int n = NS + 1;\n"
     << "  const double T = y[0];\n  const double lnT = fast_log(T);\n  const double invT = 1.0 / T;\n"
-    << "  double C[NS], wdot[NS], gRT[NS], hRT[NS], cpR[NS];\n"
+    << "  double C[NS], wdot[NS], gRT[NS], hRT[NS], cpW[NS];  // cpW: cp_k / (R W_k)\n"
     << "  double sumYW = 0.0, cpm = 0.0;\n";
   auto sp = [&](int k, int i) { return m->blob_host[m->dims.off_sp + SP_REC * k + i]; };
   for (int k = 0; k < N; ++k) {
     const std::vector<double> a = {sp(k, 2), sp(k, 3), sp(k, 4), sp(k, 5), sp(k, 6)};
+    // cp_k / (R W_k) directly: the NASA-7 coefficients times 1 / W_k
+    std::vector<double> aw(a);
+    for (double& v : aw) v *= sp(k, 1);
     const std::vector<double> ah = {sp(k, SP_H), sp(k, SP_H + 1), sp(k, SP_H + 2), sp(k, SP_H + 3)};
     const std::vector<double> as = {sp(k, SP_S), sp(k, SP_S + 1), sp(k, SP_S + 2)};
     std::vector<double> hs = {sp(k, 2)};
@@ -99,13 +102,13 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     std::vector<double> ss = {sp(k, 3)};
     ss.insert(ss.end(), as.begin(), as.end());
     o << "  {  // species " << k << "\n"
-      << "    const double cpk = " << horner(a, "T") << ";\n    cpR[" << k << "] = cpk;\n"
+      << "    const double cpw = " << horner(aw, "T") << ";\n    cpW[" << k << "] = cpw;\n"
       << "    const double hk = " << horner(hs, "T") << " + " << lit(sp(k, 7)) << " * invT;\n"
       << "    const double sk = " << lit(sp(k, 2)) << " * lnT + T * (" << horner(ss, "T") << ") + " << lit(sp(k, 8))
       << ";\n"
       << "    hRT[" << k << "] = hk;\n    gRT[" << k << "] = hk - sk;\n"
       << "    sumYW += y[" << 1 + k << "] * " << lit(sp(k, 1)) << ";\n"
-      << "    cpm += y[" << 1 + k << "] * cpk * " << lit(sp(k, 1)) << ";\n  }\n";
+      << "    cpm += y[" << 1 + k << "] * cpw;\n  }\n";
   }
   o << "  cpm = cpm * RU;\n"
     << "  const double rho = pc * invT / (RU * sumYW);\n"
@@ -251,7 +254,7 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
   for (int k = 0; k < N; ++k) {
     const std::vector<double> d = {sp(k, 3), 2.0 * sp(k, 4), 3.0 * sp(k, 5), 4.0 * sp(k, 6)};
     o << "    dcp += y[" << 1 + k << "] * (" << horner(d, "T") << ") * " << lit(sp(k, 1)) << ";\n"
-      << "    cpf += cpR[" << k << "] * " << lit(sp(k, 1)) << " * f[" << 1 + k << "];\n";
+      << "    cpf += cpW[" << k << "] * f[" << 1 + k << "];\n";
   }
   o
     << "    dcp = dcp * RU;\n    cpf = cpf * RU;\n"
@@ -263,7 +266,7 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "#pragma unroll\n      for (int k = 0; k < NS; ++k) acc += hw[k] * Jv[(1 + k) * n + jc];\n"
     << "      acc = acc * (RU * T);\n"
     << "      if (jc == 0) {\n        Jv[0] = -(invcp * (acc + cpf)) - f[0] * dcp * invcp;\n      } else {\n"
-    << "        const double iWj = mv.sp[SP_REC * (jc - 1) + 1];\n        const double cpj = RU * cpR[jc - 1] * iWj;\n"
+    << "        const double cpj = RU * cpW[jc - 1];\n"
     << "        Jv[jc] = -(invcp * acc) - f[0] * cpj * invcp;\n      }\n    }\n  }\n"
     << "  return -Hw;\n}\n\n";
 }
@@ -552,6 +555,12 @@ bool finish_module(Module& r, const Driver& drv, const std::vector<char>& cubin,
     return false;
   }
   RosTab t[2] = {make_rodas4(), make_rodas3()};
+  if (!t[0].stiff_acc || !t[1].stiff_acc) {  // ros_attempt relies on it
+    r.why = "Rosenbrock table not stiffly accurate";
+    drv.unload(r.mod);
+    r.mod = nullptr;
+    return false;
+  }
   if (cudaMemcpy((void*)tab, t, sizeof(t), cudaMemcpyHostToDevice) != cudaSuccess) {
     r.why = "upload of the Rosenbrock tables failed";
     drv.unload(r.mod);

@@ -29,6 +29,8 @@ static int ensure_tables(int dev) {
   if (dev < 0 || dev >= 64) return DF_OK;
   if (g_tab_ready[dev]) return DF_OK;
   RosTab t[2] = {make_rodas4(), make_rodas3()};
+  // the thread path forms y_new and the error estimate from the last stage
+  if (!t[0].stiff_acc || !t[1].stiff_acc) return set_error(DF_EUNSUPPORTED, "Rosenbrock table not stiffly accurate");
   int rc = cuda_check(cudaMemcpyToSymbol(c_tab, t, sizeof(t)), "upload Rosenbrock tables");
   if (rc == DF_OK) g_tab_ready[dev] = true;
   return rc;

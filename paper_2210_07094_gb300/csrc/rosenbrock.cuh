@@ -21,9 +21,22 @@ struct RosTab {
   double m[6];
   double e[6];
   int newf[6];
+  // stiffly accurate: m is the last row of a plus the last stage (m_j = a_{s-1,j}
+  // for j < s - 1, m_{s-1} = 1), the error estimate is the last stage alone and
+  // the last stage evaluates f at its own state; then y_new = Y_{s-1} + K_{s-1}
+  // and err = K_{s-1}.  Both tables are (mark_stiffly_accurate); the kernels
+  // rely on it and the host uploads no other table.
+  int stiff_acc;
 };
 
 #ifndef __CUDACC_RTC__  // host-side table builders
+static void mark_stiffly_accurate(RosTab& t) {
+  const int l = t.s - 1;
+  bool sa = l > 0 && t.m[l] == 1.0 && t.newf[l] != 0;
+  for (int j = 0; j < l; ++j) sa = sa && t.m[j] == t.a[l][j] && t.e[j] == 0.0;
+  t.stiff_acc = sa && t.e[l] == 1.0 ? 1 : 0;
+}
+
 static RosTab make_rodas4() {
   RosTab t;
   memset(&t, 0, sizeof(t));
@@ -53,6 +66,7 @@ static RosTab make_rodas4() {
   t.m[5] = 1.0;
   t.e[5] = 1.0;
   for (int i = 0; i < 6; ++i) t.newf[i] = 1;
+  mark_stiffly_accurate(t);
   return t;
 }
 
@@ -83,6 +97,7 @@ static RosTab make_rodas3() {
   t.newf[1] = 0;  // a[1][*] = 0: stage 2 reuses f(y)
   t.newf[2] = 1;
   t.newf[3] = 1;
+  mark_stiffly_accurate(t);
   return t;
 }
 #endif
@@ -170,22 +185,24 @@ __device__ __forceinline__ bool ros_attempt(const MechView& mv, const RosTab& tb
     }
     lu_solve<n, ST>(Jv, piv, Ks);
   }
+  // stiffly accurate tables (see RosTab): ynew holds the last stage's state
+  // Y_{s-1} = y + sum_j a_{s-1,j} K_j, accumulated as y + sum_j m_j K_j would be,
+  // so y_new = Y_{s-1} + K_{s-1} is that sum's double, and err = K_{s-1}; a
+  // non-finite stage shows in y_new (integer test of its exponent), not in err
   double e2 = 0.0;
+  bool fin = true;
 #pragma unroll
   for (int i = 0; i < n; ++i) {
-    double yn = y[i], e = 0.0;
-    for (int s = 0; s < tb.s; ++s) {
-      const double kv = Kv[s * n + i];
-      yn += tb.m[s] * kv;
-      e += tb.e[s] * kv;
-    }
+    const double e = Kv[(tb.s - 1) * n + i];
+    const double yn = ynew[i] + e;
+    fin = fin && (__double2hiint(yn) & 0x7ff00000) != 0x7ff00000;
     ynew[i] = yn;
     const double sc = (i == 0 ? atolT : atolY) + rtol * fmax(fabs(y[i]), fabs(yn));
     const double r = e * rcp_nr(sc);
     e2 += r * r;
   }
   en = sqrt(e2 * (1.0 / n));
-  return ok && isfinite(en);
+  return ok && fin && isfinite(en);
 }
 
 // Ignition delay (Sec. 4.1 defines it by [dT/dt]_max): the largest dT/dt

@@ -100,9 +100,10 @@ def test_generated_literals_are_the_mechanism_numbers(tmp_path):
     for k, sp in enumerate(mech["species"]):
         a = sp["nasa7"]
         blk = src.split(f"// species {k}\n")[1].split("}")[0]
-        cp = _lits([ln for ln in blk.splitlines() if "cpk =" in ln][0])
+        # cp_k / (R W_k): the cp/R coefficients times the double 1 / W_k
+        cp = _lits([ln for ln in blk.splitlines() if "cpw =" in ln][0])
         top = max(i for i in range(5) if a[i] != 0.0 or i == 0)
-        assert cp == a[: top + 1]
+        assert cp == [c * (1.0 / sp["W"]) for c in a[: top + 1]]
         h = _lits([ln for ln in blk.splitlines() if "hk =" in ln][0])
         hpoly = [a[0]] + [a[i] / (i + 1) for i in range(1, 5)]
         htop = max(i for i in range(5) if hpoly[i] != 0.0 or i == 0)
