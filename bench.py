@@ -400,6 +400,9 @@ def profile_case(args):
     moved 50-300 K outside the training T range, half below, half above).
     fp64-chains: df_probe_fp64_chains over 1-8 warps per SM and 1-8 independent
     DFMA chains per thread (FP64 dependent latency against throughput).
+    adjoint: one df_chem_adjoint call on the adjoint workload (65536 cells of
+    the 9-species field, cotangents of sum T(dt) + sum qdot(dt), stored
+    stages): one launch of the adjoint kernel.
     h2: two thread-per-cell integrator launches (warm-up, measured) on 2^18
     cells of the bimodal 9-species field, in the launch shape the autotuner
     picks for the full field (32-thread blocks, as many per SM as fit, hottest
@@ -449,6 +452,22 @@ def profile_case(args):
             acc, rej = m.last_stats()
             print(json.dumps({"case": "h2", "rep": rep, "cells": 1 << 18, "ms": e0.elapsed_time(e1),
                               "accepted": acc, "rejected": rej, "failed": int((st != 0).sum())}))
+        return 0
+    if args.profile_case == "adjoint":
+        import paper_2210_07094_gb300 as df
+        from paper_2210_07094_gb300 import synth
+        mech = synth.h2_air_mechanism()
+        m = df.Mechanism(mech)
+        f = synth.field(3, mech)
+        T0, p, Y0 = (torch.tensor(f[k], device="cuda") for k in ("T", "p", "Y"))
+        ones = torch.ones_like(T0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = df.adjoint(m, T0, p, Y0, f["dt"], gT1=ones, gQ1=ones)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "adjoint", "cells": T0.numel(), "ms": e0.elapsed_time(e1),
+                          "failed": int((out["status"] != 0).sum())}))
         return 0
     if args.profile_case == "chon":
         import paper_2210_07094_gb300 as df
@@ -550,7 +569,7 @@ def main():
                     help="skip the adjoint and 50-species measurements")
     ap.add_argument("--dnn-train-seconds", type=float, default=60.0)
     ap.add_argument("--profile-case", default=None,
-                    choices=["gemm-l2", "dnn-infer", "dnn-train", "chon", "h2", "fp64-chains"],
+                    choices=["gemm-l2", "dnn-infer", "dnn-train", "chon", "h2", "fp64-chains", "adjoint"],
                     help="run one representative launch of a kernel for a profiler and exit")
     ap.add_argument("--cells", type=int, default=NCELLS,
                     help="cells per GPU (default: the 2^20-cell workload; smaller only for profiling)")
