@@ -84,7 +84,7 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
   const int N = m->dims.N, n = N + 1, M = m->dims.M;
   o << "template <bool WITH_J, int ST>\n"
     << "__device__ __forceinline__ double gen_eval(const MechView& mv, const double pc, const double (&y)[" << n
-    << "], double (&f)[" << n << "], SVT<double, ST> Jv) {\n"
+    << "], double (&f)[" << n << "], SVT<double, ST> Jv, SVT<double, ST> sM) {\n"
     << "  constexpr int NS = " << N << ";\n  constexpr int n = NS + 1;\n"
     << "  const double T = y[0];\n  const double lnT = fast_log(T);\n  const double invT = 1.0 / T;\n"
     << "  double C[NS], wdot[NS], gRT[NS], hRT[NS], cpW[NS];  // cpW: cp_k / (R W_k)\n"
@@ -99,14 +99,15 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     const std::vector<double> as = {sp(k, SP_S), sp(k, SP_S + 1), sp(k, SP_S + 2)};
     std::vector<double> hs = {sp(k, 2)};
     hs.insert(hs.end(), ah.begin(), ah.end());
-    std::vector<double> ss = {sp(k, 3)};
-    ss.insert(ss.end(), as.begin(), as.end());
+    // g/RT = h/RT - s/R in one polynomial: (a1 - a7) - a1 ln T
+    // + T (-a2/2 + T (-a3/6 + T (-a4/12 + T (-a5/20)))) + a6 / T
+    const std::vector<double> gs = {-0.5 * a[1], -a[2] / 6.0, -a[3] / 12.0, -a[4] / 20.0};
     o << "  {  // species " << k << "\n"
       << "    const double cpw = " << horner(aw, "T") << ";\n    cpW[" << k << "] = cpw;\n"
       << "    const double hk = " << horner(hs, "T") << " + " << lit(sp(k, 7)) << " * invT;\n"
-      << "    const double sk = " << lit(sp(k, 2)) << " * lnT + T * (" << horner(ss, "T") << ") + " << lit(sp(k, 8))
-      << ";\n"
-      << "    hRT[" << k << "] = hk;\n    gRT[" << k << "] = hk - sk;\n"
+      << "    const double gk = " << lit(sp(k, 2) - sp(k, 8)) << " + " << lit(-sp(k, 2)) << " * lnT + T * ("
+      << horner(gs, "T") << ") + " << lit(sp(k, 7)) << " * invT;\n"
+      << "    hRT[" << k << "] = hk;\n    gRT[" << k << "] = gk;\n"
       << "    sumYW += y[" << 1 + k << "] * " << lit(sp(k, 1)) << ";\n"
       << "    cpm += y[" << 1 + k << "] * cpw;\n  }\n";
   }
@@ -125,7 +126,12 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     for (int k = 1; k < N; ++k) o << "  ctot += C[" << k << "];\n";
   }
   o
-    << "  if (WITH_J) {\n#pragma unroll\n    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;\n  }\n"
+    << "  if (WITH_J) {\n#pragma unroll\n    for (int i = 0; i < n * n; ++i) Jv[i] = 0.0;\n";
+  // the unit part of the collider efficiencies, sum over reactions of
+  // nu_k d q / d[M], one value per row (sM, the stage vectors' storage, idle
+  // while J is built); the conversion below adds it to every column
+  if (any_collider) o << "#pragma unroll\n    for (int k = 0; k < NS; ++k) sM[k] = 0.0;\n";
+  o << "  }\n"
     << "  const double lnP0RT = LOG_PSTD_RU - lnT;\n";
   for (int j = 0; j < M; ++j) {
     const RxMeta mt = meta_of(m, j);
@@ -220,9 +226,11 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
           o << "        Jv[" << row * n + 1 + l << "] += " << lit(nu[k] * wk_over_wl(k, l)) << " * dq" << l << ";\n";
       }
       if (type != 0) {
-        o << "        {\n          const double cM = " << nu_times(nu[k], "ro.dqdM") << ";\n";
+        o << "        {\n          const double cM = " << nu_times(nu[k], "ro.dqdM") << ";\n"
+          << "          sM[" << k << "] += cM;\n";
         for (int l = 0; l < N; ++l) {
-          const double c = l == k ? eff(l) : eff(l) * wk_over_wl(k, l);
+          if (eff(l) == 1.0) continue;
+          const double c = l == k ? eff(l) - 1.0 : (eff(l) - 1.0) * wk_over_wl(k, l);
           o << "          Jv[" << row * n + 1 + l << "] += cM * " << lit(c) << ";\n";
         }
         o << "        }\n";
@@ -247,7 +255,9 @@ void emit_eval(std::ostringstream& o, const df_mech* m) {
     << "      const int row = (1 + k) * n;\n      const double Wk = mv.sp[SP_REC * k];\n"
     << "      double s = 0.0;\n#pragma unroll\n      for (int l = 0; l < NS; ++l) s += Jv[row + 1 + l] * rY[l];\n"
     << "      s = s * mv.sp[SP_REC * k + 1];\n"
-    << "      const double wk = wdot[k];\n      const double a = Wk * Wbar * invrho * (wk - s);\n"
+    << (any_collider ? "      const double sMk = sM[k];\n      s = fma(sMk, ctot, s);\n" : "")
+    << "      const double wk = wdot[k];\n      double a = Wk * Wbar * invrho * (wk - s);\n"
+    << (any_collider ? "      a = fma(Wk, sMk, a);\n" : "")
     << "#pragma unroll\n      for (int i = 0; i < NS; ++i) Jv[row + 1 + i] = fma(a, mv.sp[SP_REC * i + 1], Jv[row + 1 + i]);\n"
     << "      Jv[row] = Wk * invrho * (Jv[row] + (wk - s) * invT);\n    }\n"
     << "    double dcp = 0.0, cpf = 0.0;\n";
@@ -282,11 +292,11 @@ std::string jit_thread_source(const df_mech* m) {
     << "  static constexpr bool kSpeciesVectors = false;\n"
     << "  template <int NS, bool WITH_J, bool CONSTV, int ST>\n"
     << "  __device__ __forceinline__ static double run(const MechView& mv, double pc, const double (&y)[NS + 1],\n"
-    << "                                               double (&f)[NS + 1], SVT<double, ST>, SVT<double, ST>,\n"
+    << "                                               double (&f)[NS + 1], SVT<double, ST> scratch, SVT<double, ST>,\n"
     << "                                               SVT<double, ST>, SVT<double, ST>, SVT<double, ST>,\n"
     << "                                               SVT<double, ST> Jv) {\n"
     << "    static_assert(!CONSTV, \"generated evaluation: constant pressure\");\n"
-    << "    return gen_eval<WITH_J, ST>(mv, pc, y, f, Jv);\n  }\n};\n\n}  // namespace df\n";
+    << "    return gen_eval<WITH_J, ST>(mv, pc, y, f, Jv, scratch);\n  }\n};\n\n}  // namespace df\n";
   return o.str();
 }
 

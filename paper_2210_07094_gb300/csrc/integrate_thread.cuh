@@ -78,8 +78,11 @@ __global__ void __launch_bounds__(128, 1) k_integrate_thread(IntegArgs a) {
   const MechView mv = make_view(blob, a.d, etab);
   double* ws = smem + boff + tid;
   typedef SVT<double, BT> V;
-  constexpr int nv = EVAL::kSpeciesVectors ? NS : 0;  // species vectors absent: views unused
-  V C{ws, stride};
+  constexpr int nv = EVAL::kSpeciesVectors ? NS : 0;
+  // without species vectors in shared memory (the generated evaluation) the
+  // first view is the evaluation's scratch while J is built: the stage vectors'
+  // storage, idle then
+  V C{ws + (nv > 0 ? 0 : (n * n) * stride), stride};
   V wdot{ws + nv * stride, stride};
   V gRT{ws + 2 * nv * stride, stride};
   V hRT{ws + 3 * nv * stride, stride};

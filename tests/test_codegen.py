@@ -108,10 +108,12 @@ def test_generated_literals_are_the_mechanism_numbers(tmp_path):
         hpoly = [a[0]] + [a[i] / (i + 1) for i in range(1, 5)]
         htop = max(i for i in range(5) if hpoly[i] != 0.0 or i == 0)
         assert h == pytest.approx(hpoly[: htop + 1] + [a[5]], rel=1e-15)
-        s = _lits([ln for ln in blk.splitlines() if "sk =" in ln][0])
-        spoly = [a[1]] + [a[i] / i for i in range(2, 5)]
-        stop = max(i for i in range(4) if spoly[i] != 0.0 or i == 0)
-        assert s == pytest.approx([a[0]] + spoly[: stop + 1] + [a[6]], rel=1e-15)
+        # g/RT = h/RT - s/R as one polynomial: (a1 - a7) - a1 ln T
+        # + T (-a2/2 - a3 T/6 - a4 T^2/12 - a5 T^3/20) + a6 / T
+        g = _lits([ln for ln in blk.splitlines() if "gk =" in ln][0])
+        gpoly = [-a[1] / 2.0, -a[2] / 6.0, -a[3] / 12.0, -a[4] / 20.0]
+        gtop = max(i for i in range(4) if gpoly[i] != 0.0 or i == 0)
+        assert g == pytest.approx([a[0] - a[6], -a[0]] + gpoly[: gtop + 1] + [a[5]], rel=1e-15)
         iw = _lits([ln for ln in blk.splitlines() if "sumYW +=" in ln][0])
         assert iw == [pytest.approx(1.0 / sp["W"], rel=1e-15)]
         fl = [ln for ln in src.splitlines() if ln.strip().startswith(f"f[{1 + k}] =")][0]
