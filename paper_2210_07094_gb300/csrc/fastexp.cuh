@@ -4,9 +4,11 @@
 //   x = (64 m + j) ln2/64 + r,  |r| <= ln2/128,
 //   exp(x) = 2^m * 2^(j/64) * exp(r),  exp(r) - 1 = r + r^2/2 + ... + r^5/120.
 // The 64 entries 2^(j/64) are stored as a double-double (hi + lo), each part
-// rounded to nearest from a 60-digit decimal evaluation; the reduction uses
-// ln2/64 split into two doubles with fused multiply-adds.  The truncated Taylor
-// tail r^6/720 <= 3.5e-17 stays below one ulp.  |x| >= 700, inf and NaN go to
+// rounded to nearest from a 60-digit decimal evaluation; the evaluation uses
+// the leading part (about 1 ulp in all instead of about half of one, one FP64
+// operation fewer); the reduction uses ln2/64 split into two doubles with
+// fused multiply-adds.  The truncated Taylor tail r^6/720 <= 3.5e-17 stays
+// below one ulp.  |x| >= 700, inf and NaN go to
 // the library exp().  The kernels stage the table into shared memory (lanes
 // index it with different j).  A variant with 256 entries 2^(j/256) (|r| <=
 // ln2/512, so exp(r) - 1 needs terms only up to r^4/24, the tail r^5/120 <=
@@ -138,8 +140,11 @@ __device__ __forceinline__ double exp_tang_core_b(double x, const double2* tab) 
   }
   q = fma(q, r, 0.5);
   const double p = fma(q, r2, r);                // exp(r) - 1
-  const double2 tj = tab[j];
-  const double s = tj.x + fma(tj.x, p, tj.y);    // 2^(j/2^B) * exp(r)
+  // 2^(j/2^B) exp(r) = t + t p with t the table's leading double alone: one
+  // rounding more than with its trailing part (about 1 ulp in all, within the
+  // 2 ulp the tests allow) for one FP64 operation less
+  const double tj = tab[j].x;
+  const double s = fma(tj, p, tj);
   return __hiloint2double(__double2hiint(s) + (int)((unsigned)m << 20), __double2loint(s));
 }
 
