@@ -69,8 +69,9 @@ def test_generated_source_compiles_with_nvrtc(tmp_path):
     names = [b"df::k_integrate_thread<9, false, 32, df::GenEval>", b"&df::c_tab"]
     for nm in names:
         assert nv.nvrtcAddNameExpression(prog, nm) == 0
+    # the options the library compiles the module with (the 256-entry exp table)
     opts = [b"--gpu-architecture=sm_103a", b"-std=c++17", b"-I" + CSRC.encode(), b"-default-device",
-            b"-diag-suppress=177"]
+            b"-diag-suppress=177", b"-DDF_EXP_TABLE_BITS=8"]
     rc = nv.nvrtcCompileProgram(prog, len(opts), (C.c_char_p * len(opts))(*opts))
     n = C.c_size_t()
     nv.nvrtcGetProgramLogSize(prog, C.byref(n))
@@ -137,3 +138,45 @@ def test_generated_literals_are_the_mechanism_numbers(tmp_path):
             expect = [np.log(lo["A"]) - np.log(r["A"]), lo["b"], lo["Ea"] * 1e3 / R, tr["alpha"],
                       1.0 / tr["T3"], 1.0 / tr["T1"], tr["T2"], 0.0]
             assert trp == pytest.approx(expect, rel=1e-14, abs=1e-300)
+
+
+def test_generated_jacobian_entries_are_prescaled(tmp_path):
+    """The Jacobian entries the generator writes: row k (a species the reaction
+    changes, net coefficient nu_k) gets d q / d C_l scaled by nu_k W_k / W_l,
+    the column scaling of the conversion to mass fractions; a third-body or
+    falloff reaction adds nu_k d q / d[M] to the row's unit sum sM[k] and enters
+    only the efficiencies that are not 1, as (eps_l - 1) W_k / W_l."""
+    mech = synth.h2_air_mechanism()
+    src = _source(mech, tmp_path)
+    names = [s["name"] for s in mech["species"]]
+    N = len(names)
+    n = N + 1
+    W = [s["W"] for s in mech["species"]]
+    iW = [1.0 / w for w in W]
+    for j, r in enumerate(mech["reactions"]):
+        blk = src.split(f"// reaction {j}\n")[1].split("// reaction")[0].split("double Hw")[0]
+        jac = blk.split("if (WITH_J) {")[1]
+        nu = {}
+        for sp_, v in r["reactants"].items():
+            nu[names.index(sp_)] = nu.get(names.index(sp_), 0) - v
+        for sp_, v in r["products"].items():
+            nu[names.index(sp_)] = nu.get(names.index(sp_), 0) + v
+        species = sorted(set(names.index(x) for x in list(r["reactants"]) + list(r["products"])))
+        for k, vk in nu.items():
+            if vk == 0:
+                continue
+            row = (1 + k) * n
+            for l in species:
+                if l == k:
+                    continue
+                lines = [ln for ln in jac.splitlines() if f"Jv[{row + 1 + l}] +=" in ln and f"* dq{l};" in ln]
+                assert len(lines) == 1, (j, k, l)
+                assert _lits(lines[0]) == [vk * (W[k] * iW[l])]
+            if r["type"] != "elementary":
+                assert f"sM[{k}] += cM;" in jac
+                eff = [r.get("efficiencies", {}).get(nm, 1.0) for nm in names]
+                cm = jac.split(f"sM[{k}] += cM;")[1].split("}")[0]
+                got = {int(m.group(1)) - row - 1: _lits(m.group(0))[0]
+                       for m in re.finditer(r"Jv\[(\d+)\] \+= cM \* (\(-?0x[0-9a-fA-F.]+p[+-]?\d+\))", cm)}
+                want = {l: (eff[l] - 1.0) * (1.0 if l == k else W[k] * iW[l]) for l in range(N) if eff[l] != 1.0}
+                assert got == want, (j, k)
